@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark: one MPPI iteration (arXiv 2308.01654, Algorithm 1) per step on GB300.
+
+Default workload ("roofline"): K=65536 samples, T=200 steps, dt=0.025 s, straight
+2000-point lane, 64 static obstacles x 3 circles; synthetic seeded inputs.  A step
+is the whole iteration: Philox noise, fused rollout+cost, argmin, softmin
+weights, weighted update, Savitzky-Golay smoothing, x* rollout, warm start.
+
+Metric: rollout-steps/s (K*T per iteration / iteration time), higher is better.
+  value     device time with inputs resident in HBM (CUDA events on the planner's
+            stream, L2 flushed between steps by writing a 256 MB buffer)
+  e2e       the same metric through mppi_plan() with host buffers: input H2D and
+            output D2H copies inside the timed region
+  roofline  the rollout kernel (the dominant kernel) against the FP32-pipe peak
+  cpu_baseline  the FP64 oracle on the host cores over a bounded sample
+N > 1 (torchrun): every rank runs an independent planner on its own GPU (weak
+scaling, no collective on the data path); value = all ranks' rollout-steps / the
+slowest rank's time.
+
+--impl reference times the FP64 oracle itself (the CPU baseline) per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rollout-steps/s (K*T) of one MPPI iteration"
+UNIT = "rollout-steps/s"
+KERNEL_LAUNCHES_PER_STEP = 7   # prep, noise, rollout, argmin, weights, wsum, finalize
+
+
+# ------------------------------------------------------------------------ helpers
+
+def rollout_ops_per_step(prob) -> float:
+    """Algorithmic FP32-pipe operations per rollout-step of the fused rollout+cost kernel.
+
+    The per-step model: ~60 operations for the dynamics, the five cost terms and the
+    control cost; 6 per (ego circle, obstacle circle) pair (every pair is tested,
+    as d_obj = min over all circles defines); and the exact nearest-segment search:
+    5 per 32-segment chunk bound plus ~11 per segment of ~2 scanned chunks.
+    """
+    p = prob.params
+    n_e, n_c, n_ref = int(p["n_ego"]), int(prob.circles.shape[0]), int(prob.ref.shape[0])
+    return 60.0 + 6.0 * n_e * n_c + 5.0 * math.ceil((n_ref - 1) / 32.0) + 11.0 * 64.0
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_id_for(device_index: int) -> str:
+    import torch
+    try:
+        u = torch.cuda.get_device_properties(device_index).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            return vis.split(",")[device_index]
+        return str(device_index)
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------------ CPU baseline (the oracle)
+
+def oracle_sample(prob, seconds: float):
+    """Time oracle.plan (the whole iteration, FP64) on a sample of K' samples of the same workload."""
+    import oracle
+    oracle.build()
+    probe = prob.copy()
+    k0 = min(prob.K, 64)
+    probe.params["K"] = k0
+    t = time.perf_counter()
+    oracle.plan(probe)
+    dt = max(time.perf_counter() - t, 1e-6)
+    k = int(max(k0, min(prob.K, k0 * seconds / dt)))
+    return k
+
+
+def time_oracle(prob, k_sample: int):
+    import oracle
+    q = prob.copy()
+    q.params["K"] = k_sample
+    t = time.perf_counter()
+    r = oracle.plan(q)
+    el = time.perf_counter() - t
+    assert r.rc == 0
+    return el
+
+
+# ------------------------------------------------------------------------ the GPU arm
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2308_01654_gb300 as mp
+    from paper_2308_01654_gb300 import scenarios
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    prob = scenarios.by_name(args.workload)
+    prob.params["session"] = rank                      # an independent planning problem per rank
+    K, T = prob.K, prob.T
+    stream = torch.cuda.current_stream()
+    pl = mp.Planner(prob.params, device=local, stream=stream.cuda_stream)
+    pl.set_profiling(True)
+    x0 = torch.tensor(prob.x0, dtype=torch.float64, device=dev)
+    ref = torch.tensor(prob.ref, dtype=torch.float64, device=dev)
+    circ = torch.tensor(prob.circles, dtype=torch.float64, device=dev)
+    cen = None if prob.centres is None else torch.tensor(prob.centres, dtype=torch.float64, device=dev)
+    u_out = torch.empty((T, 2), dtype=torch.float64, device=dev)
+    x_out = torch.empty((T + 1, 4), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def step():
+        pl.plan_device(x0, ref, circ, cen, u_out, x_out)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    info = pl.sync()
+    assert info["n_finite"] > 0
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    sampler = ClockSampler(gpu_id_for(local)) if not args.no_clocks else None
+    barrier()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    step_ms, roll_ms, ktimes = [], [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        kt = pl.kernel_times()                         # waits for this step
+        step_ms.append(e0.elapsed_time(e1))
+        roll_ms.append(kt["rollout"])
+        ktimes.append(kt)
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    pl.sync()
+
+    ms_step = statistics.mean(step_ms)
+    ms_roll = statistics.mean(roll_ms)
+    if world > 1:
+        t = torch.tensor([ms_step, ms_roll], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step, ms_roll = float(t[0]), float(t[1])
+    value = world * K * T / (ms_step * 1e-3)
+
+    # end to end through the host-buffer C ABI: H2D of inputs and D2H of outputs every step
+    h2d = 8 * (4 + prob.ref.size + prob.circles.size + (0 if prob.centres is None else prob.centres.size))
+    d2h = 8 * (2 * T + 4 * (T + 1))
+    with mp.Planner(prob.params, device=local) as pe:
+        for _ in range(max(1, args.warmup)):
+            pe.plan(prob.x0, prob.ref, prob.circles, prob.centres)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pe.plan(prob.x0, prob.ref, prob.circles, prob.centres)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t[0])
+    e2e = {"value": world * K * T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3}
+
+    # roofline of the rollout kernel: FP32-pipe bound (no dense contraction, noise bytes << compute)
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    peaks = measured_peaks()
+    f_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tops = n_sm * 128 * f_max * 1e6 / 1e12
+    ops = rollout_ops_per_step(prob) * K * T
+    achieved = ops / (ms_roll * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TOP/s",
+                "frac": achieved / peak_tops, "traffic": args.traffic,
+                "kernel": "rollout_kernel", "ops_per_rollout_step": rollout_ops_per_step(prob),
+                "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {f_max:.0f} MHz (max SM clock)",
+                "kernel_ms": ms_roll}
+    kmean = {k: statistics.mean(d[k] for d in ktimes) for k in ktimes[0]}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" + ("+bf16-noise" if prob.params["noise_bf16"] else "") + "+f64-reduce",
+        "data": "synthetic (seeded generator shaped like the paper's driving scenes)",
+        "config": {"workload": f"{prob.name}: K={K} T={T} dt={prob.params['dt']} n_ref={prob.ref.shape[0]} "
+                               f"n_circ={prob.circles.shape[0]}", "K": K, "T": T,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed between steps (256 MB write)"},
+        "e2e": e2e, "roofline": roofline, "gpu_launches": KERNEL_LAUNCHES_PER_STEP * args.steps,
+        "kernel_ms": kmean, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        k_s = oracle_sample(prob, args.cpu_seconds)
+        el = time_oracle(prob, k_s)
+        out["cpu_baseline"] = {"value": k_s * T / el, "unit": UNIT, "cores": oracle.num_threads(),
+                               "kind": "oracle",
+                               "sample": f"one full FP64 iteration at K={k_s} of the same workload (T={T}), "
+                                         f"{el:.1f} s"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    pl.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------------ the reference arm (the oracle)
+
+def run_reference(args, world, rank, local):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2308_01654_gb300 import scenarios
+    prob = scenarios.by_name(args.workload)
+    T = prob.T
+    budget = max(2.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    k_s = oracle_sample(prob, budget)
+    for _ in range(args.warmup):
+        time_oracle(prob, min(k_s, 64))
+    times = [time_oracle(prob, k_s) for _ in range(args.steps)]
+    s = statistics.mean(times)
+    value = k_s * T / s
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": s * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"{prob.name}: K={prob.K} T={T} (timed on a K={k_s} sample per step)"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": f"one full FP64 iteration at K={k_s} of the same workload per step"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="roofline",
+                    choices=["roofline", "roofline_bf16", "closed_loop", "single_plan"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per rollout launch from an ncu capture of the current kernel")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank, local)
+    else:
+        run_gpu(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * mppi.h - C ABI of the GB300 (sm_103a) MPPI motion planner.
+ *
+ * One call of mppi_plan() is one iteration of the Model Predictive Path Integral
+ * planner of Testouri, Elghazaly and Frank, "Towards a Safe Real-Time Motion
+ * Planning Framework for Autonomous Driving Systems: A Model Predictive Path
+ * Integral Approach" (arXiv 2308.01654), Algorithm 1 (one pass of its loop):
+ *
+ *   1. draw K Gaussian perturbations eps ~ N(0, Sigma) of the control sequence
+ *      (Algorithm 1 GenerateRandomNoise; Eq. (1)),
+ *   2. roll every perturbed sequence out through the kinematic bicycle model
+ *      (Eq. (5), explicit Euler) over T steps and add up the step cost
+ *      (Eq. (6)-(9) and the five terms of Sec. IV-C, Eq. (12)-(18)),
+ *   3. take the minimum cost and the min-shifted softmin weights with
+ *      temperature lambda (Eq. (11)),
+ *   4. move the nominal controls by the weighted average perturbation (Eq. (11)),
+ *   5. smooth with the 5-point Savitzky-Golay filter (Eq. (19)), roll out the
+ *      optimal trajectory x* and shift the warm start (Algorithm 1, last lines).
+ *
+ * Conventions
+ *  - Channel 0 of a control is the acceleration a [m/s^2], channel 1 the
+ *    steering angle delta [rad].  States are (x [m], y [m], yaw [rad], v [m/s]).
+ *  - Arrays are row-major and tightly packed, element type double unless noted.
+ *  - Host arrays belong to the caller and are only read (inputs) or written
+ *    (outputs) during the call.  Device arrays passed to the *_device entry
+ *    points must stay valid until the work queued on the context's stream has
+ *    finished.
+ *  - Every function returns an mppi_status (0 = MPPI_OK, negative = error);
+ *    nothing is thrown across the ABI.  mppi_last_error() gives a message.
+ *  - A context is not thread-safe: use one context per host thread.
+ *  - All arithmetic of the iteration runs in this library's CUDA kernels; there
+ *    is no CPU fallback.  Without a usable GPU mppi_create() fails with
+ *    MPPI_ERR_CUDA.
+ */
+#ifndef MPPI_H
+#define MPPI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPPI_MAX_EGO 8          /* ego-vehicle circles */
+#define MPPI_MAX_T 1024         /* horizon steps */
+#define MPPI_MAX_REF 4096       /* reference polyline vertices (held in shared memory) */
+#define MPPI_MAX_CIRC 1024      /* obstacle circles */
+
+/* Opaque planner context: owns the device buffers, a stream and the warm start. */
+typedef struct mppi_ctx mppi_ctx;
+
+typedef enum {
+    MPPI_OK = 0,
+    MPPI_ERR_ARG = -1,       /* invalid argument or non-finite input */
+    MPPI_ERR_OOM = -2,       /* device or pinned host allocation failed */
+    MPPI_ERR_CUDA = -3,      /* a CUDA call failed (message in mppi_last_error) */
+    MPPI_ERR_NUMERIC = -4,   /* no sample cost was finite; the controls are left unchanged */
+    MPPI_ERR_TIMEOUT = -5,   /* a bounded device wait ran out */
+    MPPI_ERR_CAPACITY = -6   /* a size exceeds a fixed capacity of the library or context */
+} mppi_status;
+
+/* Obstacle circle C_k = {x_k, y_k, r_k} (Sec. III, Fig. 3) with a constant velocity:
+   its centre at rollout step t (state x_{t+1}) is (x, y) + (vx, vy) * (t + 1) * dt. */
+typedef struct {
+    double x, y, r, vx, vy;
+} mppi_circle;
+
+/* Hyper-parameters (Algorithm 1 "Given": M = K, T, lambda, gamma, Sigma, R, D, Z). */
+typedef struct {
+    int32_t K;                  /* samples (rollouts), >= 1 */
+    int32_t T;                  /* horizon steps, 1 ..  MPPI_MAX_T */
+    double dt;                  /* step [s], > 0 */
+    double wheelbase;           /* l of Eq. (5) [m], > 0 */
+    double sigma[2];            /* noise standard deviations per channel, >= 0 */
+    double u_min[2], u_max[2];  /* control box; u + eps is clamped into it */
+    double lam;                 /* softmin temperature lambda, > 0 */
+    double gamma;               /* alpha = (gamma - 1) / (2 gamma) of Eq. (9), > 0 */
+    double R[2];                /* diagonal control weight of Eq. (8) */
+    double w_dist, w_target, w_yaw, w_speed, w_safe;   /* Eq. (18): 15, 7, 120, 5, 25 */
+    double w_terminal;          /* terminal cost phi(x_T) = w_terminal * q_x(x_T); 0 = none */
+    double v_ref;               /* reference speed v^r of Eq. (15) [m/s] */
+    double v_max;               /* speed cap v_G on the rollouts; +inf disables it */
+    double d_safe_c, d_safe_0;  /* d_safe = d_safe_c * v + d_safe_0, Eq. (16) */
+    int32_t collision_only;     /* 1: c_safe only where d_obj <= 0 (Sec. IV-C, object avoidance) */
+    int32_t n_ego;              /* ego circles, 0 .. MPPI_MAX_EGO */
+    double ego_offset[MPPI_MAX_EGO];  /* centre offset along the heading from (x, y) [m] */
+    double ego_radius[MPPI_MAX_EGO];  /* radius [m] */
+    int32_t ref_mode;           /* 0: closest point of the polyline, 1: closest vertex */
+    int32_t sg_enable;          /* 1: Savitzky-Golay smoothing (Eq. (19)) */
+    int32_t shift;              /* 1: warm start u_t <- u*_{t+1} (receding horizon) */
+    int32_t noise_bf16;         /* 1: store the noise as bfloat16 (half the bytes) */
+    uint64_t seed;              /* Philox key */
+    uint32_t session;           /* Philox counter word 3: independent streams per session */
+    int32_t group;              /* lanes per sample in the rollout kernel: 0 = choose, else 1,2,4,8,16,32 */
+} mppi_params;
+
+/* Results of one iteration. */
+typedef struct {
+    int32_t argmin;             /* index of the lowest-cost sample (ties: lowest index) */
+    int32_t n_finite;           /* samples with a finite cost */
+    double s_min;               /* lowest cost S_min */
+    double eta;                 /* sum of the softmin weights exp(-(S_k - S_min) / lambda) */
+    uint64_t iter;              /* iteration index used for the noise counter */
+} mppi_info;
+
+/* Fills *p with the defaults: the paper's cost weights, gamma = 1, R = lam / sigma^2,
+   three ego circles of radius 1.1 m at 0, 1.35 and 2.7 m, SG on, no shift, seed 0. */
+int mppi_default_params(mppi_params* p, int32_t K, int32_t T, double dt);
+
+/* Creates a planner on CUDA device `device`.  cuda_stream is a cudaStream_t to
+   queue work on (NULL: the context creates its own non-blocking stream).  The
+   context owns all device buffers; they are sized here for params->K and T,
+   a reference of up to max_ref vertices and max_circ circles (0: the library
+   maxima); later calls do not allocate.  The nominal controls start at zero. */
+int mppi_create(const mppi_params* params, int device, void* cuda_stream, int32_t max_ref,
+                int32_t max_circ, mppi_ctx** out_ctx);
+
+/* Frees every resource of the context; NULL is accepted. */
+int mppi_destroy(mppi_ctx* ctx);
+
+/* Changes the stream later work is queued on (NULL: the context's own stream). */
+int mppi_set_stream(mppi_ctx* ctx, void* cuda_stream);
+
+/* One MPPI iteration from host buffers; returns when the outputs are written.
+   x0[4]          initial state (Algorithm 1 GetInitialState)
+   ref_xy[n_ref][2] reference polyline vertices, n_ref >= 2 (the road model B, Eq. (3))
+   circ[n_circ]   obstacle circles (Algorithm 1 ApproximateObstacles), may be NULL if 0
+   centres        optional [T][n_circ][2] predicted centres per step (overrides vx, vy)
+   u_out[T][2]    smoothed controls u* (Algorithm 1 SavitzkyGolayFilter)
+   x_out[T+1][4]  optimal trajectory x*, x_out[0] = x0
+   info           optional results record
+   The warm start (the context's nominal controls) is updated in place.
+   Errors: MPPI_ERR_ARG for bad sizes or non-finite inputs (nothing changes),
+   MPPI_ERR_CAPACITY above the context's capacities, MPPI_ERR_NUMERIC when no
+   sample cost is finite (controls unchanged, outputs not written). */
+int mppi_plan(mppi_ctx* ctx, const double* x0, const double* ref_xy, int32_t n_ref,
+              const mppi_circle* circ, int32_t n_circ, const double* centres,
+              double* u_out, double* x_out, mppi_info* info);
+
+/* The same iteration with every array in device memory (same layouts; circ is
+   [n_circ][5] doubles).  Queued on the context's stream and returns at once
+   when info is NULL; with a host info pointer it waits and reports the status.
+   Non-finite device inputs turn the iteration into a no-op whose status is
+   reported by the next call that waits (mppi_sync). */
+int mppi_plan_device(mppi_ctx* ctx, const double* d_x0, const double* d_ref_xy, int32_t n_ref,
+                     const double* d_circ, int32_t n_circ, const double* d_centres,
+                     double* d_u_out, double* d_x_out, mppi_info* info);
+
+/* Waits for the context's queued work and returns the status of the last iteration. */
+int mppi_sync(mppi_ctx* ctx, mppi_info* info);
+
+/* Warm start I/O (checkpoint / resume): U[T][2] host doubles and the iteration index. */
+int mppi_set_controls(mppi_ctx* ctx, const double* U, uint64_t iter);
+int mppi_get_controls(mppi_ctx* ctx, double* U, uint64_t* iter);
+
+/* Debug / parity views of the last iteration (host outputs, waits for the stream):
+   S[K] sample costs; z[T][K][2] unit normals as float (bf16 widened exactly). */
+int mppi_get_costs(mppi_ctx* ctx, double* S);
+int mppi_get_noise(mppi_ctx* ctx, float* z);
+
+/* Raw Philox4x32-10 words on the device for n host counters ctr[n][4] and key
+   (seed low, seed high): the generator used by the noise kernel. out[n][4]. */
+int mppi_philox(uint64_t seed, const uint32_t* ctr, int32_t n, uint32_t* out);
+
+/* Per-kernel timing with CUDA events on the context's stream (the library's own
+   tracing; no effect on results).  When on, each iteration records
+   MPPI_N_KERNELS + 1 events; mppi_kernel_times() waits for the last iteration
+   and writes the durations in milliseconds of its kernels, in launch order:
+   prep, noise, rollout, argmin, weights, wsum, finalize. */
+#define MPPI_N_KERNELS 7
+int mppi_set_profiling(mppi_ctx* ctx, int32_t on);
+int mppi_kernel_times(mppi_ctx* ctx, float* ms, int32_t n);
+
+const char* mppi_status_string(int status);
+const char* mppi_last_error(mppi_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPPI_H */

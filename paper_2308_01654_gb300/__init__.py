@@ -1,0 +1,275 @@
+"""GB300-native MPPI motion planner (arXiv 2308.01654): Python binding of ``libmppi.so``.
+
+The binding only marshals arguments to the C ABI declared in ``include/mppi.h``;
+every step of the iteration runs in the library's CUDA kernels.  There is no CPU
+fallback: if the library cannot be built or loaded, or no GPU is present, the
+calls raise.
+
+Typical use::
+
+    from paper_2308_01654_gb300 import Planner, scenarios
+    prob = scenarios.single_plan()
+    with Planner(prob.params) as pl:
+        u, x, info = pl.plan(prob.x0, prob.ref, prob.circles)
+
+``plan_device`` takes torch CUDA tensors (float64) and queues the iteration on the
+planner's stream without host copies.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Dict, Optional, Tuple
+
+import numpy as np
+
+from . import _build
+
+MAX_EGO = 8
+MAX_T = 1024
+MAX_REF = 4096
+MAX_CIRC = 1024
+
+STATUS = {0: "MPPI_OK", -1: "MPPI_ERR_ARG", -2: "MPPI_ERR_OOM", -3: "MPPI_ERR_CUDA", -4: "MPPI_ERR_NUMERIC",
+          -5: "MPPI_ERR_TIMEOUT", -6: "MPPI_ERR_CAPACITY"}
+
+
+class MppiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MppiParams(C.Structure):
+    _fields_ = [
+        ("K", C.c_int32), ("T", C.c_int32), ("dt", C.c_double), ("wheelbase", C.c_double),
+        ("sigma", C.c_double * 2), ("u_min", C.c_double * 2), ("u_max", C.c_double * 2),
+        ("lam", C.c_double), ("gamma", C.c_double), ("R", C.c_double * 2),
+        ("w_dist", C.c_double), ("w_target", C.c_double), ("w_yaw", C.c_double), ("w_speed", C.c_double),
+        ("w_safe", C.c_double), ("w_terminal", C.c_double),
+        ("v_ref", C.c_double), ("v_max", C.c_double),
+        ("d_safe_c", C.c_double), ("d_safe_0", C.c_double),
+        ("collision_only", C.c_int32), ("n_ego", C.c_int32),
+        ("ego_offset", C.c_double * MAX_EGO), ("ego_radius", C.c_double * MAX_EGO),
+        ("ref_mode", C.c_int32), ("sg_enable", C.c_int32), ("shift", C.c_int32), ("noise_bf16", C.c_int32),
+        ("seed", C.c_uint64), ("session", C.c_uint32), ("group", C.c_int32),
+    ]
+
+
+class MppiInfo(C.Structure):
+    _fields_ = [("argmin", C.c_int32), ("n_finite", C.c_int32), ("s_min", C.c_double), ("eta", C.c_double),
+                ("iter", C.c_uint64)]
+
+    def as_dict(self) -> Dict[str, object]:
+        return dict(argmin=self.argmin, n_finite=self.n_finite, s_min=self.s_min, eta=self.eta, iter=self.iter)
+
+
+_lib = None
+
+# every entry point of include/mppi.h with its ctypes signature
+_VP, _DP, _FP, _U32P = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float), C.POINTER(C.c_uint32)
+SIGNATURES = {
+    "mppi_default_params": (C.c_int, [C.POINTER(MppiParams), C.c_int32, C.c_int32, C.c_double]),
+    "mppi_create": (C.c_int, [C.POINTER(MppiParams), C.c_int, _VP, C.c_int32, C.c_int32, C.POINTER(_VP)]),
+    "mppi_destroy": (C.c_int, [_VP]),
+    "mppi_set_stream": (C.c_int, [_VP, _VP]),
+    "mppi_plan": (C.c_int, [_VP, _DP, _DP, C.c_int32, _DP, C.c_int32, _DP, _DP, _DP, C.POINTER(MppiInfo)]),
+    "mppi_plan_device": (C.c_int, [_VP, _VP, _VP, C.c_int32, _VP, C.c_int32, _VP, _VP, _VP, C.POINTER(MppiInfo)]),
+    "mppi_sync": (C.c_int, [_VP, C.POINTER(MppiInfo)]),
+    "mppi_set_controls": (C.c_int, [_VP, _DP, C.c_uint64]),
+    "mppi_get_controls": (C.c_int, [_VP, _DP, C.POINTER(C.c_uint64)]),
+    "mppi_get_costs": (C.c_int, [_VP, _DP]),
+    "mppi_get_noise": (C.c_int, [_VP, _FP]),
+    "mppi_philox": (C.c_int, [C.c_uint64, _U32P, C.c_int32, _U32P]),
+    "mppi_set_profiling": (C.c_int, [_VP, C.c_int32]),
+    "mppi_kernel_times": (C.c_int, [_VP, _FP, C.c_int32]),
+    "mppi_status_string": (C.c_char_p, [C.c_int]),
+    "mppi_last_error": (C.c_char_p, [_VP]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Build (if needed) and load libmppi.so; raises if that is impossible."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, ctx=None):
+    if rc != 0:
+        msg = lib().mppi_last_error(ctx)
+        raise MppiError(rc, msg.decode() if msg else "")
+
+
+def make_params(p: Dict[str, object]) -> MppiParams:
+    """Fill the C parameter struct from a parameter dictionary (scenarios.default_params keys)."""
+    s = MppiParams()
+    s.K, s.T = int(p["K"]), int(p["T"])
+    s.dt, s.wheelbase = float(p["dt"]), float(p["wheelbase"])
+    for name in ("sigma", "u_min", "u_max", "R"):
+        arr = getattr(s, name)
+        arr[0], arr[1] = float(p[name][0]), float(p[name][1])
+    s.lam, s.gamma = float(p["lam"]), float(p["gamma"])
+    for name in ("w_dist", "w_target", "w_yaw", "w_speed", "w_safe", "w_terminal", "v_ref", "v_max",
+                 "d_safe_c", "d_safe_0"):
+        setattr(s, name, float(p[name]))
+    s.collision_only = int(p["collision_only"])
+    s.n_ego = int(p["n_ego"])
+    for e in range(min(max(s.n_ego, 0), MAX_EGO)):
+        s.ego_offset[e] = float(p["ego_offset"][e])
+        s.ego_radius[e] = float(p["ego_radius"][e])
+    s.ref_mode, s.sg_enable, s.shift = int(p["ref_mode"]), int(p["sg_enable"]), int(p["shift"])
+    s.noise_bf16 = int(p["noise_bf16"])
+    s.seed = int(p["seed"]) & 0xFFFFFFFFFFFFFFFF
+    s.session = int(p["session"]) & 0xFFFFFFFF
+    s.group = int(p.get("group", 0))
+    return s
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _dp(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(_DP)
+
+
+class Planner:
+    """One planner context (device buffers, stream, warm start) on one GPU."""
+
+    def __init__(self, params: Dict[str, object], device: int = 0, stream: Optional[int] = None,
+                 max_ref: int = 0, max_circ: int = 0):
+        self.params = dict(params)
+        self.K, self.T = int(params["K"]), int(params["T"])
+        self._p = make_params(params)
+        h = _VP()
+        rc = lib().mppi_create(C.byref(self._p), int(device), _VP(stream) if stream else None, int(max_ref),
+                               int(max_circ), C.byref(h))
+        _check(rc)
+        self._h = h
+
+    # context management ------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mppi_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_stream(self, stream: Optional[int]):
+        _check(lib().mppi_set_stream(self._h, _VP(stream) if stream else None), self._h)
+
+    # the iteration -----------------------------------------------------------
+    def plan(self, x0, ref, circles=None, centres=None) -> Tuple[np.ndarray, np.ndarray, Dict[str, object]]:
+        """One MPPI iteration from host arrays; returns (u*[T][2], x*[T+1][4], info)."""
+        x0 = _f64(x0)
+        ref = _f64(ref).reshape(-1, 2)
+        circ = _f64(np.zeros((0, 5)) if circles is None else circles).reshape(-1, 5)
+        cen = None if centres is None else _f64(centres)
+        u = np.empty((self.T, 2))
+        x = np.empty((self.T + 1, 4))
+        info = MppiInfo()
+        rc = lib().mppi_plan(self._h, _dp(x0), _dp(ref), ref.shape[0], _dp(circ) if circ.shape[0] else None,
+                             circ.shape[0], _dp(cen), _dp(u), _dp(x), C.byref(info))
+        _check(rc, self._h)
+        return u, x, info.as_dict()
+
+    def plan_device(self, x0, ref, circles, centres, u_out, x_out, wait: bool = False):
+        """One iteration on torch CUDA float64 tensors, queued on the planner's stream."""
+        info = MppiInfo() if wait else None
+        ptr = (lambda t: None if t is None else _VP(t.data_ptr()))
+        n_circ = 0 if circles is None else int(circles.shape[0])
+        rc = lib().mppi_plan_device(self._h, ptr(x0), ptr(ref), int(ref.shape[0]), ptr(circles) if n_circ else None,
+                                    n_circ, ptr(centres), ptr(u_out), ptr(x_out),
+                                    C.byref(info) if wait else None)
+        _check(rc, self._h)
+        return info.as_dict() if wait else None
+
+    def sync(self) -> Dict[str, object]:
+        info = MppiInfo()
+        _check(lib().mppi_sync(self._h, C.byref(info)), self._h)
+        return info.as_dict()
+
+    # warm start and debug views ------------------------------------------------
+    def set_controls(self, U, iter_: int = 0):
+        U = _f64(U).reshape(self.T, 2)
+        _check(lib().mppi_set_controls(self._h, _dp(U), int(iter_)), self._h)
+
+    def get_controls(self):
+        U = np.empty((self.T, 2))
+        it = C.c_uint64()
+        _check(lib().mppi_get_controls(self._h, _dp(U), C.byref(it)), self._h)
+        return U, it.value
+
+    def get_costs(self) -> np.ndarray:
+        S = np.empty(self.K)
+        _check(lib().mppi_get_costs(self._h, _dp(S)), self._h)
+        return S
+
+    def get_noise(self) -> np.ndarray:
+        z = np.empty((self.T, self.K, 2), dtype=np.float32)
+        _check(lib().mppi_get_noise(self._h, z.ctypes.data_as(_FP)), self._h)
+        return z
+
+
+KERNELS = ("prep", "noise", "rollout", "argmin", "weights", "wsum", "finalize")
+
+
+def _kernel_times(self) -> Dict[str, float]:
+    """Per-kernel durations (ms) of the last iteration; needs set_profiling(True)."""
+    ms = (C.c_float * len(KERNELS))()
+    _check(lib().mppi_kernel_times(self._h, ms, len(KERNELS)), self._h)
+    return dict(zip(KERNELS, [float(v) for v in ms]))
+
+
+def _set_profiling(self, on: bool = True):
+    _check(lib().mppi_set_profiling(self._h, 1 if on else 0), self._h)
+
+
+Planner.kernel_times = _kernel_times
+Planner.set_profiling = _set_profiling
+
+
+def philox(seed: int, ctr) -> np.ndarray:
+    """Raw Philox4x32-10 words computed on the GPU for counters ctr[n][4]."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+    out = np.empty_like(c)
+    rc = lib().mppi_philox(int(seed) & 0xFFFFFFFFFFFFFFFF, c.ctypes.data_as(_U32P), c.shape[0],
+                           out.ctypes.data_as(_U32P))
+    _check(rc)
+    return out
+
+
+def default_params(K: int, T: int, dt: float) -> MppiParams:
+    p = MppiParams()
+    _check(lib().mppi_default_params(C.byref(p), K, T, dt))
+    return p
+
+
+INF = math.inf

@@ -1,0 +1,531 @@
+// mppi_api.cu - the C ABI of include/mppi.h: contexts, buffers, validation, launch order.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "mppi.h"
+#include "mppi_device.cuh"
+#include "mppi_internal.h"
+
+using namespace mppi;
+
+struct mppi_ctx {
+    mppi_params p;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    int cap_ref = 0, cap_circ = 0;
+    PlanConst pc{};
+    PlanBuffers b{};
+    double* d_in = nullptr;      // x0 | ref | circ | centres (binary64, device)
+    double* d_out = nullptr;     // u_out [T][2] | x_out [T+1][4]
+    double* h_in = nullptr;      // pinned staging of the same layout
+    double* h_out = nullptr;     // pinned staging of outputs
+    DevState* h_state = nullptr; // pinned copy of the device record
+    size_t in_elems = 0, out_elems = 0;
+    int group = 1;
+    int profiling = 0;
+    cudaEvent_t ev[N_KERNELS + 1] = {};
+    std::string err;
+};
+
+static thread_local std::string g_err;
+
+static int fail(mppi_ctx* c, int status, const std::string& msg) {
+    if (c) c->err = msg;
+    g_err = msg;
+    return status;
+}
+
+static int cuda_fail(mppi_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, MPPI_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+static bool finite_all(const double* v, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!isfinite(v[i])) return false;
+    return true;
+}
+
+static int check_params(const mppi_params* p, std::string& why) {
+    if (!p) { why = "params is NULL"; return MPPI_ERR_ARG; }
+    if (p->K < 1) { why = "K must be >= 1"; return MPPI_ERR_ARG; }
+    if (p->T < 1 || p->T > MPPI_MAX_T) { why = "T must be in [1, MPPI_MAX_T]"; return MPPI_ERR_ARG; }
+    if (!(p->dt > 0.0) || !isfinite(p->dt)) { why = "dt must be finite and > 0"; return MPPI_ERR_ARG; }
+    if (!(p->wheelbase > 0.0) || !isfinite(p->wheelbase)) { why = "wheelbase must be > 0"; return MPPI_ERR_ARG; }
+    if (!(p->lam > 0.0)) { why = "lam must be > 0"; return MPPI_ERR_ARG; }
+    if (!(p->gamma > 0.0) || !isfinite(p->gamma)) { why = "gamma must be > 0"; return MPPI_ERR_ARG; }
+    for (int c = 0; c < 2; ++c) {
+        if (!(p->sigma[c] >= 0.0) || !isfinite(p->sigma[c])) { why = "sigma must be finite and >= 0"; return MPPI_ERR_ARG; }
+        if (!isfinite(p->u_min[c]) || !isfinite(p->u_max[c]) || !(p->u_min[c] <= p->u_max[c])) {
+            why = "u_min <= u_max must hold with finite bounds";
+            return MPPI_ERR_ARG;
+        }
+        if (!isfinite(p->R[c])) { why = "R must be finite"; return MPPI_ERR_ARG; }
+    }
+    if (p->n_ego < 0 || p->n_ego > MPPI_MAX_EGO) { why = "n_ego must be in [0, MPPI_MAX_EGO]"; return MPPI_ERR_ARG; }
+    const double w[] = {p->w_dist, p->w_target, p->w_yaw, p->w_speed, p->w_safe, p->w_terminal,
+                        p->v_ref, p->d_safe_c, p->d_safe_0};
+    if (!finite_all(w, sizeof(w) / sizeof(w[0]))) { why = "weights and speeds must be finite"; return MPPI_ERR_ARG; }
+    if (isnan(p->v_max)) { why = "v_max must not be NaN"; return MPPI_ERR_ARG; }
+    for (int e = 0; e < p->n_ego; ++e)
+        if (!isfinite(p->ego_offset[e]) || !isfinite(p->ego_radius[e])) { why = "ego circles must be finite"; return MPPI_ERR_ARG; }
+    if (p->ref_mode != 0 && p->ref_mode != 1) { why = "ref_mode must be 0 or 1"; return MPPI_ERR_ARG; }
+    const int g = p->group;
+    if (!(g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32)) {
+        why = "group must be 0, 1, 2, 4, 8, 16 or 32";
+        return MPPI_ERR_ARG;
+    }
+    return MPPI_OK;
+}
+
+static int auto_group(int K) {
+    // enough lanes to keep every SM busy when K is small; one lane per sample when K is large
+    const long long target = 152LL * 512LL;
+    int g = 1;
+    while (g < 32 && (long long)K * g * 2 <= target) g *= 2;
+    return g;
+}
+
+static PlanConst make_const(const mppi_params& p) {
+    PlanConst c{};
+    c.K = p.K;
+    c.T = p.T;
+    c.dt = (float)p.dt;
+    c.dt_over_L = (float)(p.dt / p.wheelbase);
+    c.sig_a = (float)p.sigma[0];
+    c.sig_d = (float)p.sigma[1];
+    c.amin = (float)p.u_min[0];
+    c.amax = (float)p.u_max[0];
+    c.dmin = (float)p.u_min[1];
+    c.dmax = (float)p.u_max[1];
+    c.w_dist = (float)p.w_dist;
+    c.w_target = (float)p.w_target;
+    c.w_yaw = (float)p.w_yaw;
+    c.w_speed = (float)p.w_speed;
+    c.w_safe = (float)p.w_safe;
+    c.w_terminal = (float)p.w_terminal;
+    c.v_ref = (float)p.v_ref;
+    c.vcap = isfinite(p.v_max) ? 1 : 0;
+    c.v_max = c.vcap ? (float)p.v_max : 0.0f;
+    c.d_safe_c = (float)p.d_safe_c;
+    c.d_safe_0 = (float)p.d_safe_0;
+    c.collision_only = p.collision_only ? 1 : 0;
+    c.n_ego = p.n_ego;
+    c.ego_same_radius = 1;
+    for (int e = 0; e < 8; ++e) {
+        c.ego_off[e] = e < p.n_ego ? (float)p.ego_offset[e] : 0.0f;
+        c.ego_rad[e] = e < p.n_ego ? (float)p.ego_radius[e] : 0.0f;
+        if (e < p.n_ego && p.ego_radius[e] != p.ego_radius[0]) c.ego_same_radius = 0;
+    }
+    c.ref_mode = p.ref_mode;
+    c.has_table = 0;
+    c.key0 = (uint32_t)(p.seed & 0xffffffffull);
+    c.key1 = (uint32_t)(p.seed >> 32);
+    c.session = p.session;
+    c.lam = p.lam;
+    c.dt_d = p.dt;
+    c.wheelbase_d = p.wheelbase;
+    c.amin_d = p.u_min[0];
+    c.amax_d = p.u_max[0];
+    c.dmin_d = p.u_min[1];
+    c.dmax_d = p.u_max[1];
+    c.v_max_d = p.v_max;
+    const double alpha = (p.gamma - 1.0) / (2.0 * p.gamma);
+    c.g_a = (1.0 + alpha) * p.R[0];
+    c.g_d = (1.0 + alpha) * p.R[1];
+    c.half_Ra = 0.5 * p.R[0];
+    c.half_Rd = 0.5 * p.R[1];
+    c.sg_enable = p.sg_enable ? 1 : 0;
+    c.shift = p.shift ? 1 : 0;
+    return c;
+}
+
+static void free_all(mppi_ctx* c) {
+    PlanBuffers& b = c->b;
+    void* dev[] = {b.state, b.scene, b.table, b.z, b.S, b.w, b.eta_part, b.min_part, b.min_idx_part,
+                   b.min_cnt_part, b.du_part, b.U, c->d_in, c->d_out};
+    for (void* p : dev)
+        if (p) cudaFree(p);
+    if (c->h_in) cudaFreeHost(c->h_in);
+    if (c->h_out) cudaFreeHost(c->h_out);
+    if (c->h_state) cudaFreeHost(c->h_state);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+}
+
+extern "C" {
+
+int mppi_default_params(mppi_params* p, int32_t K, int32_t T, double dt) {
+    if (!p) return MPPI_ERR_ARG;
+    memset(p, 0, sizeof(*p));
+    p->K = K;
+    p->T = T;
+    p->dt = dt;
+    p->wheelbase = 2.7;
+    p->sigma[0] = 0.5;
+    p->sigma[1] = 0.05;
+    p->u_min[0] = -3.0;
+    p->u_max[0] = 3.0;
+    p->u_min[1] = -0.5;
+    p->u_max[1] = 0.5;
+    p->lam = 1.0;
+    p->gamma = 1.0;
+    p->R[0] = p->lam / (p->sigma[0] * p->sigma[0]);
+    p->R[1] = p->lam / (p->sigma[1] * p->sigma[1]);
+    p->w_dist = 15.0;
+    p->w_target = 7.0;
+    p->w_yaw = 120.0;
+    p->w_speed = 5.0;
+    p->w_safe = 25.0;
+    p->w_terminal = 0.0;
+    p->v_ref = 30.0 / 3.6;
+    p->v_max = INFINITY;
+    p->d_safe_c = 0.0;
+    p->d_safe_0 = 0.5;
+    p->n_ego = 3;
+    p->ego_offset[0] = 0.0;
+    p->ego_offset[1] = 1.35;
+    p->ego_offset[2] = 2.7;
+    p->ego_radius[0] = p->ego_radius[1] = p->ego_radius[2] = 1.1;
+    p->sg_enable = 1;
+    return MPPI_OK;
+}
+
+int mppi_create(const mppi_params* params, int device, void* cuda_stream, int32_t max_ref, int32_t max_circ,
+                mppi_ctx** out_ctx) {
+    std::string why;
+    if (!out_ctx) return fail(nullptr, MPPI_ERR_ARG, "out_ctx is NULL");
+    *out_ctx = nullptr;
+    int rc = check_params(params, why);
+    if (rc != MPPI_OK) return fail(nullptr, rc, why);
+    if (max_ref < 0 || max_ref > MPPI_MAX_REF || max_circ < 0 || max_circ > MPPI_MAX_CIRC)
+        return fail(nullptr, MPPI_ERR_CAPACITY, "max_ref / max_circ above the library maxima");
+    mppi_ctx* c = new (std::nothrow) mppi_ctx();
+    if (!c) return fail(nullptr, MPPI_ERR_OOM, "host allocation failed");
+    c->p = *params;
+    c->device = device;
+    c->cap_ref = max_ref ? max_ref : MPPI_MAX_REF;
+    c->cap_circ = max_circ ? max_circ : MPPI_MAX_CIRC;
+    c->group = params->group ? params->group : auto_group(params->K);
+    c->pc = make_const(*params);
+    auto bail = [&](int status) {
+        free_all(c);
+        delete c;
+        return status;
+    };
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaSetDevice"));
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaStreamCreate"));
+        c->stream = c->own_stream;
+    }
+    const int K = params->K, T = params->T;
+    PlanBuffers& b = c->b;
+    b.n_mblk = (int)std::min<long long>((K + 255) / 256, 296);
+    b.n_wblk = b.n_mblk;
+    b.kt_size = 256 * 8;
+    b.n_kt = (K + b.kt_size - 1) / b.kt_size;
+    b.n_tt = (T + 31) / 32;
+    const SceneLayout Lmax = make_layout(T, c->cap_ref, c->cap_circ);
+    const size_t zbytes = (size_t)T * K * (params->noise_bf16 ? 4 : 8);
+    c->in_elems = 4 + 2 * (size_t)c->cap_ref + 5 * (size_t)c->cap_circ + 2 * (size_t)T * c->cap_circ;
+    c->out_elems = 2 * (size_t)T + 4 * (size_t)(T + 1);
+    struct A {
+        void** p;
+        size_t n;
+    } allocs[] = {
+        {(void**)&b.state, sizeof(DevState)},
+        {(void**)&b.scene, (size_t)Lmax.bytes},
+        {(void**)&b.table, sizeof(float2) * (size_t)T * std::max(c->cap_circ, 1)},
+        {(void**)&b.z, zbytes},
+        {(void**)&b.S, sizeof(double) * K},
+        {(void**)&b.w, sizeof(float) * K},
+        {(void**)&b.eta_part, sizeof(double) * b.n_wblk},
+        {(void**)&b.min_part, sizeof(double) * b.n_mblk},
+        {(void**)&b.min_idx_part, sizeof(int) * b.n_mblk},
+        {(void**)&b.min_cnt_part, sizeof(int) * b.n_mblk},
+        {(void**)&b.du_part, sizeof(double) * 2 * (size_t)T * b.n_kt},
+        {(void**)&b.U, sizeof(double) * 2 * (size_t)T},
+        {(void**)&c->d_in, sizeof(double) * c->in_elems},
+        {(void**)&c->d_out, sizeof(double) * c->out_elems},
+    };
+    for (auto& a : allocs) {
+        e = cudaMalloc(a.p, a.n);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(nullptr, MPPI_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e)));
+        }
+    }
+    if (cudaMallocHost((void**)&c->h_in, sizeof(double) * c->in_elems) != cudaSuccess ||
+        cudaMallocHost((void**)&c->h_out, sizeof(double) * c->out_elems) != cudaSuccess ||
+        cudaMallocHost((void**)&c->h_state, sizeof(DevState)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(nullptr, MPPI_ERR_OOM, "pinned host allocation failed"));
+    }
+    DevState s0;
+    memset(&s0, 0, sizeof(s0));
+    s0.jkey = ~0ull;
+    e = cudaMemcpyAsync(b.state, &s0, sizeof(s0), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.U, 0, sizeof(double) * 2 * (size_t)T, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "context initialisation"));
+    *out_ctx = c;
+    return MPPI_OK;
+}
+
+int mppi_destroy(mppi_ctx* c) {
+    if (!c) return MPPI_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+    return MPPI_OK;
+}
+
+int mppi_set_stream(mppi_ctx* c, void* cuda_stream) {
+    if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    c->stream = cuda_stream ? (cudaStream_t)cuda_stream : c->own_stream;
+    if (!c->stream) {
+        CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        c->stream = c->own_stream;
+    }
+    return MPPI_OK;
+}
+
+static int check_sizes(mppi_ctx* c, int32_t n_ref, int32_t n_circ) {
+    if (n_ref < 2) return fail(c, MPPI_ERR_ARG, "n_ref must be >= 2");
+    if (n_circ < 0) return fail(c, MPPI_ERR_ARG, "n_circ must be >= 0");
+    if (n_ref > c->cap_ref || n_circ > c->cap_circ)
+        return fail(c, MPPI_ERR_CAPACITY, "reference or circle count above the context capacity");
+    const SceneLayout L = make_layout(c->p.T, n_ref, n_circ);
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if ((int)rollout_smem_bytes(L) + 1024 > max_smem)
+        return fail(c, MPPI_ERR_CAPACITY, "reference + circles + horizon exceed shared memory");
+    return MPPI_OK;
+}
+
+static int enqueue(mppi_ctx* c, const PlanInputs& in, int has_table) {
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const SceneLayout L = make_layout(c->p.T, in.n_ref, in.n_circ);
+    PlanConst pc = c->pc;
+    pc.has_table = has_table;
+    CK(launch_iteration(pc, L, c->b, in, c->group, c->p.noise_bf16, c->stream, c->profiling ? c->ev : nullptr),
+       "kernel launch");
+    return MPPI_OK;
+}
+
+static void fill_info(const DevState& s, mppi_info* info) {
+    if (!info) return;
+    info->argmin = s.argmin;
+    info->n_finite = s.n_finite;
+    info->s_min = s.s_min;
+    info->eta = 0.0;
+    info->iter = s.iter_used;
+}
+
+static int wait_status(mppi_ctx* c, mppi_info* info, double eta_unused) {
+    (void)eta_unused;
+    CK(cudaMemcpyAsync(c->h_state, c->b.state, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "state copy");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    const DevState& s = *c->h_state;
+    if (info) {
+        fill_info(s, info);
+        info->eta = s.eta;
+    }
+    if (s.status == MPPI_ERR_ARG) return fail(c, MPPI_ERR_ARG, "non-finite input detected on the device");
+    if (s.status == MPPI_ERR_TIMEOUT) return fail(c, MPPI_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (s.status == MPPI_ERR_NUMERIC) return fail(c, MPPI_ERR_NUMERIC, "no sample cost was finite");
+    return s.status;
+}
+
+int mppi_plan(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n_ref, const mppi_circle* circ,
+              int32_t n_circ, const double* centres, double* u_out, double* x_out, mppi_info* info) {
+    if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
+    if (!x0 || !ref_xy || !u_out || !x_out || (n_circ > 0 && !circ))
+        return fail(c, MPPI_ERR_ARG, "NULL array argument");
+    int rc = check_sizes(c, n_ref, n_circ);
+    if (rc != MPPI_OK) return rc;
+    const int T = c->p.T;
+    const size_t nr = 2 * (size_t)n_ref, nc = 5 * (size_t)n_circ, nt = centres ? 2 * (size_t)T * n_circ : 0;
+    if (!finite_all(x0, 4) || !finite_all(ref_xy, nr) || !finite_all((const double*)circ, nc) ||
+        (centres && !finite_all(centres, nt)))
+        return fail(c, MPPI_ERR_ARG, "non-finite input");
+    double* h = c->h_in;
+    memcpy(h, x0, 4 * sizeof(double));
+    memcpy(h + 4, ref_xy, nr * sizeof(double));
+    if (nc) memcpy(h + 4 + nr, circ, nc * sizeof(double));
+    if (nt) memcpy(h + 4 + nr + nc, centres, nt * sizeof(double));
+    const size_t n_in = 4 + nr + nc + nt;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    CK(cudaMemcpyAsync(c->d_in, h, n_in * sizeof(double), cudaMemcpyHostToDevice, c->stream), "input copy");
+    PlanInputs in;
+    in.x0 = c->d_in;
+    in.ref = c->d_in + 4;
+    in.circ = c->d_in + 4 + nr;
+    in.centres = nt ? c->d_in + 4 + nr + nc : nullptr;
+    in.n_ref = n_ref;
+    in.n_circ = n_circ;
+    in.u_out = c->d_out;
+    in.x_out = c->d_out + 2 * (size_t)T;
+    rc = enqueue(c, in, nt ? 1 : 0);
+    if (rc != MPPI_OK) return rc;
+    CK(cudaMemcpyAsync(c->h_out, c->d_out, c->out_elems * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+       "output copy");
+    rc = wait_status(c, info, 0.0);
+    if (rc != MPPI_OK) return rc;
+    memcpy(u_out, c->h_out, 2 * (size_t)T * sizeof(double));
+    memcpy(x_out, c->h_out + 2 * (size_t)T, 4 * (size_t)(T + 1) * sizeof(double));
+    return MPPI_OK;
+}
+
+int mppi_plan_device(mppi_ctx* c, const double* d_x0, const double* d_ref_xy, int32_t n_ref, const double* d_circ,
+                     int32_t n_circ, const double* d_centres, double* d_u_out, double* d_x_out, mppi_info* info) {
+    if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
+    if (!d_x0 || !d_ref_xy || !d_u_out || !d_x_out || (n_circ > 0 && !d_circ))
+        return fail(c, MPPI_ERR_ARG, "NULL array argument");
+    int rc = check_sizes(c, n_ref, n_circ);
+    if (rc != MPPI_OK) return rc;
+    PlanInputs in;
+    in.x0 = d_x0;
+    in.ref = d_ref_xy;
+    in.circ = n_circ > 0 ? d_circ : c->d_in;
+    in.centres = d_centres;
+    in.n_ref = n_ref;
+    in.n_circ = n_circ;
+    in.u_out = d_u_out;
+    in.x_out = d_x_out;
+    rc = enqueue(c, in, d_centres ? 1 : 0);
+    if (rc != MPPI_OK) return rc;
+    if (info) return wait_status(c, info, 0.0);
+    return MPPI_OK;
+}
+
+int mppi_sync(mppi_ctx* c, mppi_info* info) {
+    if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    return wait_status(c, info, 0.0);
+}
+
+int mppi_set_controls(mppi_ctx* c, const double* U, uint64_t iter) {
+    if (!c || !U) return fail(c, MPPI_ERR_ARG, "NULL argument");
+    if (!finite_all(U, 2 * (size_t)c->p.T)) return fail(c, MPPI_ERR_ARG, "non-finite controls");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    CK(cudaMemcpyAsync(c->b.U, U, sizeof(double) * 2 * c->p.T, cudaMemcpyHostToDevice, c->stream), "controls copy");
+    unsigned long long it = iter;
+    CK(cudaMemcpyAsync(&c->b.state->iter, &it, sizeof(it), cudaMemcpyHostToDevice, c->stream), "iter copy");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    return MPPI_OK;
+}
+
+int mppi_get_controls(mppi_ctx* c, double* U, uint64_t* iter) {
+    if (!c || !U) return fail(c, MPPI_ERR_ARG, "NULL argument");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    CK(cudaMemcpyAsync(U, c->b.U, sizeof(double) * 2 * c->p.T, cudaMemcpyDeviceToHost, c->stream), "controls copy");
+    CK(cudaMemcpyAsync(c->h_state, c->b.state, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "state copy");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (iter) *iter = c->h_state->iter;
+    return MPPI_OK;
+}
+
+int mppi_get_costs(mppi_ctx* c, double* S) {
+    if (!c || !S) return fail(c, MPPI_ERR_ARG, "NULL argument");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    CK(cudaMemcpyAsync(S, c->b.S, sizeof(double) * c->p.K, cudaMemcpyDeviceToHost, c->stream), "cost copy");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    return MPPI_OK;
+}
+
+int mppi_get_noise(mppi_ctx* c, float* z) {
+    if (!c || !z) return fail(c, MPPI_ERR_ARG, "NULL argument");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const size_t n = 2 * (size_t)c->p.T * c->p.K;
+    if (!c->p.noise_bf16) {
+        CK(cudaMemcpyAsync(z, c->b.z, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "noise copy");
+        CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+        return MPPI_OK;
+    }
+    // bfloat16 -> binary32 is an exact widening: the 16 bits become the top half
+    uint16_t* tmp = (uint16_t*)malloc(n * sizeof(uint16_t));
+    if (!tmp) return fail(c, MPPI_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaMemcpyAsync(tmp, c->b.z, n * sizeof(uint16_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        free(tmp);
+        return cuda_fail(c, e, "noise copy");
+    }
+    for (size_t i = 0; i < n; ++i) {
+        const uint32_t bits = (uint32_t)tmp[i] << 16;
+        memcpy(&z[i], &bits, 4);
+    }
+    free(tmp);
+    return MPPI_OK;
+}
+
+int mppi_philox(uint64_t seed, const uint32_t* ctr, int32_t n, uint32_t* out) {
+    mppi_ctx* c = nullptr;
+    if (!ctr || !out || n < 0) return fail(nullptr, MPPI_ERR_ARG, "bad argument");
+    if (n == 0) return MPPI_OK;
+    uint4 *d_ctr = nullptr, *d_out = nullptr;
+    const size_t bytes = sizeof(uint4) * (size_t)n;
+    CK(cudaMalloc(&d_ctr, bytes), "cudaMalloc");
+    cudaError_t e = cudaMalloc(&d_out, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(d_ctr, ctr, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_philox(make_uint2((uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32)), d_ctr, d_out, n, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d_out, bytes, cudaMemcpyDeviceToHost);
+    cudaFree(d_ctr);
+    if (d_out) cudaFree(d_out);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "philox");
+    return MPPI_OK;
+}
+
+int mppi_set_profiling(mppi_ctx* c, int32_t on) {
+    if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    if (on && !c->ev[0])
+        for (auto& e : c->ev) CK(cudaEventCreate(&e), "cudaEventCreate");
+    c->profiling = on ? 1 : 0;
+    return MPPI_OK;
+}
+
+int mppi_kernel_times(mppi_ctx* c, float* ms, int32_t n) {
+    if (!c || !ms || n < N_KERNELS) return fail(c, MPPI_ERR_ARG, "ms must hold MPPI_N_KERNELS floats");
+    if (!c->profiling) return fail(c, MPPI_ERR_ARG, "profiling is off");
+    CK(cudaEventSynchronize(c->ev[N_KERNELS]), "cudaEventSynchronize");
+    for (int i = 0; i < N_KERNELS; ++i) CK(cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]), "cudaEventElapsedTime");
+    return MPPI_OK;
+}
+
+const char* mppi_status_string(int status) {
+    switch (status) {
+        case MPPI_OK: return "MPPI_OK";
+        case MPPI_ERR_ARG: return "MPPI_ERR_ARG: invalid argument";
+        case MPPI_ERR_OOM: return "MPPI_ERR_OOM: allocation failed";
+        case MPPI_ERR_CUDA: return "MPPI_ERR_CUDA: CUDA error";
+        case MPPI_ERR_NUMERIC: return "MPPI_ERR_NUMERIC: no finite sample cost";
+        case MPPI_ERR_TIMEOUT: return "MPPI_ERR_TIMEOUT: bounded device wait ran out";
+        case MPPI_ERR_CAPACITY: return "MPPI_ERR_CAPACITY: size above capacity";
+        default: return "unknown status";
+    }
+}
+
+const char* mppi_last_error(mppi_ctx* c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// mppi_device.cuh - device math of the MPPI iteration (arXiv 2308.01654), sm_103a.
+//
+// Shared by the noise, rollout and update kernels so that each quantity that two
+// kernels must agree on (the noise words, the clamped perturbation eps') comes
+// from one function and is bit-identical wherever it is recomputed.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mppi {
+
+// Chunking of the reference polyline for the exact bounded nearest-segment search:
+// level-1 chunks of L1 segments, level-2 groups of L2 level-1 chunks.
+constexpr int REF_L1 = 16;
+constexpr int REF_L2 = 16;
+
+// Status bits raised on the device (DevState::flags).
+constexpr int FLAG_NONFINITE_INPUT = 1;
+constexpr int FLAG_TIMEOUT = 2;
+
+// -----------------------------------------------------------------------------
+// Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11):
+// ten rounds of two 32x32->64 multiplications whose halves are XORed with the
+// other two counter words and the round key; the key advances by the Weyl
+// increments between rounds.  Noise of sample k at steps 2j and 2j+1 uses the
+// counter (j, k, iter, session) with key (seed low, seed high).
+// -----------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = mulhi32(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = mulhi32(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Uniform in (0, 1): the top 24 bits forced odd, times 2^-24 (exact in binary32).
+__device__ __forceinline__ float uniform24(uint32_t w) {
+    return (float)((w >> 8) | 1u) * 0x1p-24f;
+}
+
+// Box-Muller in binary32: sqrt(-2 ln u0) * (cos, sin)(2 pi u1).
+__device__ __forceinline__ float2 box_muller(float u0, float u1) {
+    const float r = sqrtf(-2.0f * logf(u0));
+    float s, c;
+    sincospif(2.0f * u1, &s, &c);
+    return make_float2(r * c, r * s);
+}
+
+// -----------------------------------------------------------------------------
+// Noise storage: [T][K] of (z_a, z_delta), binary32 pairs or bfloat16 pairs.
+// -----------------------------------------------------------------------------
+template <bool BF16> struct NoiseT;
+template <> struct NoiseT<false> {
+    using type = float2;
+    __device__ __forceinline__ static float2 load(const type* p) { return __ldg(p); }
+    __device__ __forceinline__ static type pack(float2 z) { return z; }
+};
+template <> struct NoiseT<true> {
+    using type = __nv_bfloat162;
+    __device__ __forceinline__ static float2 load(const type* p) {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+    }
+    __device__ __forceinline__ static type pack(float2 z) { return __floats2bfloat162_rn(z.x, z.y); }
+};
+
+// -----------------------------------------------------------------------------
+// Control perturbation with the noise check of Sec. III-A: v = clamp(u + sigma z)
+// and eps' = v - u.  Written with explicit rounding so the rollout and the update
+// kernels produce the same bits.
+// -----------------------------------------------------------------------------
+struct Perturbed {
+    float va, vd;    // applied controls
+    float ea, ed;    // eps' = applied - nominal
+};
+
+__device__ __forceinline__ Perturbed perturb(float ua, float ud, float2 z, float sa, float sd,
+                                             float amin, float amax, float dmin, float dmax) {
+    Perturbed p;
+    p.va = fminf(fmaxf(__fmaf_rn(sa, z.x, ua), amin), amax);
+    p.vd = fminf(fmaxf(__fmaf_rn(sd, z.y, ud), dmin), dmax);
+    p.ea = __fsub_rn(p.va, ua);
+    p.ed = __fsub_rn(p.vd, ud);
+    return p;
+}
+
+// yaw error wrapped into [-pi, pi]: d - 2 pi rint(d / 2 pi)
+__device__ __forceinline__ float wrap_pi(float d) {
+    const float k = rintf(d * 0.15915494309189535f);
+    return fmaf(-6.283185307179586f, k, d);
+}
+
+// Squared distance from p to segment (a, b = next vertex), the closest point being an
+// endpoint exactly when the projection parameter leaves (0, 1).  seg = (ex, ey, 1/|e|^2, heading).
+__device__ __forceinline__ float seg_dist2(float px, float py, float2 a, float2 b, float4 seg) {
+    const float dax = px - a.x, day = py - a.y;
+    const float tau = fmaf(dax, seg.x, day * seg.y) * seg.z;
+    float qx, qy;
+    if (tau <= 0.0f) {
+        qx = a.x; qy = a.y;
+    } else if (tau >= 1.0f) {
+        qx = b.x; qy = b.y;
+    } else {
+        qx = fmaf(tau, seg.x, a.x);
+        qy = fmaf(tau, seg.y, a.y);
+    }
+    const float dx = px - qx, dy = py - qy;
+    return fmaf(dx, dx, dy * dy);
+}
+
+// Squared distance from p to an axis-aligned box (minx, miny, maxx, maxy).
+__device__ __forceinline__ float box_dist2(float px, float py, float4 bb) {
+    const float dx = fmaxf(fmaxf(bb.x - px, px - bb.z), 0.0f);
+    const float dy = fmaxf(fmaxf(bb.y - py, py - bb.w), 0.0f);
+    return fmaf(dx, dx, dy * dy);
+}
+
+}  // namespace mppi

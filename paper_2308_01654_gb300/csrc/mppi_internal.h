@@ -1,0 +1,107 @@
+// mppi_internal.h - types shared by the kernels and the C ABI implementation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mppi {
+
+// Per-context device record: iteration counter, status and the reduction results.
+struct __align__(16) DevState {
+    unsigned long long iter;     // next iteration index (low 32 bits enter the Philox counter)
+    int32_t flags;               // FLAG_* raised by kernels
+    int32_t status;              // mppi_status of the last iteration
+    double s_min;                // lowest sample cost
+    double eta;                  // sum of softmin weights
+    int32_t argmin;
+    int32_t n_finite;
+    unsigned int ticket;         // last-block-done counter of the argmin reduction
+    int32_t jb0;                 // reference segment closest to x0
+    unsigned long long jkey;     // packed (distance bits, index) for the jb0 search
+    float4 x0f;                  // (0, 0, yaw0, v0): x0 in the local frame
+    unsigned long long iter_used;  // iteration index of the last finished iteration
+};
+
+// Byte offsets of the arrays in the scene blob that the rollout kernel stages into
+// shared memory with one bulk copy.  Every offset is a multiple of 16.
+struct SceneLayout {
+    int T, n_ref, n_seg, n_l1, n_l2, n_circ;
+    int off_ctl;     // float4 [T]       (u_a, u_d, g_a, g_d): nominal controls and control-cost slopes
+    int off_c0;      // float  [T]       1/2 u^T R u
+    int off_vert;    // float2 [n_ref]   vertices, local frame
+    int off_seg;     // float4 [n_seg]   (ex, ey, 1/|e|^2, heading)
+    int off_l1;      // float4 [n_l1]    level-1 chunk boxes
+    int off_l2;      // float4 [n_l2]    level-2 group boxes
+    int off_circ;    // float4 [n_circ]  (x, y, r, (d_safe_0 + r + r_ego)^2 when d_safe is constant)
+    int off_vel;     // float2 [n_circ]  velocities
+    int bytes;       // total, a multiple of 16
+};
+
+// Per-plan constants in the precision the kernels use.
+struct PlanConst {
+    int K, T;
+    float dt, dt_over_L;
+    float sig_a, sig_d, amin, amax, dmin, dmax;
+    float w_dist, w_target, w_yaw, w_speed, w_safe, w_terminal;
+    float v_ref, v_max;
+    int vcap;
+    float d_safe_c, d_safe_0;
+    int collision_only;
+    int n_ego;
+    int ego_same_radius;     // all ego radii equal: the band limit is per circle
+    float ego_off[8], ego_rad[8];
+    int ref_mode;
+    int has_table;           // per-step centre table given
+    uint32_t key0, key1, session;
+    // double-precision parameters of the update and the optimal rollout
+    double lam, dt_d, wheelbase_d, amin_d, amax_d, dmin_d, dmax_d, v_max_d;
+    double g_a, g_d;         // (1 + alpha) R_a, (1 + alpha) R_d
+    double half_Ra, half_Rd; // R / 2
+    int sg_enable, shift;
+};
+
+SceneLayout make_layout(int T, int n_ref, int n_circ);
+
+struct PlanBuffers {
+    DevState* state;
+    unsigned char* scene;    // SceneLayout::bytes
+    float2* table;           // [T][n_circ] centres, local frame (when given)
+    void* z;                 // [T][K] float2 or bf16x2
+    double* S;               // [K]
+    float* w;                // [K] softmin weights
+    double* eta_part;        // [n_wblk]
+    double* min_part;        // [n_mblk] (value)
+    int* min_idx_part;       // [n_mblk]
+    int* min_cnt_part;       // [n_mblk]
+    double* du_part;         // [n_kt][T][2]
+    double* U;               // [T][2] nominal controls (the warm start)
+    int n_mblk, n_wblk, n_kt, n_tt, kt_size;
+};
+
+struct PlanInputs {
+    const double* x0;        // [4]
+    const double* ref;       // [n_ref][2]
+    const double* circ;      // [n_circ][5]
+    const double* centres;   // [T][n_circ][2] or null
+    int n_ref, n_circ;
+    double* u_out;           // [T][2]
+    double* x_out;           // [T+1][4]
+};
+
+// Launch the whole iteration (prep, noise, rollout, reductions, update) on a stream.
+// ev: optional array of N_KERNELS + 1 events recorded around the kernels (per-kernel timing).
+constexpr int N_KERNELS = 7;   // prep, noise, rollout, argmin, weights, wsum, finalize
+cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
+                             const PlanInputs& in, int group, int noise_bf16, cudaStream_t st,
+                             cudaEvent_t* ev = nullptr);
+
+// Raw Philox words for n counters (device buffers).
+cudaError_t launch_philox(uint2 key, const uint4* ctr, uint4* out, int n, cudaStream_t st);
+
+// Rollout kernel only (for timing and tuning); requires prep and noise of the same plan.
+cudaError_t launch_rollout(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int group,
+                           int noise_bf16, cudaStream_t st);
+
+size_t rollout_smem_bytes(const SceneLayout& L);
+
+}  // namespace mppi

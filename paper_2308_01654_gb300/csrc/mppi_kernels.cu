@@ -1,0 +1,843 @@
+// mppi_kernels.cu - the CUDA kernels of one MPPI iteration (arXiv 2308.01654, Algorithm 1), sm_103a.
+//
+//   prep      reference polyline, obstacle circles and controls -> scene blob (local frame, binary32)
+//   noise     Philox4x32-10 + Box-Muller -> z[T][K]                    (Algorithm 1 GenerateRandomNoise)
+//   rollout   fused Euler rollout of Eq. (5) + step costs of Eq. (12)-(18) -> S[K]
+//   argmin    S_min and its index, last-block reduction                (Algorithm 1, S_min)
+//   weights   w_k = exp(-(S_k - S_min) / lambda), eta partials in binary64  (Eq. (11))
+//   wsum      sum_k w_k eps'_{t,k} per step, eps' recomputed from z      (Eq. (11))
+//   finalize  u + du, clamp, Savitzky-Golay (Eq. (19)), clamp, x* by prefix scans, warm start
+#include <math.h>
+
+#include "mppi_device.cuh"
+#include "mppi_internal.h"
+
+namespace mppi {
+
+static inline int align16(int x) { return (x + 15) & ~15; }
+
+SceneLayout make_layout(int T, int n_ref, int n_circ) {
+    SceneLayout L;
+    L.T = T;
+    L.n_ref = n_ref;
+    L.n_seg = n_ref - 1;
+    L.n_l1 = (L.n_seg + REF_L1 - 1) / REF_L1;
+    L.n_l2 = (L.n_l1 + REF_L2 - 1) / REF_L2;
+    L.n_circ = n_circ;
+    int o = 0;
+    L.off_ctl = o;  o = align16(o + 16 * T);
+    L.off_c0 = o;   o = align16(o + 4 * T);
+    L.off_vert = o; o = align16(o + 8 * n_ref);
+    L.off_seg = o;  o = align16(o + 16 * L.n_seg);
+    L.off_l1 = o;   o = align16(o + 16 * L.n_l1);
+    L.off_l2 = o;   o = align16(o + 16 * L.n_l2);
+    L.off_circ = o; o = align16(o + 16 * n_circ);
+    L.off_vel = o;  o = align16(o + 8 * n_circ);
+    L.bytes = o;
+    return L;
+}
+
+size_t rollout_smem_bytes(const SceneLayout& L) { return (size_t)L.bytes; }
+
+// -----------------------------------------------------------------------------
+// prep: one pass over the inputs.  Positions are shifted into a frame centred on
+// (x0, y0) in binary64 before rounding, so binary32 keeps its resolution where
+// the rollouts happen.
+// -----------------------------------------------------------------------------
+__device__ __forceinline__ float2 local_vertex(const double* ref, int i, double ox, double oy) {
+    return make_float2((float)(ref[2 * i] - ox), (float)(ref[2 * i + 1] - oy));
+}
+
+__device__ __forceinline__ float4 seg_record(const double* ref, int i, double ox, double oy) {
+    const float2 a = local_vertex(ref, i, ox, oy), b = local_vertex(ref, i + 1, ox, oy);
+    const float ex = b.x - a.x, ey = b.y - a.y;
+    const float l2 = fmaf(ex, ex, ey * ey);
+    const float inv = l2 > 0.0f ? 1.0f / l2 : 0.0f;
+    const double hx = ref[2 * i + 2] - ref[2 * i], hy = ref[2 * i + 3] - ref[2 * i + 1];
+    return make_float4(ex, ey, inv, (float)atan2(hy, hx));
+}
+
+__device__ __forceinline__ float4 vertex_box(const double* ref, int v0, int v1, double ox, double oy) {
+    float4 bb = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
+    for (int j = v0; j <= v1; ++j) {
+        const float2 p = local_vertex(ref, j, ox, oy);
+        bb.x = fminf(bb.x, p.x); bb.y = fminf(bb.y, p.y);
+        bb.z = fmaxf(bb.z, p.x); bb.w = fmaxf(bb.w, p.y);
+    }
+    return bb;
+}
+
+__global__ void __launch_bounds__(256) prep_kernel(PlanConst pc, SceneLayout L, PlanInputs in, PlanBuffers b) {
+    const double ox = in.x0[0], oy = in.x0[1];
+    unsigned char* sc = b.scene;
+    float4* ctl = reinterpret_cast<float4*>(sc + L.off_ctl);
+    float* c0 = reinterpret_cast<float*>(sc + L.off_c0);
+    float2* vert = reinterpret_cast<float2*>(sc + L.off_vert);
+    float4* seg = reinterpret_cast<float4*>(sc + L.off_seg);
+    float4* l1 = reinterpret_cast<float4*>(sc + L.off_l1);
+    float4* l2 = reinterpret_cast<float4*>(sc + L.off_l2);
+    float4* circ = reinterpret_cast<float4*>(sc + L.off_circ);
+    float2* vel = reinterpret_cast<float2*>(sc + L.off_vel);
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nth = gridDim.x * blockDim.x;
+    bool bad = false;
+
+    if (tid == 0) {
+        for (int i = 0; i < 4; ++i) bad |= !isfinite(in.x0[i]);
+        b.state->x0f = make_float4(0.0f, 0.0f, (float)in.x0[2], (float)in.x0[3]);
+    }
+    for (int t = tid; t < L.T; t += nth) {
+        const double ua = b.U[2 * t], ud = b.U[2 * t + 1];
+        ctl[t] = make_float4((float)ua, (float)ud, (float)(pc.g_a * ua), (float)(pc.g_d * ud));
+        c0[t] = (float)(pc.half_Ra * ua * ua + pc.half_Rd * ud * ud);
+    }
+    for (int i = tid; i < L.n_ref; i += nth) {
+        bad |= !isfinite(in.ref[2 * i]) || !isfinite(in.ref[2 * i + 1]);
+        vert[i] = local_vertex(in.ref, i, ox, oy);
+    }
+    for (int i = tid; i < L.n_seg; i += nth) {
+        const float4 s = seg_record(in.ref, i, ox, oy);
+        seg[i] = s;
+        // closest segment (or vertex) to x0 itself: the rollouts' first warm start
+        const float2 a = local_vertex(in.ref, i, ox, oy), bv = local_vertex(in.ref, i + 1, ox, oy);
+        const float d2 = pc.ref_mode == 0 ? seg_dist2(0.0f, 0.0f, a, bv, s) : fmaf(a.x, a.x, a.y * a.y);
+        const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)i;
+        atomicMin(&b.state->jkey, key);
+    }
+    for (int c = tid; c < L.n_l1; c += nth) {
+        const int v0 = c * REF_L1, v1 = min(v0 + REF_L1, L.n_seg);
+        l1[c] = vertex_box(in.ref, v0, v1, ox, oy);
+    }
+    for (int g = tid; g < L.n_l2; g += nth) {
+        const int v0 = g * REF_L1 * REF_L2, v1 = min(v0 + REF_L1 * REF_L2, L.n_seg);
+        l2[g] = vertex_box(in.ref, v0, v1, ox, oy);
+    }
+    for (int k = tid; k < L.n_circ; k += nth) {
+        const double* c = in.circ + 5 * k;
+        for (int j = 0; j < 5; ++j) bad |= !isfinite(c[j]);
+        const float r = (float)c[2];
+        // band limit (m + r + r_ego)^2 for the constant-d_safe, equal-ego-radius case
+        const float m = pc.collision_only ? fmaxf(pc.d_safe_0, 0.0f) : pc.d_safe_0;
+        const float lim = m + r + pc.ego_rad[0];
+        circ[k] = make_float4((float)(c[0] - ox), (float)(c[1] - oy), r, lim > 0.0f ? lim * lim : -1.0f);
+        vel[k] = make_float2((float)c[3], (float)c[4]);
+    }
+    if (in.centres) {
+        for (int i = tid; i < L.T * L.n_circ; i += nth) {
+            const double cx = in.centres[2 * i], cy = in.centres[2 * i + 1];
+            bad |= !isfinite(cx) || !isfinite(cy);
+            b.table[i] = make_float2((float)(cx - ox), (float)(cy - oy));
+        }
+    }
+    if (bad) atomicOr(&b.state->flags, FLAG_NONFINITE_INPUT);
+}
+
+// -----------------------------------------------------------------------------
+// noise: one thread per (step pair j, sample k); coalesced stores along k.
+// -----------------------------------------------------------------------------
+template <bool BF16>
+__global__ void __launch_bounds__(256) noise_kernel(PlanConst pc, const DevState* st,
+                                                    typename NoiseT<BF16>::type* z) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (k >= pc.K) return;
+    const uint32_t it = (uint32_t)st->iter;
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)k, it, pc.session), make_uint2(pc.key0, pc.key1));
+    const size_t K = (size_t)pc.K;
+    z[(size_t)(2 * j) * K + k] = NoiseT<BF16>::pack(box_muller(uniform24(w.x), uniform24(w.y)));
+    if (2 * j + 1 < pc.T)
+        z[(size_t)(2 * j + 1) * K + k] = NoiseT<BF16>::pack(box_muller(uniform24(w.z), uniform24(w.w)));
+}
+
+__global__ void philox_kernel(uint2 key, const uint4* ctr, uint4* out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = philox4x32_10(ctr[i], key);
+}
+
+// -----------------------------------------------------------------------------
+// 1-D bulk (TMA) copy global -> shared, completion on an mbarrier, bounded wait.
+// -----------------------------------------------------------------------------
+__device__ __forceinline__ bool stage_to_smem(unsigned char* dst, const unsigned char* src, int bytes,
+                                              unsigned long long* bar, int* flags) {
+    const uint32_t bar_a = (uint32_t)__cvta_generic_to_shared(bar);
+    const uint32_t dst_a = (uint32_t)__cvta_generic_to_shared(dst);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(bytes) : "memory");
+        constexpr int CHUNK = 32768;
+        for (int off = 0; off < bytes; off += CHUNK) {
+            const int n = min(CHUNK, bytes - off);
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    dst_a + off),
+                "l"(src + off), "r"(n), "r"(bar_a)
+                : "memory");
+        }
+    }
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 22) && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar_a), "r"(0u)
+            : "memory");
+    }
+    if (!done) {
+        if (threadIdx.x == 0) atomicOr(flags, FLAG_TIMEOUT);
+        return false;
+    }
+    return true;
+}
+
+// -----------------------------------------------------------------------------
+// rollout + cost.  G lanes (a power of two <= 32) work on one sample: they run the
+// dynamics redundantly (identical bits) and split the reference search and the
+// obstacle pairs, combining with shuffles inside the group.
+// -----------------------------------------------------------------------------
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    if constexpr (G == 32) {
+        return 0xffffffffu;
+    } else {
+        const unsigned lane = threadIdx.x & 31u;
+        return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void group_argmin(float& d2, int& idx, unsigned mask) {
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) {
+        const float od = __shfl_xor_sync(mask, d2, o, G);
+        const int oi = __shfl_xor_sync(mask, idx, o, G);
+        if (od < d2 || (od == d2 && oi < idx)) {
+            d2 = od;
+            idx = oi;
+        }
+    }
+}
+
+template <int G>
+__device__ __forceinline__ float group_min(float v, unsigned mask) {
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) v = fminf(v, __shfl_xor_sync(mask, v, o, G));
+    return v;
+}
+
+// Exact closest point of the polyline (ties -> lowest segment) with a two-level box
+// hierarchy; a box is skipped only when its lower bound exceeds the best distance
+// so far (with a relative slack far above binary32 rounding), so the result equals
+// a brute-force scan in the same arithmetic.
+template <int G>
+__device__ __forceinline__ void nearest_segment(float px, float py, const float2* vert, const float4* seg,
+                                                const float4* l1, const float4* l2, int n_seg, int n_l1,
+                                                int n_l2, int lane_g, unsigned mask, int& jb, float& best2) {
+    constexpr float SLACK = 1.0f + 1.0f / 1024.0f;
+    float b2 = seg_dist2(px, py, vert[jb], vert[jb + 1], seg[jb]);
+    int bi = jb;
+    for (int g = 0; g < n_l2; ++g) {
+        if (box_dist2(px, py, l2[g]) > b2 * SLACK) continue;
+        const int c1 = min((g + 1) * REF_L2, n_l1);
+        for (int c = g * REF_L2; c < c1; ++c) {
+            if (box_dist2(px, py, l1[c]) > b2 * SLACK) continue;
+            const int i1 = min((c + 1) * REF_L1, n_seg);
+            for (int i = c * REF_L1 + lane_g; i < i1; i += G) {
+                const float d2 = seg_dist2(px, py, vert[i], vert[i + 1], seg[i]);
+                if (d2 < b2 || (d2 == b2 && i < bi)) {
+                    b2 = d2;
+                    bi = i;
+                }
+            }
+            group_argmin<G>(b2, bi, mask);
+        }
+    }
+    jb = bi;
+    best2 = b2;
+}
+
+// Closest vertex (ties -> lowest index), same hierarchy (chunk c covers vertices c*L1 .. c*L1+L1).
+template <int G>
+__device__ __forceinline__ void nearest_vertex(float px, float py, const float2* vert, const float4* l1,
+                                               const float4* l2, int n_ref, int n_l1, int n_l2, int lane_g,
+                                               unsigned mask, int& jb, float& best2) {
+    constexpr float SLACK = 1.0f + 1.0f / 1024.0f;
+    float dx = px - vert[jb].x, dy = py - vert[jb].y;
+    float b2 = fmaf(dx, dx, dy * dy);
+    int bi = jb;
+    for (int g = 0; g < n_l2; ++g) {
+        if (box_dist2(px, py, l2[g]) > b2 * SLACK) continue;
+        const int c1 = min((g + 1) * REF_L2, n_l1);
+        for (int c = g * REF_L2; c < c1; ++c) {
+            if (box_dist2(px, py, l1[c]) > b2 * SLACK) continue;
+            const int i1 = min((c + 1) * REF_L1 + 1, n_ref);
+            for (int i = c * REF_L1 + lane_g; i < i1; i += G) {
+                const float ex = px - vert[i].x, ey = py - vert[i].y;
+                const float d2 = fmaf(ex, ex, ey * ey);
+                if (d2 < b2 || (d2 == b2 && i < bi)) {
+                    b2 = d2;
+                    bi = i;
+                }
+            }
+            group_argmin<G>(b2, bi, mask);
+        }
+    }
+    jb = bi;
+    best2 = b2;
+}
+
+template <int G, bool BF16>
+__global__ void __launch_bounds__(256) rollout_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
+                                                      const typename NoiseT<BF16>::type* __restrict__ z) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ unsigned long long bar;
+    if (!stage_to_smem(smem, b.scene, L.bytes, &bar, &b.state->flags)) return;
+
+    const float4* ctl = reinterpret_cast<const float4*>(smem + L.off_ctl);
+    const float* c0 = reinterpret_cast<const float*>(smem + L.off_c0);
+    const float2* vert = reinterpret_cast<const float2*>(smem + L.off_vert);
+    const float4* seg = reinterpret_cast<const float4*>(smem + L.off_seg);
+    const float4* l1 = reinterpret_cast<const float4*>(smem + L.off_l1);
+    const float4* l2 = reinterpret_cast<const float4*>(smem + L.off_l2);
+    const float4* circ = reinterpret_cast<const float4*>(smem + L.off_circ);
+    const float2* vel = reinterpret_cast<const float2*>(smem + L.off_vel);
+
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = gtid / G;
+    const int lane_g = threadIdx.x & (G - 1);
+    const unsigned mask = group_mask<G>();
+    const int K = pc.K, T = pc.T;
+    const int kk = min(k, K - 1);               // whole groups past K run along (shuffle safety)
+    const float4 x0 = b.state->x0f;
+    const float2 tp = vert[L.n_ref - 1];        // target point T_P: last vertex
+    const bool dconst = pc.d_safe_c == 0.0f && pc.ego_same_radius;
+    const float m_off = pc.collision_only ? 1.0f : 0.0f;
+
+    float px = x0.x, py = x0.y, th = x0.z, v = x0.w;
+    float sth, cth;
+    sincosf(th, &sth, &cth);
+    int jb = (int)(b.state->jkey & 0xffffffffu);
+    float s_hi = 0.0f, s_c = 0.0f, q_last = 0.0f;
+
+    for (int t = 0; t < T; ++t) {
+        const float4 ct = ctl[t];
+        const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
+        const Perturbed pe = perturb(ct.x, ct.y, zz, pc.sig_a, pc.sig_d, pc.amin, pc.amax, pc.dmin, pc.dmax);
+        float acc = pe.va;
+        if (pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - v) / pc.dt), pc.amin);
+        // Eq. (5), explicit Euler from x_t
+        const float tn = tanf(pe.vd);
+        const float nx = fmaf(v * cth, pc.dt, px);
+        const float ny = fmaf(v * sth, pc.dt, py);
+        const float nth = fmaf(v * tn, pc.dt_over_L, th);
+        const float nv = fmaf(acc, pc.dt, v);
+        float snth, cnth;
+        sincosf(nth, &snth, &cnth);
+
+        // Eq. (12), (14): closest waypoint and reference yaw
+        float d2r;
+        if (pc.ref_mode == 0)
+            nearest_segment<G>(nx, ny, vert, seg, l1, l2, L.n_seg, L.n_l1, L.n_l2, lane_g, mask, jb, d2r);
+        else
+            nearest_vertex<G>(nx, ny, vert, l1, l2, L.n_ref, L.n_l1, L.n_l2, lane_g, mask, jb, d2r);
+        const float thr = seg[min(jb, L.n_seg - 1)].w;
+        // Eq. (13): progress towards the target point
+        const float tnx = nx - tp.x, tny = ny - tp.y, tpx = px - tp.x, tpy = py - tp.y;
+        const float c_target = fmaf(tnx, tnx, tny * tny) > fmaf(tpx, tpx, tpy * tpy) ? 1.0f : 0.0f;
+        const float dyaw = wrap_pi(nth - thr);
+        const float dv = nv - pc.v_ref;
+
+        // Eq. (16)-(17): ego circles against obstacle circles
+        const float ds = fmaf(pc.d_safe_c, nv, pc.d_safe_0);
+        const float mband = m_off != 0.0f ? fmaxf(ds, 0.0f) : ds;
+        float ex[8], ey[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            ex[e] = fmaf(pc.ego_off[e], cnth, nx);
+            ey[e] = fmaf(pc.ego_off[e], snth, ny);
+        }
+        const float st = (float)(t + 1) * pc.dt;
+        float dobj = INFINITY;
+        for (int kc = lane_g; kc < L.n_circ; kc += G) {
+            const float4 c = circ[kc];
+            float cx, cy;
+            if (pc.has_table) {
+                const float2 q = b.table[(size_t)t * L.n_circ + kc];
+                cx = q.x;
+                cy = q.y;
+            } else {
+                const float2 vv = vel[kc];
+                cx = fmaf(vv.x, st, c.x);
+                cy = fmaf(vv.y, st, c.y);
+            }
+            if (dconst) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    if (e < pc.n_ego) {
+                        const float dx = ex[e] - cx, dy = ey[e] - cy;
+                        const float d2 = fmaf(dx, dx, dy * dy);
+                        if (d2 <= c.w) dobj = fminf(dobj, sqrtf(d2) - (c.z + pc.ego_rad[e]));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    if (e < pc.n_ego) {
+                        const float R = c.z + pc.ego_rad[e];
+                        const float lim = mband + R;
+                        const float dx = ex[e] - cx, dy = ey[e] - cy;
+                        const float d2 = fmaf(dx, dx, dy * dy);
+                        if (lim > 0.0f && d2 <= lim * lim) dobj = fminf(dobj, sqrtf(d2) - R);
+                    }
+                }
+            }
+        }
+        dobj = group_min<G>(dobj, mask);
+        const float gap = ds - dobj;
+        float c_safe = gap > 0.0f ? gap * gap : 0.0f;
+        if (pc.collision_only && !(dobj <= 0.0f)) c_safe = 0.0f;
+
+        // Eq. (18) weighted state cost, Eq. (8) control cost
+        const float qx = fmaf(pc.w_dist, d2r,
+                              fmaf(pc.w_target, c_target,
+                                   fmaf(pc.w_yaw, dyaw * dyaw, fmaf(pc.w_speed, dv * dv, pc.w_safe * c_safe))));
+        const float qu = fmaf(ct.z, pe.ea, fmaf(ct.w, pe.ed, c0[t]));
+        // compensated (Kahan) sum of the step costs, Eq. (6)
+        const float y = (qx + qu) - s_c;
+        const float tsum = s_hi + y;
+        s_c = (tsum - s_hi) - y;
+        s_hi = tsum;
+        q_last = qx;
+        px = nx; py = ny; th = nth; v = nv; sth = snth; cth = cnth;
+    }
+    if (lane_g == 0 && k < K) {
+        double S = (double)s_hi - (double)s_c;
+        if (pc.w_terminal != 0.0f) S += (double)pc.w_terminal * (double)q_last;
+        b.S[k] = S;
+    }
+}
+
+// -----------------------------------------------------------------------------
+// argmin over S with ties to the lowest index; non-finite costs are skipped.
+// -----------------------------------------------------------------------------
+struct MinRec {
+    double v;
+    int i;
+    int n;
+};
+
+__device__ __forceinline__ MinRec min_combine(MinRec a, MinRec b) {
+    MinRec r;
+    r.n = a.n + b.n;
+    if (b.v < a.v || (b.v == a.v && b.i < a.i)) {
+        r.v = b.v;
+        r.i = b.i;
+    } else {
+        r.v = a.v;
+        r.i = a.i;
+    }
+    return r;
+}
+
+__device__ __forceinline__ MinRec warp_min(MinRec a) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        MinRec b;
+        b.v = __shfl_xor_sync(0xffffffffu, a.v, o);
+        b.i = __shfl_xor_sync(0xffffffffu, a.i, o);
+        b.n = __shfl_xor_sync(0xffffffffu, a.n, o);
+        a = min_combine(a, b);
+    }
+    return a;
+}
+
+__device__ MinRec block_min(MinRec a) {
+    __shared__ double sv[32];
+    __shared__ int si[32], sn[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    a = warp_min(a);
+    if (lane == 0) {
+        sv[w] = a.v;
+        si[w] = a.i;
+        sn[w] = a.n;
+    }
+    __syncthreads();
+    if (w == 0) {
+        MinRec r{INFINITY, 0x7fffffff, 0};
+        if (lane < nw) r = MinRec{sv[lane], si[lane], sn[lane]};
+        a = warp_min(r);
+    }
+    __syncthreads();
+    return a;
+}
+
+__global__ void __launch_bounds__(256) argmin_kernel(int K, PlanBuffers b) {
+    MinRec r{INFINITY, 0x7fffffff, 0};
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+        const double s = b.S[k];
+        if (isfinite(s)) {
+            r.n += 1;
+            if (s < r.v) {
+                r.v = s;
+                r.i = k;
+            }
+        }
+    }
+    r = block_min(r);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        b.min_part[blockIdx.x] = r.v;
+        b.min_idx_part[blockIdx.x] = r.i;
+        b.min_cnt_part[blockIdx.x] = r.n;
+        __threadfence();
+        last = atomicAdd(&b.state->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    MinRec q{INFINITY, 0x7fffffff, 0};
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        const MinRec p{((volatile double*)b.min_part)[i], ((volatile int*)b.min_idx_part)[i],
+                       ((volatile int*)b.min_cnt_part)[i]};
+        q = min_combine(q, p);
+    }
+    q = block_min(q);
+    if (threadIdx.x == 0) {
+        b.state->s_min = q.v;
+        b.state->argmin = q.n > 0 ? q.i : -1;
+        b.state->n_finite = q.n;
+        b.state->ticket = 0u;
+    }
+}
+
+// -----------------------------------------------------------------------------
+// softmin weights in binary64 (Eq. (11)); eta partial sums per block.
+// -----------------------------------------------------------------------------
+__device__ double block_sum_d(double v) {
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    return v;
+}
+
+__global__ void __launch_bounds__(256) weights_kernel(int K, double lam, PlanBuffers b) {
+    const double smin = b.state->s_min;
+    double acc = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+        const double s = b.S[k];
+        const double w = isfinite(s) ? exp((smin - s) / lam) : 0.0;
+        b.w[k] = (float)w;
+        acc += w;
+    }
+    acc = block_sum_d(acc);
+    if (threadIdx.x == 0) b.eta_part[blockIdx.x] = acc;
+}
+
+// -----------------------------------------------------------------------------
+// wsum: per step t, sum_k w_k eps'_{t,k}.  Each thread owns J samples of a k-tile,
+// recomputes eps' from z exactly as the rollout did, accumulates in binary32 over
+// its J samples and its warp (32 x J products), and the per-warp partials are
+// added in binary64.
+// -----------------------------------------------------------------------------
+constexpr int WS_J = 8;
+constexpr int WS_TT = 32;
+
+template <bool BF16>
+__global__ void __launch_bounds__(256) wsum_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
+                                                   const typename NoiseT<BF16>::type* __restrict__ z) {
+    __shared__ float red[8][WS_TT][2];
+    const int K = pc.K, T = pc.T;
+    const int kt = blockIdx.x;
+    const int t0 = blockIdx.y * WS_TT, t1 = min(T, t0 + WS_TT);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float4* ctl = reinterpret_cast<const float4*>(b.scene + L.off_ctl);
+    float wj[WS_J];
+    int kj[WS_J];
+#pragma unroll
+    for (int j = 0; j < WS_J; ++j) {
+        kj[j] = kt * b.kt_size + j * blockDim.x + threadIdx.x;
+        wj[j] = kj[j] < K ? b.w[kj[j]] : 0.0f;
+    }
+    for (int t = t0; t < t1; ++t) {
+        const float4 ct = ctl[t];
+        float aa = 0.0f, ad = 0.0f;
+#pragma unroll
+        for (int j = 0; j < WS_J; ++j) {
+            if (kj[j] < K) {
+                const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kj[j]);
+                const Perturbed pe =
+                    perturb(ct.x, ct.y, zz, pc.sig_a, pc.sig_d, pc.amin, pc.amax, pc.dmin, pc.dmax);
+                aa = fmaf(wj[j], pe.ea, aa);
+                ad = fmaf(wj[j], pe.ed, ad);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            aa += __shfl_xor_sync(0xffffffffu, aa, o);
+            ad += __shfl_xor_sync(0xffffffffu, ad, o);
+        }
+        if (lane == 0) {
+            red[warp][t - t0][0] = aa;
+            red[warp][t - t0][1] = ad;
+        }
+    }
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < (t1 - t0) * 2; i += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += (double)red[w][i >> 1][i & 1];
+        b.du_part[((size_t)kt * T + t0 + (i >> 1)) * 2 + (i & 1)] = s;
+    }
+}
+
+// -----------------------------------------------------------------------------
+// finalize: u <- clamp(u + du), u* = clamp(SG(u)), x* = F-rollout of u*, warm start.
+// One block, one thread per step (T <= 1024).  x* is a chain of prefix sums:
+// v_t from sum a dt, yaw from sum v tan(delta)/L dt, x and y from sum v (cos, sin) dt.
+// -----------------------------------------------------------------------------
+__device__ double block_scan_incl(double v, double* sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    if (lane == 31) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        double s = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double n = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += n;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    if (w > 0) v += sh[w - 1];
+    __syncthreads();
+    return v;
+}
+
+__device__ __forceinline__ double clampd(double x, double lo, double hi) { return fmin(fmax(x, lo), hi); }
+
+__global__ void __launch_bounds__(1024) finalize_kernel(PlanConst pc, PlanBuffers b, PlanInputs in) {
+    __shared__ double s_un[2 * 1024];
+    __shared__ double s_us[2 * 1024];
+    __shared__ double s_scan[32];
+    __shared__ double s_eta;
+    __shared__ int s_status;
+    DevState* st = b.state;
+    const int T = pc.T;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        const int flags = st->flags;
+        int status = 0;
+        if (flags & FLAG_NONFINITE_INPUT) status = -1;
+        else if (flags & FLAG_TIMEOUT) status = -5;
+        else if (st->n_finite == 0) status = -4;
+        s_status = status;
+        double e = 0.0;
+        for (int i = 0; i < b.n_wblk; ++i) e += b.eta_part[i];
+        s_eta = e;
+    }
+    __syncthreads();
+    if (s_status != 0) {
+        if (t == 0) {
+            st->status = s_status;
+            st->flags = 0;
+            st->jkey = ~0ull;
+        }
+        return;
+    }
+    const double eta = s_eta;
+    for (int i = t; i < 2 * T; i += blockDim.x) {
+        double num = 0.0;
+        for (int kt = 0; kt < b.n_kt; ++kt) num += b.du_part[(size_t)kt * 2 * T + i];
+        const bool ch = i & 1;
+        s_un[i] = clampd(b.U[i] + num / eta, ch ? pc.dmin_d : pc.amin_d, ch ? pc.dmax_d : pc.amax_d);
+    }
+    __syncthreads();
+    for (int i = t; i < 2 * T; i += blockDim.x) {
+        const int tt = i >> 1, ch = i & 1;
+        double val;
+        if (pc.sg_enable) {
+            const double cf[5] = {-3.0, 12.0, 17.0, 12.0, -3.0};
+            double acc = 0.0;
+#pragma unroll
+            for (int j = -2; j <= 2; ++j) {
+                const int s = min(max(tt + j, 0), T - 1);
+                acc += cf[j + 2] * s_un[2 * s + ch];
+            }
+            val = clampd(acc / 35.0, ch ? pc.dmin_d : pc.amin_d, ch ? pc.dmax_d : pc.amax_d);
+        } else {
+            val = s_un[i];
+        }
+        s_us[i] = val;
+        in.u_out[i] = val;
+    }
+    __syncthreads();
+
+    // x*: prefix sums in binary64 (sequential when the speed cap makes v nonlinear)
+    const double x0 = in.x0[0], y0 = in.x0[1], th0 = in.x0[2], v0 = in.x0[3];
+    if (t == 0) {
+        in.x_out[0] = x0; in.x_out[1] = y0; in.x_out[2] = th0; in.x_out[3] = v0;
+    }
+    const double dt = pc.dt_d;
+    if (pc.vcap) {
+        if (t == 0) {
+            double x = x0, y = y0, th = th0, v = v0;
+            for (int s = 0; s < T; ++s) {
+                double a = s_us[2 * s];
+                const double lim = (pc.v_max_d - v) / dt;
+                if (a > lim) a = lim;
+                if (a < pc.amin_d) a = pc.amin_d;
+                const double nx = x + v * cos(th) * dt, ny = y + v * sin(th) * dt;
+                const double nth = th + v * tan(s_us[2 * s + 1]) / pc.wheelbase_d * dt;
+                const double nv = v + a * dt;
+                x = nx; y = ny; th = nth; v = nv;
+                in.x_out[4 * (s + 1)] = x; in.x_out[4 * (s + 1) + 1] = y;
+                in.x_out[4 * (s + 1) + 2] = th; in.x_out[4 * (s + 1) + 3] = v;
+            }
+        }
+    } else {
+        const bool on = t < T;
+        const double a = on ? s_us[2 * t] : 0.0, dl = on ? s_us[2 * t + 1] : 0.0;
+        const double pv = block_scan_incl(on ? a * dt : 0.0, s_scan);          // v_{t+1} - v0
+        const double vt = v0 + (pv - (on ? a * dt : 0.0));                      // v_t
+        const double dth = on ? vt * tan(dl) / pc.wheelbase_d * dt : 0.0;
+        const double pth = block_scan_incl(dth, s_scan);                         // yaw_{t+1} - yaw0
+        const double tht = th0 + (pth - dth);                                    // yaw_t
+        const double dx = on ? vt * cos(tht) * dt : 0.0, dy = on ? vt * sin(tht) * dt : 0.0;
+        const double px = block_scan_incl(dx, s_scan);
+        const double py = block_scan_incl(dy, s_scan);
+        if (on) {
+            in.x_out[4 * (t + 1)] = x0 + px;
+            in.x_out[4 * (t + 1) + 1] = y0 + py;
+            in.x_out[4 * (t + 1) + 2] = th0 + pth;
+            in.x_out[4 * (t + 1) + 3] = v0 + pv;
+        }
+    }
+    // warm start for the next iteration (Algorithm 1, last loop)
+    for (int i = t; i < 2 * T; i += blockDim.x) {
+        const int tt = i >> 1, ch = i & 1;
+        const int src = pc.shift ? min(tt + 1, T - 1) : tt;
+        b.U[i] = s_us[2 * src + ch];
+    }
+    if (t == 0) {
+        st->status = 0;
+        st->eta = eta;
+        st->iter_used = st->iter;
+        st->iter += 1ull;
+        st->flags = 0;
+        st->jkey = ~0ull;
+    }
+}
+
+// -----------------------------------------------------------------------------
+// host-side launchers
+// -----------------------------------------------------------------------------
+template <int G, bool BF16>
+static cudaError_t launch_rollout_t(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
+                                    cudaStream_t st) {
+    const size_t smem = rollout_smem_bytes(L);
+    static int configured_smem = -1;
+    if (configured_smem < (int)smem) {
+        cudaError_t e = cudaFuncSetAttribute(rollout_kernel<G, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(smem < 48 * 1024 ? 48 * 1024 : smem));
+        if (e != cudaSuccess) return e;
+        configured_smem = (int)(smem < 48 * 1024 ? 48 * 1024 : smem);
+    }
+    const int threads = 256;
+    const long long total = (long long)pc.K * G;
+    const int blocks = (int)((total + threads - 1) / threads);
+    rollout_kernel<G, BF16><<<blocks, threads, smem, st>>>(
+        pc, L, b, reinterpret_cast<const typename NoiseT<BF16>::type*>(b.z));
+    return cudaGetLastError();
+}
+
+template <bool BF16>
+static cudaError_t launch_rollout_b(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int group,
+                                    cudaStream_t st) {
+    switch (group) {
+        case 1: return launch_rollout_t<1, BF16>(pc, L, b, st);
+        case 2: return launch_rollout_t<2, BF16>(pc, L, b, st);
+        case 4: return launch_rollout_t<4, BF16>(pc, L, b, st);
+        case 8: return launch_rollout_t<8, BF16>(pc, L, b, st);
+        case 16: return launch_rollout_t<16, BF16>(pc, L, b, st);
+        case 32: return launch_rollout_t<32, BF16>(pc, L, b, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_rollout(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int group,
+                           int noise_bf16, cudaStream_t st) {
+    return noise_bf16 ? launch_rollout_b<true>(pc, L, b, group, st) : launch_rollout_b<false>(pc, L, b, group, st);
+}
+
+cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
+                             const PlanInputs& in, int group, int noise_bf16, cudaStream_t st, cudaEvent_t* ev) {
+    cudaError_t e;
+    int stage = 0;
+    auto mark = [&]() -> cudaError_t {
+        if (!ev) return cudaGetLastError();
+        cudaError_t r = cudaGetLastError();
+        if (r != cudaSuccess) return r;
+        return cudaEventRecord(ev[stage++], st);
+    };
+    if (ev && (e = cudaEventRecord(ev[stage++], st)) != cudaSuccess) return e;
+    {
+        int items = L.n_ref;
+        items = max(items, L.T);
+        items = max(items, L.n_circ);
+        if (in.centres) items = max(items, L.T * L.n_circ);
+        const int blocks = min(max((items + 255) / 256, 1), 148);
+        prep_kernel<<<blocks, 256, 0, st>>>(pc, L, in, b);
+        if ((e = mark()) != cudaSuccess) return e;
+    }
+    {
+        dim3 grid((pc.K + 255) / 256, (pc.T + 1) / 2);
+        if (noise_bf16)
+            noise_kernel<true><<<grid, 256, 0, st>>>(pc, b.state, reinterpret_cast<__nv_bfloat162*>(b.z));
+        else
+            noise_kernel<false><<<grid, 256, 0, st>>>(pc, b.state, reinterpret_cast<float2*>(b.z));
+        if ((e = mark()) != cudaSuccess) return e;
+    }
+    if ((e = launch_rollout(pc, L, b, group, noise_bf16, st)) != cudaSuccess) return e;
+    if ((e = mark()) != cudaSuccess) return e;
+    argmin_kernel<<<b.n_mblk, 256, 0, st>>>(pc.K, b);
+    if ((e = mark()) != cudaSuccess) return e;
+    weights_kernel<<<b.n_wblk, 256, 0, st>>>(pc.K, pc.lam, b);
+    if ((e = mark()) != cudaSuccess) return e;
+    {
+        dim3 grid(b.n_kt, b.n_tt);
+        if (noise_bf16)
+            wsum_kernel<true><<<grid, 256, 0, st>>>(pc, L, b, reinterpret_cast<const __nv_bfloat162*>(b.z));
+        else
+            wsum_kernel<false><<<grid, 256, 0, st>>>(pc, L, b, reinterpret_cast<const float2*>(b.z));
+        if ((e = mark()) != cudaSuccess) return e;
+    }
+    finalize_kernel<<<1, ((pc.T + 31) / 32) * 32, 0, st>>>(pc, b, in);
+    return mark();
+}
+
+cudaError_t launch_philox(uint2 key, const uint4* ctr, uint4* out, int n, cudaStream_t st) {
+    philox_kernel<<<(n + 255) / 256, 256, 0, st>>>(key, ctr, out, n);
+    return cudaGetLastError();
+}
+
+}  // namespace mppi

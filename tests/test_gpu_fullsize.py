@@ -1,0 +1,39 @@
+"""Full-size parity on the roofline workload (K=65536, T=200, 2000-point lane, 192 circles).
+
+The CUDA path runs in the launch configuration the benchmark times; the oracle
+computes every one of the 65536 sample costs (brute-force reference search,
+binary64) on the host cores, so costs, argmin, u* and x* are compared in full.
+The BF16-noise form is compared with the oracle's bf16-rounded noise, and its
+error against the unrounded FP64 oracle is reported.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2308_01654_gb300 as mp
+from paper_2308_01654_gb300 import scenarios as sc
+from parity import U_ABS_TOL, X_ABS_TOL, argmin_ok, assert_costs
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_roofline_workload_full_parity(bf16):
+    prob = sc.roofline(bf16=bf16)
+    with mp.Planner(prob.params) as pl:
+        u, x, info = pl.plan(prob.x0, prob.ref, prob.circles)
+        S = pl.get_costs()
+    orc = oracle.plan(prob)
+    rep = assert_costs(S, orc.S, orc.margin)
+    assert argmin_ok(info["argmin"], orc.S)
+    if info["argmin"] == orc.info.argmin:
+        np.testing.assert_allclose(u, orc.u_star, rtol=0, atol=U_ABS_TOL)
+        np.testing.assert_allclose(x, orc.x_star, rtol=0, atol=X_ABS_TOL)
+    if bf16:
+        # the stated error of the BF16 form against the unrounded FP64 method
+        p64 = dict(prob.params, noise_bf16=0)
+        full = oracle.plan(prob, params=p64)
+        rel = np.abs(S - full.S) / np.maximum(np.abs(full.S), 1.0)
+        print(f"bf16 form vs fp64 oracle: max rel S err {rel.max():.3e}, median {np.median(rel):.3e}, "
+              f"|du*| {np.abs(u - full.u_star).max():.3e}, argmin {info['argmin']} vs {full.info.argmin}")
+    print("roofline", "bf16" if bf16 else "fp32", rep)

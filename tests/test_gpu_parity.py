@@ -1,0 +1,275 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (needs a GB300).
+
+Sizes: the oracle finishes each case in seconds; the cases span several tiles
+of every kernel and end in ragged tails (K not a multiple of the block or tile
+sizes, T not a multiple of the step tiles).  Full-size cases of the benchmark
+workload are in test_gpu_fullsize.py.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2308_01654_gb300 as mp
+from paper_2308_01654_gb300 import scenarios as sc
+from parity import U_ABS_TOL, X_ABS_TOL, argmin_ok, assert_costs
+
+pytestmark = pytest.mark.gpu
+
+
+def run_gpu(prob, U=None, iters=1, params=None):
+    p = params if params is not None else prob.params
+    with mp.Planner(p) as pl:
+        if U is not None:
+            pl.set_controls(U, 0)
+        outs = []
+        for _ in range(iters):
+            u, x, info = pl.plan(prob.x0, prob.ref, prob.circles, prob.centres)
+            outs.append((u, x, info, pl.get_costs()))
+        z = pl.get_noise()
+        Ud, it = pl.get_controls()
+    return outs, z, Ud, it
+
+
+def check_iteration(prob, gpu_out, orc, max_excused=0.02):
+    u, x, info, S = gpu_out
+    rep = assert_costs(S, orc.S, orc.margin, max_excused)
+    assert argmin_ok(info["argmin"], orc.S), (info["argmin"], orc.info.argmin)
+    assert info["n_finite"] == orc.info.n_finite
+    if info["argmin"] == orc.info.argmin:
+        np.testing.assert_allclose(u, orc.u_star, rtol=0, atol=U_ABS_TOL)
+        np.testing.assert_allclose(x, orc.x_star, rtol=0, atol=X_ABS_TOL)
+    return rep
+
+
+# ----------------------------------------------------------------------------- noise
+
+def test_philox_words_bit_exact():
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:4] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4], [7, 0, 0, 0xFFFFFFFF]]
+    for seed in (0, 0x0123456789ABCDEF, 0xFFFFFFFFFFFFFFFF):
+        got = mp.philox(seed, ctr)
+        key = (seed & 0xFFFFFFFF, seed >> 32)
+        exp = np.array([oracle.philox4x32_10(c, key) for c in ctr[:512]])
+        np.testing.assert_array_equal(got[:512], exp)
+
+
+@pytest.mark.parametrize("K,T", [(1000, 7), (2048, 16), (3, 1)])
+def test_noise_matches_oracle(K, T):
+    prob = sc.tiny(K=K, T=T)
+    prob.params.update(seed=0xABCDEF12345, session=3)
+    outs, z, _, _ = run_gpu(prob)
+    zo = oracle.noise(prob.params, outs[0][2]["iter"])
+    # binary32 Box-Muller (logf, sqrtf, sincospif) against binary64: a few ulps of |z|, plus
+    # an absolute floor for values near zero where cos / sin cancel
+    err = np.abs(z.astype(np.float64) - zo)
+    assert np.all(err <= 4e-7 * np.maximum(np.abs(zo), 1.0)), err.max()
+
+
+def test_bf16_noise_is_the_rounded_normal():
+    prob = sc.tiny(K=4096, T=8)
+    prob.params.update(noise_bf16=1)
+    outs, z, _, _ = run_gpu(prob)
+    zo = oracle.noise(prob.params, outs[0][2]["iter"])          # oracle rounds its fp64 normals to bf16
+    same = z.astype(np.float64) == zo
+    # a value whose fp32 and fp64 normals straddle a bf16 rounding midpoint rounds apart: rare
+    assert same.mean() > 0.999
+    diff = np.abs(z.astype(np.float64) - zo)[~same]
+    assert np.all(diff <= 2.0 ** -7 * np.maximum(np.abs(zo[~same]), 1e-30))
+
+
+# ----------------------------------------------------------------------------- one iteration
+
+@pytest.mark.parametrize("K,T,group", [(1024, 50, 0), (1000, 37, 1), (777, 33, 4), (257, 13, 32), (1, 5, 0)])
+def test_single_plan_parity(K, T, group):
+    prob = sc.single_plan()
+    prob.params.update(K=K, T=T, group=group)
+    outs, _, _, _ = run_gpu(prob)
+    orc = oracle.plan(prob)
+    check_iteration(prob, outs[0], orc)
+
+
+def test_ten_warm_started_iterations():
+    prob = sc.single_plan()                          # K=1024, T=50, 10 iterations, shift off
+    outs, _, Ud, it = run_gpu(prob, iters=10)
+    U = None
+    for i in range(10):
+        orc = oracle.plan(prob, U=U, iter_=i)
+        U = orc.U
+        assert outs[i][2]["iter"] == i
+        check_iteration(prob, outs[i], orc)
+    assert it == 10
+    np.testing.assert_allclose(Ud, U, rtol=0, atol=U_ABS_TOL)
+
+
+def test_closed_loop_cycles_with_shift():
+    prob = sc.closed_loop()
+    prob.params.update(K=2048, shift=1)
+    outs, _, _, _ = run_gpu(prob, iters=3)
+    U = None
+    for i in range(3):
+        orc = oracle.plan(prob, U=U, iter_=i)
+        U = orc.U
+        check_iteration(prob, outs[i], orc)
+
+
+def test_closed_loop_full_K():
+    prob = sc.closed_loop()                          # K=8192, T=100, 1000-point curved lane
+    outs, _, _, _ = run_gpu(prob)
+    orc = oracle.plan(prob)
+    rep = check_iteration(prob, outs[0], orc)
+    print("closed_loop", rep)
+
+
+def test_groups_give_identical_costs():
+    prob = sc.closed_loop()
+    prob.params.update(K=512, T=40)
+    S = {}
+    for g in (1, 2, 4, 8, 16, 32):
+        p = dict(prob.params, group=g)
+        outs, _, _, _ = run_gpu(prob, params=p)
+        S[g] = outs[0][3]
+    for g in (2, 4, 8, 16, 32):
+        np.testing.assert_array_equal(S[g], S[1])
+
+
+@pytest.mark.parametrize("variant", ["vertex", "collision_only", "vcap", "gamma", "terminal", "dsafe_v",
+                                     "radii", "sg_off", "moving_velocity", "moving_table", "no_obstacles",
+                                     "two_point_ref"])
+def test_variants(variant):
+    prob = sc.tiny(K=1500, T=25, n_ref=60, n_obs=3, moving=variant.startswith("moving"))
+    p = prob.params
+    p["d_safe_0"] = 2.0
+    if variant == "vertex":
+        p["ref_mode"] = 1
+    elif variant == "collision_only":
+        p.update(collision_only=1, ego_radius=[2.5, 2.5, 2.5])
+    elif variant == "vcap":
+        p["v_max"] = 4.5
+    elif variant == "gamma":
+        p["gamma"] = 3.0
+        prob_U = np.random.default_rng(1).normal(size=(prob.T, 2)) * [0.5, 0.05]
+    elif variant == "terminal":
+        p["w_terminal"] = 4.0
+    elif variant == "dsafe_v":
+        p.update(d_safe_c=0.4, d_safe_0=1.0)
+    elif variant == "radii":
+        p.update(ego_radius=[1.3, 0.9, 1.1])
+    elif variant == "sg_off":
+        p["sg_enable"] = 0
+    elif variant == "moving_table":
+        prob.centres = sc.predicted_centres(prob.circles, prob.T, p["dt"])
+    elif variant == "no_obstacles":
+        prob.circles = np.zeros((0, 5))
+    elif variant == "two_point_ref":
+        prob.ref = np.array([[-5.0, 0.0], [30.0, 1.0]])
+    U = prob_U if variant == "gamma" else np.random.default_rng(2).normal(size=(prob.T, 2)) * [0.3, 0.03]
+    outs, _, _, _ = run_gpu(prob, U=U)
+    orc = oracle.plan(prob, U=U)
+    check_iteration(prob, outs[0], orc)
+
+
+def test_device_entry_point_matches_host_entry_point():
+    torch = pytest.importorskip("torch")
+    prob = sc.single_plan()
+    prob.params.update(K=2000, T=30)
+    outs, _, _, _ = run_gpu(prob)
+    dev = torch.device("cuda:0")
+    with mp.Planner(prob.params, stream=torch.cuda.current_stream().cuda_stream) as pl:
+        x0 = torch.tensor(prob.x0, dtype=torch.float64, device=dev)
+        ref = torch.tensor(prob.ref, dtype=torch.float64, device=dev)
+        circ = torch.tensor(prob.circles, dtype=torch.float64, device=dev)
+        u = torch.empty((prob.T, 2), dtype=torch.float64, device=dev)
+        x = torch.empty((prob.T + 1, 4), dtype=torch.float64, device=dev)
+        info = pl.plan_device(x0, ref, circ, None, u, x, wait=True)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(u.cpu().numpy(), outs[0][0])
+        np.testing.assert_array_equal(x.cpu().numpy(), outs[0][1])
+        assert info["argmin"] == outs[0][2]["argmin"]
+
+
+# ----------------------------------------------------------------------------- errors and state
+
+def test_non_finite_input_is_rejected_and_state_kept():
+    prob = sc.single_plan()
+    prob.params.update(K=256, T=10)
+    with mp.Planner(prob.params) as pl:
+        U0 = np.full((10, 2), 0.01)
+        pl.set_controls(U0, 5)
+        bad = prob.ref.copy()
+        bad[3, 0] = np.nan
+        with pytest.raises(mp.MppiError) as e:
+            pl.plan(prob.x0, bad, prob.circles)
+        assert e.value.status == -1
+        U, it = pl.get_controls()
+        np.testing.assert_array_equal(U, U0)
+        assert it == 5
+
+
+def test_non_finite_device_input_is_a_no_op():
+    torch = pytest.importorskip("torch")
+    prob = sc.single_plan()
+    prob.params.update(K=256, T=10)
+    dev = torch.device("cuda:0")
+    with mp.Planner(prob.params) as pl:
+        x0 = torch.tensor(prob.x0, dtype=torch.float64, device=dev)
+        ref = torch.tensor(prob.ref, dtype=torch.float64, device=dev)
+        ref[5, 1] = float("inf")
+        circ = torch.tensor(prob.circles, dtype=torch.float64, device=dev)
+        u = torch.zeros((10, 2), dtype=torch.float64, device=dev)
+        x = torch.zeros((11, 4), dtype=torch.float64, device=dev)
+        with pytest.raises(mp.MppiError) as e:
+            pl.plan_device(x0, ref, circ, None, u, x, wait=True)
+        assert e.value.status == -1
+        U, it = pl.get_controls()
+        assert np.all(U == 0.0) and it == 0
+        # the context stays usable
+        u2, x2, info = pl.plan(prob.x0, prob.ref, prob.circles)
+        assert info["iter"] == 0
+
+
+def test_all_costs_non_finite_leaves_controls():
+    prob = sc.single_plan()
+    prob.params.update(K=128, T=8)
+    x0 = prob.x0.copy()
+    x0[3] = 1e30                                   # v^2 overflows binary32: every cost is +inf
+    with mp.Planner(prob.params) as pl:
+        U0 = np.full((8, 2), 0.02)
+        pl.set_controls(U0, 0)
+        with pytest.raises(mp.MppiError) as e:
+            pl.plan(x0, prob.ref, prob.circles)
+        assert e.value.status == -4
+        U, it = pl.get_controls()
+        np.testing.assert_array_equal(U, U0)
+        assert it == 0
+
+
+def test_capacity_is_enforced():
+    prob = sc.single_plan()
+    prob.params.update(K=64, T=8)
+    with mp.Planner(prob.params, max_ref=100, max_circ=2) as pl:
+        with pytest.raises(mp.MppiError) as e:
+            pl.plan(prob.x0, prob.ref, prob.circles)       # 200 vertices > 100
+        assert e.value.status == -6
+        with pytest.raises(mp.MppiError) as e:
+            pl.plan(prob.x0, prob.ref[:50], prob.circles)  # 3 circles > 2
+        assert e.value.status == -6
+        with pytest.raises(mp.MppiError) as e:
+            pl.plan(prob.x0, prob.ref[:1], prob.circles[:1])
+        assert e.value.status == -1
+
+
+def test_checkpoint_resume_reproduces_the_stream():
+    prob = sc.single_plan()
+    prob.params.update(K=512, T=20)
+    with mp.Planner(prob.params) as a:
+        a.plan(prob.x0, prob.ref, prob.circles)
+        U, it = a.get_controls()
+        u1, x1, i1 = a.plan(prob.x0, prob.ref, prob.circles)
+    with mp.Planner(prob.params) as b:
+        b.set_controls(U, it)
+        u2, x2, i2 = b.plan(prob.x0, prob.ref, prob.circles)
+    np.testing.assert_array_equal(u1, u2)
+    assert i1["iter"] == i2["iter"] == 1
