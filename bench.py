@@ -186,8 +186,10 @@ def run_gpu(args, world, rank, local):
     prob = scenarios.by_name(args.workload)
     prob.params["session"] = rank                      # an independent planning problem per rank
     K, T = prob.K, prob.T
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(device=dev)             # the planner and the timing events share it
+    torch.cuda.set_stream(stream)
     pl = mp.Planner(prob.params, device=local, stream=stream.cuda_stream)
+    group, block = pl.autotune(prob.x0, prob.ref, prob.circles, prob.centres, cache_path=args.tune_cache)
     pl.set_profiling(True)
     x0 = torch.tensor(prob.x0, dtype=torch.float64, device=dev)
     ref = torch.tensor(prob.ref, dtype=torch.float64, device=dev)
@@ -212,7 +214,7 @@ def run_gpu(args, world, rank, local):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
-    sampler = ClockSampler(gpu_id_for(local)) if not args.no_clocks else None
+    sampler = ClockSampler(gpu_id_for(local)) if not (args.no_clocks or args.quick) else None
     barrier()
     if sampler:
         sampler.start()
@@ -244,20 +246,23 @@ def run_gpu(args, world, rank, local):
     # end to end through the host-buffer C ABI: H2D of inputs and D2H of outputs every step
     h2d = 8 * (4 + prob.ref.size + prob.circles.size + (0 if prob.centres is None else prob.centres.size))
     d2h = 8 * (2 * T + 4 * (T + 1))
-    with mp.Planner(prob.params, device=local) as pe:
-        for _ in range(max(1, args.warmup)):
-            pe.plan(prob.x0, prob.ref, prob.circles, prob.centres)
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            pe.plan(prob.x0, prob.ref, prob.circles, prob.centres)
-        e2e_s = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t[0])
-    e2e = {"value": world * K * T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-           "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3}
+    e2e = None
+    if not args.quick:
+        p_e = dict(prob.params, group=group, block=block)
+        with mp.Planner(p_e, device=local) as pe:
+            for _ in range(max(1, args.warmup)):
+                pe.plan(prob.x0, prob.ref, prob.circles, prob.centres)
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                pe.plan(prob.x0, prob.ref, prob.circles, prob.centres)
+            e2e_s = (time.perf_counter() - t0) / args.steps
+        if world > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t[0])
+        e2e = {"value": world * K * T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3}
 
     # roofline of the rollout kernel: FP32-pipe bound (no dense contraction, noise bytes << compute)
     props = torch.cuda.get_device_properties(local)
@@ -282,11 +287,12 @@ def run_gpu(args, world, rank, local):
         "config": {"workload": f"{prob.name}: K={K} T={T} dt={prob.params['dt']} n_ref={prob.ref.shape[0]} "
                                f"n_circ={prob.circles.shape[0]}", "K": K, "T": T,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "flushed between steps (256 MB write)"},
+                   "l2": "flushed between steps (256 MB write)",
+                   "rollout_launch": {"lanes_per_sample": group, "threads_per_block": block}},
         "e2e": e2e, "roofline": roofline, "gpu_launches": KERNEL_LAUNCHES_PER_STEP * args.steps,
         "kernel_ms": kmean, "clocks": clocks,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.quick):
         import oracle
         k_s = oracle_sample(prob, args.cpu_seconds)
         el = time_oracle(prob, k_s)
@@ -338,6 +344,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--tune-cache", default=None, help="autotuner cache file (read first, appended after tuning)")
+    ap.add_argument("--quick", action="store_true",
+                    help="device timing only (no e2e, clocks or CPU baseline): the profiling run")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per rollout launch from an ncu capture of the current kernel")
     args = ap.parse_args()

@@ -92,6 +92,7 @@ typedef struct {
     uint64_t seed;              /* Philox key */
     uint32_t session;           /* Philox counter word 3: independent streams per session */
     int32_t group;              /* lanes per sample in the rollout kernel: 0 = choose, else 1,2,4,8,16,32 */
+    int32_t block;              /* threads per block of the rollout kernel: 0 = choose, else 64, 128, 256 */
 } mppi_params;
 
 /* Results of one iteration. */
@@ -145,6 +146,17 @@ int mppi_plan(mppi_ctx* ctx, const double* x0, const double* ref_xy, int32_t n_r
 int mppi_plan_device(mppi_ctx* ctx, const double* d_x0, const double* d_ref_xy, int32_t n_ref,
                      const double* d_circ, int32_t n_circ, const double* d_centres,
                      double* d_u_out, double* d_x_out, mppi_info* info);
+
+/* Autotuner: times the rollout kernel for every lanes-per-sample group (1..32) and
+   block size (64, 128, 256) on the given inputs (host arrays, as for mppi_plan) and
+   keeps the fastest for this context; *group and *block receive the choice (either
+   may be NULL).  The warm start and the iteration counter are not changed.  With a
+   cache_path (may be NULL) the choice is looked up first and stored after tuning,
+   keyed by GPU name, K, T, n_ref, n_circ and the noise precision (one text line per
+   entry).  Errors as for mppi_plan. */
+int mppi_autotune(mppi_ctx* ctx, const double* x0, const double* ref_xy, int32_t n_ref,
+                  const mppi_circle* circ, int32_t n_circ, const double* centres,
+                  const char* cache_path, int32_t* group, int32_t* block);
 
 /* Waits for the context's queued work and returns the status of the last iteration. */
 int mppi_sync(mppi_ctx* ctx, mppi_info* info);

@@ -53,7 +53,7 @@ class MppiParams(C.Structure):
         ("collision_only", C.c_int32), ("n_ego", C.c_int32),
         ("ego_offset", C.c_double * MAX_EGO), ("ego_radius", C.c_double * MAX_EGO),
         ("ref_mode", C.c_int32), ("sg_enable", C.c_int32), ("shift", C.c_int32), ("noise_bf16", C.c_int32),
-        ("seed", C.c_uint64), ("session", C.c_uint32), ("group", C.c_int32),
+        ("seed", C.c_uint64), ("session", C.c_uint32), ("group", C.c_int32), ("block", C.c_int32),
     ]
 
 
@@ -77,6 +77,8 @@ SIGNATURES = {
     "mppi_plan": (C.c_int, [_VP, _DP, _DP, C.c_int32, _DP, C.c_int32, _DP, _DP, _DP, C.POINTER(MppiInfo)]),
     "mppi_plan_device": (C.c_int, [_VP, _VP, _VP, C.c_int32, _VP, C.c_int32, _VP, _VP, _VP, C.POINTER(MppiInfo)]),
     "mppi_sync": (C.c_int, [_VP, C.POINTER(MppiInfo)]),
+    "mppi_autotune": (C.c_int, [_VP, _DP, _DP, C.c_int32, _DP, C.c_int32, _DP, C.c_char_p,
+                                C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "mppi_set_controls": (C.c_int, [_VP, _DP, C.c_uint64]),
     "mppi_get_controls": (C.c_int, [_VP, _DP, C.POINTER(C.c_uint64)]),
     "mppi_get_costs": (C.c_int, [_VP, _DP]),
@@ -135,6 +137,7 @@ def make_params(p: Dict[str, object]) -> MppiParams:
     s.seed = int(p["seed"]) & 0xFFFFFFFFFFFFFFFF
     s.session = int(p["session"]) & 0xFFFFFFFF
     s.group = int(p.get("group", 0))
+    s.block = int(p.get("block", 0))
     return s
 
 
@@ -210,6 +213,19 @@ class Planner:
                                     C.byref(info) if wait else None)
         _check(rc, self._h)
         return info.as_dict() if wait else None
+
+    def autotune(self, x0, ref, circles=None, centres=None, cache_path: Optional[str] = None):
+        """Pick the rollout kernel's (group, block) for these inputs; returns the choice."""
+        x0 = _f64(x0)
+        ref = _f64(ref).reshape(-1, 2)
+        circ = _f64(np.zeros((0, 5)) if circles is None else circles).reshape(-1, 5)
+        cen = None if centres is None else _f64(centres)
+        g, b = C.c_int32(), C.c_int32()
+        rc = lib().mppi_autotune(self._h, _dp(x0), _dp(ref), ref.shape[0], _dp(circ) if circ.shape[0] else None,
+                                 circ.shape[0], _dp(cen), cache_path.encode() if cache_path else None,
+                                 C.byref(g), C.byref(b))
+        _check(rc, self._h)
+        return g.value, b.value
 
     def sync(self) -> Dict[str, object]:
         info = MppiInfo()

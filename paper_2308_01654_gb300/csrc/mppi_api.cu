@@ -28,6 +28,7 @@ struct mppi_ctx {
     DevState* h_state = nullptr; // pinned copy of the device record
     size_t in_elems = 0, out_elems = 0;
     int group = 1;
+    int threads = 128;
     int profiling = 0;
     cudaEvent_t ev[N_KERNELS + 1] = {};
     std::string err;
@@ -86,6 +87,10 @@ static int check_params(const mppi_params* p, std::string& why) {
         why = "group must be 0, 1, 2, 4, 8, 16 or 32";
         return MPPI_ERR_ARG;
     }
+    if (!(p->block == 0 || p->block == 64 || p->block == 128 || p->block == 256)) {
+        why = "block must be 0, 64, 128 or 256";
+        return MPPI_ERR_ARG;
+    }
     return MPPI_OK;
 }
 
@@ -127,6 +132,14 @@ static PlanConst make_const(const mppi_params& p) {
         c.ego_off[e] = e < p.n_ego ? (float)p.ego_offset[e] : 0.0f;
         c.ego_rad[e] = e < p.n_ego ? (float)p.ego_radius[e] : 0.0f;
         if (e < p.n_ego && p.ego_radius[e] != p.ego_radius[0]) c.ego_same_radius = 0;
+    }
+    c.ego_omin = 0.0f;
+    c.ego_omax = 0.0f;
+    c.ego_rmax = 0.0f;
+    for (int e = 0; e < p.n_ego; ++e) {
+        c.ego_omin = e == 0 ? c.ego_off[0] : fminf(c.ego_omin, c.ego_off[e]);
+        c.ego_omax = e == 0 ? c.ego_off[0] : fmaxf(c.ego_omax, c.ego_off[e]);
+        c.ego_rmax = e == 0 ? c.ego_rad[0] : fmaxf(c.ego_rmax, c.ego_rad[e]);
     }
     c.ref_mode = p.ref_mode;
     c.has_table = 0;
@@ -219,6 +232,7 @@ int mppi_create(const mppi_params* params, int device, void* cuda_stream, int32_
     c->cap_ref = max_ref ? max_ref : MPPI_MAX_REF;
     c->cap_circ = max_circ ? max_circ : MPPI_MAX_CIRC;
     c->group = params->group ? params->group : auto_group(params->K);
+    c->threads = params->block ? params->block : 128;
     c->pc = make_const(*params);
     auto bail = [&](int status) {
         free_all(c);
@@ -326,7 +340,8 @@ static int enqueue(mppi_ctx* c, const PlanInputs& in, int has_table) {
     const SceneLayout L = make_layout(c->p.T, in.n_ref, in.n_circ);
     PlanConst pc = c->pc;
     pc.has_table = has_table;
-    CK(launch_iteration(pc, L, c->b, in, c->group, c->p.noise_bf16, c->stream, c->profiling ? c->ev : nullptr),
+    CK(launch_iteration(pc, L, c->b, in, c->group, c->threads, c->p.noise_bf16, c->stream,
+                        c->profiling ? c->ev : nullptr),
        "kernel launch");
     return MPPI_OK;
 }
@@ -355,16 +370,15 @@ static int wait_status(mppi_ctx* c, mppi_info* info, double eta_unused) {
     return s.status;
 }
 
-int mppi_plan(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n_ref, const mppi_circle* circ,
-              int32_t n_circ, const double* centres, double* u_out, double* x_out, mppi_info* info) {
-    if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
-    if (!x0 || !ref_xy || !u_out || !x_out || (n_circ > 0 && !circ))
-        return fail(c, MPPI_ERR_ARG, "NULL array argument");
+// Validates host inputs and queues their copy into the context's device input buffer.
+static int stage_host_inputs(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n_ref,
+                             const mppi_circle* circ, int32_t n_circ, const double* centres, PlanInputs& in) {
+    if (!x0 || !ref_xy || (n_circ > 0 && !circ)) return fail(c, MPPI_ERR_ARG, "NULL array argument");
     int rc = check_sizes(c, n_ref, n_circ);
     if (rc != MPPI_OK) return rc;
     const int T = c->p.T;
     const size_t nr = 2 * (size_t)n_ref, nc = 5 * (size_t)n_circ, nt = centres ? 2 * (size_t)T * n_circ : 0;
-    if (!finite_all(x0, 4) || !finite_all(ref_xy, nr) || !finite_all((const double*)circ, nc) ||
+    if (!finite_all(x0, 4) || !finite_all(ref_xy, nr) || (nc && !finite_all((const double*)circ, nc)) ||
         (centres && !finite_all(centres, nt)))
         return fail(c, MPPI_ERR_ARG, "non-finite input");
     double* h = c->h_in;
@@ -375,7 +389,6 @@ int mppi_plan(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n_ref
     const size_t n_in = 4 + nr + nc + nt;
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     CK(cudaMemcpyAsync(c->d_in, h, n_in * sizeof(double), cudaMemcpyHostToDevice, c->stream), "input copy");
-    PlanInputs in;
     in.x0 = c->d_in;
     in.ref = c->d_in + 4;
     in.circ = c->d_in + 4 + nr;
@@ -384,7 +397,18 @@ int mppi_plan(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n_ref
     in.n_circ = n_circ;
     in.u_out = c->d_out;
     in.x_out = c->d_out + 2 * (size_t)T;
-    rc = enqueue(c, in, nt ? 1 : 0);
+    return MPPI_OK;
+}
+
+int mppi_plan(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n_ref, const mppi_circle* circ,
+              int32_t n_circ, const double* centres, double* u_out, double* x_out, mppi_info* info) {
+    if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
+    if (!u_out || !x_out) return fail(c, MPPI_ERR_ARG, "NULL array argument");
+    const int T = c->p.T;
+    PlanInputs in;
+    int rc = stage_host_inputs(c, x0, ref_xy, n_ref, circ, n_circ, centres, in);
+    if (rc != MPPI_OK) return rc;
+    rc = enqueue(c, in, in.centres ? 1 : 0);
     if (rc != MPPI_OK) return rc;
     CK(cudaMemcpyAsync(c->h_out, c->d_out, c->out_elems * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
        "output copy");
@@ -414,6 +438,107 @@ int mppi_plan_device(mppi_ctx* c, const double* d_x0, const double* d_ref_xy, in
     rc = enqueue(c, in, d_centres ? 1 : 0);
     if (rc != MPPI_OK) return rc;
     if (info) return wait_status(c, info, 0.0);
+    return MPPI_OK;
+}
+
+static std::string gpu_name(int device) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return "unknown";
+    std::string n = prop.name;
+    for (auto& ch : n)
+        if (ch == ' ' || ch == '|') ch = '_';
+    return n;
+}
+
+static std::string tune_key(mppi_ctx* c, int n_ref, int n_circ) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s|%d|%d|%d|%d|%d", gpu_name(c->device).c_str(), c->p.K, c->p.T, n_ref, n_circ,
+             c->p.noise_bf16);
+    return buf;
+}
+
+static bool cache_lookup(const char* path, const std::string& key, int& g, int& t) {
+    if (!path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (fgets(line, sizeof(line), f)) {
+        char k[300];
+        int gg, tt;
+        float ms;
+        if (sscanf(line, "%299s %d %d %f", k, &gg, &tt, &ms) == 4 && key == k) {
+            g = gg;
+            t = tt;
+            found = true;   // the last entry for a key wins
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+static void cache_store(const char* path, const std::string& key, int g, int t, float ms) {
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %.6f\n", key.c_str(), g, t, ms);
+    fclose(f);
+}
+
+int mppi_autotune(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n_ref, const mppi_circle* circ,
+                  int32_t n_circ, const double* centres, const char* cache_path, int32_t* group, int32_t* block) {
+    if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
+    const std::string key = tune_key(c, n_ref, n_circ);
+    int g = 0, t = 0;
+    if (cache_lookup(cache_path, key, g, t)) {
+        c->group = g;
+        c->threads = t;
+    } else {
+        PlanInputs in;
+        int rc = stage_host_inputs(c, x0, ref_xy, n_ref, circ, n_circ, centres, in);
+        if (rc != MPPI_OK) return rc;
+        const SceneLayout L = make_layout(c->p.T, n_ref, n_circ);
+        PlanConst pc = c->pc;
+        pc.has_table = in.centres ? 1 : 0;
+        CK(launch_prep_noise(pc, L, c->b, in, c->p.noise_bf16, c->stream), "prep/noise launch");
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0), "cudaEventCreate");
+        CK(cudaEventCreate(&e1), "cudaEventCreate");
+        float best = INFINITY;
+        int bg = c->group, bt = c->threads;
+        const int groups[] = {1, 2, 4, 8, 16, 32};
+        const int blocks[] = {64, 128, 256};
+        cudaError_t err = cudaSuccess;
+        for (int gi = 0; gi < 6 && err == cudaSuccess; ++gi) {
+            for (int bi = 0; bi < 3 && err == cudaSuccess; ++bi) {
+                const long long lanes = (long long)c->p.K * groups[gi];
+                if (groups[gi] > 1 && lanes > 4LL * 152 * 2048) continue;   // far more lanes than the GPU holds
+                err = launch_rollout(pc, L, c->b, groups[gi], blocks[bi], c->p.noise_bf16, c->stream);  // warm-up
+                if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+                for (int r = 0; r < 3 && err == cudaSuccess; ++r)
+                    err = launch_rollout(pc, L, c->b, groups[gi], blocks[bi], c->p.noise_bf16, c->stream);
+                if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+                if (err == cudaSuccess && ms < best) {
+                    best = ms;
+                    bg = groups[gi];
+                    bt = blocks[bi];
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (err == cudaSuccess) err = launch_reset_state(c->b.state, c->stream);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+        if (err != cudaSuccess) return cuda_fail(c, err, "autotune");
+        c->group = bg;
+        c->threads = bt;
+        cache_store(cache_path, key, bg, bt, best / 3.0f);
+    }
+    if (group) *group = c->group;
+    if (block) *block = c->threads;
     return MPPI_OK;
 }
 

@@ -62,6 +62,35 @@ __device__ __forceinline__ float2 box_muller(float u0, float u1) {
     return make_float2(r * c, r * s);
 }
 
+// Box-Muller in binary64 (the slow path of the bfloat16 store).
+__device__ __forceinline__ double2 box_muller_f64(float u0, float u1) {
+    const double r = sqrt(-2.0 * log((double)u0));
+    double s, c;
+    sincospi(2.0 * (double)u1, &s, &c);
+    return make_double2(r * c, r * s);
+}
+
+// Round a binary64 value to the nearest bfloat16 (8 significant bits, ties to even)
+// in one step: add half of the dropped 45-bit field (plus the kept LSB for ties) and
+// truncate; the result has 8 significant bits, so the final conversion is exact.
+__device__ __forceinline__ __nv_bfloat16 bf16_from_f64(double z) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(z);
+    const unsigned long long lsb = (b >> 45) & 1ull;
+    b += 0x0FFFFFFFFFFFull + lsb;
+    b &= ~0x1FFFFFFFFFFFull;
+    return __float2bfloat16_rn((float)__longlong_as_double((long long)b));
+}
+
+// True when a binary32 normal may sit on the other side of a bfloat16 rounding
+// midpoint than the exact normal: within the binary32 Box-Muller error bound
+// (4e-7 * max(1, |z|)) of the midpoint, or so small that the bound covers the spacing.
+__device__ __forceinline__ bool near_bf16_midpoint(float z) {
+    const float az = fabsf(z);
+    if (az < 1e-4f) return true;
+    const float mid = __uint_as_float((__float_as_uint(z) & 0xFFFF0000u) | 0x8000u);
+    return fabsf(z - mid) <= 4e-7f * fmaxf(1.0f, az);
+}
+
 // -----------------------------------------------------------------------------
 // Noise storage: [T][K] of (z_a, z_delta), binary32 pairs or bfloat16 pairs.
 // -----------------------------------------------------------------------------
@@ -121,6 +150,27 @@ __device__ __forceinline__ float seg_dist2(float px, float py, float2 a, float2 
     }
     const float dx = px - qx, dy = py - qy;
     return fmaf(dx, dx, dy * dy);
+}
+
+// The same distance in binary64 from the binary32 inputs: used to settle near ties
+// between two segments, where the two binary32 distances cannot be ordered (next to a
+// vertex on the outside of a bend the gap is second order in the offset).
+__device__ __forceinline__ double seg_dist2_f64(float px, float py, float2 a, float2 b) {
+    const double ax = a.x, ay = a.y, ex = (double)b.x - ax, ey = (double)b.y - ay;
+    const double dax = (double)px - ax, day = (double)py - ay;
+    const double l2 = ex * ex + ey * ey;
+    const double tau = l2 > 0.0 ? (dax * ex + day * ey) / l2 : 0.0;
+    double qx, qy;
+    if (tau <= 0.0) {
+        qx = ax; qy = ay;
+    } else if (tau >= 1.0) {
+        qx = b.x; qy = b.y;
+    } else {
+        qx = ax + tau * ex;
+        qy = ay + tau * ey;
+    }
+    const double dx = (double)px - qx, dy = (double)py - qy;
+    return dx * dx + dy * dy;
 }
 
 // Squared distance from p to an axis-aligned box (minx, miny, maxx, maxy).

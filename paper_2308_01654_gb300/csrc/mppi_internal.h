@@ -20,6 +20,8 @@ struct __align__(16) DevState {
     unsigned long long jkey;     // packed (distance bits, index) for the jb0 search
     float4 x0f;                  // (0, 0, yaw0, v0): x0 in the local frame
     unsigned long long iter_used;  // iteration index of the last finished iteration
+    int32_t moving;              // some obstacle circle has a nonzero velocity
+    int32_t pad_[3];
 };
 
 // Byte offsets of the arrays in the scene blob that the rollout kernel stages into
@@ -50,6 +52,7 @@ struct PlanConst {
     int n_ego;
     int ego_same_radius;     // all ego radii equal: the band limit is per circle
     float ego_off[8], ego_rad[8];
+    float ego_omin, ego_omax, ego_rmax;   // extent of the ego circles along the heading, largest radius
     int ref_mode;
     int has_table;           // per-step centre table given
     uint32_t key0, key1, session;
@@ -92,15 +95,21 @@ struct PlanInputs {
 // ev: optional array of N_KERNELS + 1 events recorded around the kernels (per-kernel timing).
 constexpr int N_KERNELS = 7;   // prep, noise, rollout, argmin, weights, wsum, finalize
 cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
-                             const PlanInputs& in, int group, int noise_bf16, cudaStream_t st,
+                             const PlanInputs& in, int group, int threads, int noise_bf16, cudaStream_t st,
                              cudaEvent_t* ev = nullptr);
+
+// prep + noise only (no change to the warm start or the iteration counter) and the
+// reset of the fields prep accumulates into; used by the autotuner.
+cudaError_t launch_prep_noise(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
+                              const PlanInputs& in, int noise_bf16, cudaStream_t st);
+cudaError_t launch_reset_state(DevState* st, cudaStream_t s);
 
 // Raw Philox words for n counters (device buffers).
 cudaError_t launch_philox(uint2 key, const uint4* ctr, uint4* out, int n, cudaStream_t st);
 
 // Rollout kernel only (for timing and tuning); requires prep and noise of the same plan.
 cudaError_t launch_rollout(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int group,
-                           int noise_bf16, cudaStream_t st);
+                           int threads, int noise_bf16, cudaStream_t st);
 
 size_t rollout_smem_bytes(const SceneLayout& L);
 

@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(256) prep_kernel(PlanConst pc, SceneLayout L, 
         const float lim = m + r + pc.ego_rad[0];
         circ[k] = make_float4((float)(c[0] - ox), (float)(c[1] - oy), r, lim > 0.0f ? lim * lim : -1.0f);
         vel[k] = make_float2((float)c[3], (float)c[4]);
+        if (c[3] != 0.0 || c[4] != 0.0) atomicOr(&b.state->moving, 1);
     }
     if (in.centres) {
         for (int i = tid; i < L.T * L.n_circ; i += nth) {
@@ -134,7 +135,25 @@ __global__ void __launch_bounds__(256) prep_kernel(PlanConst pc, SceneLayout L, 
 
 // -----------------------------------------------------------------------------
 // noise: one thread per (step pair j, sample k); coalesced stores along k.
+// The bfloat16 store is a rounding decision: it is taken on the exact normal
+// (binary64 Box-Muller) whenever the binary32 normal lies within its error bound
+// of a rounding midpoint, so the stored code is the one of the exact value.
 // -----------------------------------------------------------------------------
+template <bool BF16>
+__device__ __forceinline__ typename NoiseT<BF16>::type make_noise(float u0, float u1) {
+    const float2 zf = box_muller(u0, u1);
+    if constexpr (BF16) {
+        if (near_bf16_midpoint(zf.x) || near_bf16_midpoint(zf.y)) {
+            const double2 zd = box_muller_f64(u0, u1);
+            __nv_bfloat162 r;
+            r.x = bf16_from_f64(zd.x);
+            r.y = bf16_from_f64(zd.y);
+            return r;
+        }
+    }
+    return NoiseT<BF16>::pack(zf);
+}
+
 template <bool BF16>
 __global__ void __launch_bounds__(256) noise_kernel(PlanConst pc, const DevState* st,
                                                     typename NoiseT<BF16>::type* z) {
@@ -144,9 +163,8 @@ __global__ void __launch_bounds__(256) noise_kernel(PlanConst pc, const DevState
     const uint32_t it = (uint32_t)st->iter;
     const uint4 w = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)k, it, pc.session), make_uint2(pc.key0, pc.key1));
     const size_t K = (size_t)pc.K;
-    z[(size_t)(2 * j) * K + k] = NoiseT<BF16>::pack(box_muller(uniform24(w.x), uniform24(w.y)));
-    if (2 * j + 1 < pc.T)
-        z[(size_t)(2 * j + 1) * K + k] = NoiseT<BF16>::pack(box_muller(uniform24(w.z), uniform24(w.w)));
+    z[(size_t)(2 * j) * K + k] = make_noise<BF16>(uniform24(w.x), uniform24(w.y));
+    if (2 * j + 1 < pc.T) z[(size_t)(2 * j + 1) * K + k] = make_noise<BF16>(uniform24(w.z), uniform24(w.w));
 }
 
 __global__ void philox_kernel(uint2 key, const uint4* ctr, uint4* out, int n) {
@@ -230,35 +248,69 @@ __device__ __forceinline__ float group_min(float v, unsigned mask) {
     return v;
 }
 
-// Exact closest point of the polyline (ties -> lowest segment) with a two-level box
-// hierarchy; a box is skipped only when its lower bound exceeds the best distance
-// so far (with a relative slack far above binary32 rounding), so the result equals
-// a brute-force scan in the same arithmetic.
+// Closest point of the polyline (ties -> lowest segment) with a two-level box
+// hierarchy; a box is skipped only when its lower bound exceeds the best distance so
+// far (with a relative slack far above binary32 rounding), so no segment that can be
+// the closest is missed.  The scan keeps the two best distinct segments; when their
+// binary32 distances are within 4e-6 relative, the pair is re-ordered in binary64.
+struct Best2 {
+    float b2, c2;
+    int bi, ci;
+};
+
+__device__ __forceinline__ bool better(float d, int i, float e, int j) { return d < e || (d == e && i < j); }
+
+__device__ __forceinline__ void best2_insert(Best2& r, float d, int i) {
+    if (i == r.bi) return;
+    if (better(d, i, r.b2, r.bi)) {
+        r.c2 = r.b2;
+        r.ci = r.bi;
+        r.b2 = d;
+        r.bi = i;
+    } else if (i != r.ci && better(d, i, r.c2, r.ci)) {
+        r.c2 = d;
+        r.ci = i;
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void group_best2(Best2& r, unsigned mask) {
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) {
+        const float ob = __shfl_xor_sync(mask, r.b2, o, G), oc = __shfl_xor_sync(mask, r.c2, o, G);
+        const int obi = __shfl_xor_sync(mask, r.bi, o, G), oci = __shfl_xor_sync(mask, r.ci, o, G);
+        best2_insert(r, ob, obi);
+        if (oci >= 0) best2_insert(r, oc, oci);
+    }
+}
+
 template <int G>
 __device__ __forceinline__ void nearest_segment(float px, float py, const float2* vert, const float4* seg,
                                                 const float4* l1, const float4* l2, int n_seg, int n_l1,
                                                 int n_l2, int lane_g, unsigned mask, int& jb, float& best2) {
     constexpr float SLACK = 1.0f + 1.0f / 1024.0f;
-    float b2 = seg_dist2(px, py, vert[jb], vert[jb + 1], seg[jb]);
-    int bi = jb;
+    Best2 r{seg_dist2(px, py, vert[jb], vert[jb + 1], seg[jb]), INFINITY, jb, -1};
     for (int g = 0; g < n_l2; ++g) {
-        if (box_dist2(px, py, l2[g]) > b2 * SLACK) continue;
+        if (box_dist2(px, py, l2[g]) > r.b2 * SLACK) continue;
         const int c1 = min((g + 1) * REF_L2, n_l1);
         for (int c = g * REF_L2; c < c1; ++c) {
-            if (box_dist2(px, py, l1[c]) > b2 * SLACK) continue;
+            if (box_dist2(px, py, l1[c]) > r.b2 * SLACK) continue;
             const int i1 = min((c + 1) * REF_L1, n_seg);
-            for (int i = c * REF_L1 + lane_g; i < i1; i += G) {
-                const float d2 = seg_dist2(px, py, vert[i], vert[i + 1], seg[i]);
-                if (d2 < b2 || (d2 == b2 && i < bi)) {
-                    b2 = d2;
-                    bi = i;
-                }
-            }
-            group_argmin<G>(b2, bi, mask);
+            for (int i = c * REF_L1 + lane_g; i < i1; i += G)
+                best2_insert(r, seg_dist2(px, py, vert[i], vert[i + 1], seg[i]), i);
+            group_best2<G>(r, mask);
         }
     }
-    jb = bi;
-    best2 = b2;
+    if (r.ci >= 0 && r.c2 - r.b2 <= 4e-6f * r.b2 + 1e-20f && seg[r.bi].w != seg[r.ci].w) {
+        const double db = seg_dist2_f64(px, py, vert[r.bi], vert[r.bi + 1]);
+        const double dc = seg_dist2_f64(px, py, vert[r.ci], vert[r.ci + 1]);
+        if (dc < db || (dc == db && r.ci < r.bi)) {
+            r.bi = r.ci;
+            r.b2 = r.c2;
+        }
+    }
+    jb = r.bi;
+    best2 = r.b2;
 }
 
 // Closest vertex (ties -> lowest index), same hierarchy (chunk c covers vertices c*L1 .. c*L1+L1).
@@ -291,6 +343,104 @@ __device__ __forceinline__ void nearest_vertex(float px, float py, const float2*
     best2 = b2;
 }
 
+// Kahan-compensated accumulator: the value is hi - lo.
+__device__ __forceinline__ void kahan_add(float& hi, float& lo, float inc) {
+    const float y = inc - lo;
+    const float t = hi + y;
+    lo = (t - hi) - y;
+    hi = t;
+}
+
+// Centre of circle kc at rollout step t (state x_{t+1}).
+__device__ __forceinline__ float2 circle_centre(const float4* circ, const float2* vel, const float2* table, int n_circ,
+                                                int t, int kc, float st, bool has_table, bool moving) {
+    if (has_table) return table[(size_t)t * n_circ + kc];
+    const float4 c = circ[kc];
+    if (!moving) return make_float2(c.x, c.y);
+    const float2 vv = vel[kc];
+    return make_float2(fmaf(vv.x, st, c.x), fmaf(vv.y, st, c.y));
+}
+
+__device__ __forceinline__ float warp_min_f(float v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// d_obj of Eq. (16) restricted to the pairs that can lie inside the safety band (the
+// only pairs that change c_safe), with a warp-wide broad phase: the lanes test the
+// circles against the bounding box of every ego circle of the warp, and only the
+// circles that pass (ballot) get the exact per-pair test.  A circle is skipped only
+// when no ego circle of the warp can come within the band of it, so the result equals
+// the brute-force minimum over all in-band pairs.
+template <int G>
+__device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4* circ, const float2* vel,
+                                              const float2* table, int n_circ, int t, bool has_table, bool moving,
+                                              bool dconst, float nx, float ny, float cnth, float snth, float mband,
+                                              int lane, int lane_g, unsigned mask) {
+    float ex[8], ey[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        if (e >= pc.n_ego) break;
+        ex[e] = fmaf(pc.ego_off[e], cnth, nx);
+        ey[e] = fmaf(pc.ego_off[e], snth, ny);
+    }
+    // box of the ego circle centres of the whole warp
+    const float xa = fmaf(pc.ego_omin, cnth, nx), xb = fmaf(pc.ego_omax, cnth, nx);
+    const float ya = fmaf(pc.ego_omin, snth, ny), yb = fmaf(pc.ego_omax, snth, ny);
+    const float bx0 = warp_min_f(fminf(xa, xb)), bx1 = warp_max_f(fmaxf(xa, xb));
+    const float by0 = warp_min_f(fminf(ya, yb)), by1 = warp_max_f(fmaxf(ya, yb));
+    const float mmax = dconst ? mband : warp_max_f(mband);
+    const float st = (float)(t + 1) * pc.dt;
+    float dobj = INFINITY;
+    for (int base = 0; base < n_circ; base += 32) {
+        const int kc = base + lane;
+        bool hit = false;
+        if (kc < n_circ) {
+            const float2 cc = circle_centre(circ, vel, table, n_circ, t, kc, st, has_table, moving);
+            const float lim = (mmax + circ[kc].z + pc.ego_rmax) * 1.0001f + 1e-4f;
+            const float dx = fmaxf(fmaxf(bx0 - cc.x, cc.x - bx1), 0.0f);
+            const float dy = fmaxf(fmaxf(by0 - cc.y, cc.y - by1), 0.0f);
+            hit = lim > 0.0f && fmaf(dx, dx, dy * dy) <= lim * lim;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, hit);
+        for (int j = 0; m; ++j) {
+            const int bit = __ffs(m) - 1;
+            m &= m - 1;
+            if ((j & (G - 1)) != lane_g) continue;
+            const int kc2 = base + bit;
+            const float4 c = circ[kc2];
+            const float2 cc = circle_centre(circ, vel, table, n_circ, t, kc2, st, has_table, moving);
+            if (dconst) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    if (e >= pc.n_ego) break;
+                    const float dx = ex[e] - cc.x, dy = ey[e] - cc.y;
+                    const float d2 = fmaf(dx, dx, dy * dy);
+                    if (d2 <= c.w) dobj = fminf(dobj, sqrtf(d2) - (c.z + pc.ego_rad[e]));
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    if (e >= pc.n_ego) break;
+                    const float R = c.z + pc.ego_rad[e];
+                    const float lim = mband + R;
+                    const float dx = ex[e] - cc.x, dy = ey[e] - cc.y;
+                    const float d2 = fmaf(dx, dx, dy * dy);
+                    if (lim > 0.0f && d2 <= lim * lim) dobj = fminf(dobj, sqrtf(d2) - R);
+                }
+            }
+        }
+    }
+    return group_min<G>(dobj, mask);
+}
+
 template <int G, bool BF16>
 __global__ void __launch_bounds__(256) rollout_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
                                                       const typename NoiseT<BF16>::type* __restrict__ z) {
@@ -309,18 +459,23 @@ __global__ void __launch_bounds__(256) rollout_kernel(PlanConst pc, SceneLayout 
 
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = gtid / G;
+    const int lane = threadIdx.x & 31;
     const int lane_g = threadIdx.x & (G - 1);
     const unsigned mask = group_mask<G>();
     const int K = pc.K, T = pc.T;
     const int kk = min(k, K - 1);               // whole groups past K run along (shuffle safety)
     const float4 x0 = b.state->x0f;
+    const bool moving = b.state->moving != 0;
+    const bool has_table = pc.has_table != 0;
     const float2 tp = vert[L.n_ref - 1];        // target point T_P: last vertex
     const bool dconst = pc.d_safe_c == 0.0f && pc.ego_same_radius;
-    const float m_off = pc.collision_only ? 1.0f : 0.0f;
 
+    // x_t with compensated (Kahan) accumulation; the value of each coordinate is hi - lo
     float px = x0.x, py = x0.y, th = x0.z, v = x0.w;
+    float px_c = 0.0f, py_c = 0.0f, th_c = 0.0f, v_c = 0.0f;
     float sth, cth;
     sincosf(th, &sth, &cth);
+    float tdp = fmaf(tp.x, tp.x, tp.y * tp.y);   // |P_0 - T_P|^2 with P_0 = (0, 0)
     int jb = (int)(b.state->jkey & 0xffffffffu);
     float s_hi = 0.0f, s_c = 0.0f, q_last = 0.0f;
 
@@ -328,76 +483,59 @@ __global__ void __launch_bounds__(256) rollout_kernel(PlanConst pc, SceneLayout 
         const float4 ct = ctl[t];
         const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
         const Perturbed pe = perturb(ct.x, ct.y, zz, pc.sig_a, pc.sig_d, pc.amin, pc.amax, pc.dmin, pc.dmax);
+        const float vt = v - v_c;
         float acc = pe.va;
-        if (pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - v) / pc.dt), pc.amin);
+        if (pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt) / pc.dt), pc.amin);
         // Eq. (5), explicit Euler from x_t
         const float tn = tanf(pe.vd);
-        const float nx = fmaf(v * cth, pc.dt, px);
-        const float ny = fmaf(v * sth, pc.dt, py);
-        const float nth = fmaf(v * tn, pc.dt_over_L, th);
-        const float nv = fmaf(acc, pc.dt, v);
+        kahan_add(px, px_c, vt * cth * pc.dt);
+        kahan_add(py, py_c, vt * sth * pc.dt);
+        kahan_add(th, th_c, vt * tn * pc.dt_over_L);
+        kahan_add(v, v_c, acc * pc.dt);
+        const float nx = px, ny = py;
         float snth, cnth;
-        sincosf(nth, &snth, &cnth);
+        sincosf(th, &snth, &cnth);
 
-        // Eq. (12), (14): closest waypoint and reference yaw
+        // Eq. (12), (14): closest waypoint (search on the binary32 position) and reference yaw
         float d2r;
         if (pc.ref_mode == 0)
             nearest_segment<G>(nx, ny, vert, seg, l1, l2, L.n_seg, L.n_l1, L.n_l2, lane_g, mask, jb, d2r);
         else
             nearest_vertex<G>(nx, ny, vert, l1, l2, L.n_ref, L.n_l1, L.n_l2, lane_g, mask, jb, d2r);
         const float thr = seg[min(jb, L.n_seg - 1)].w;
+        {
+            // c_dist on the compensated position: closest point of the winning segment or vertex
+            const float2 a = vert[jb];
+            float qx = a.x, qy = a.y;
+            if (pc.ref_mode == 0) {
+                const float4 sg = seg[jb];
+                const float tau = fmaf(nx - a.x, sg.x, (ny - a.y) * sg.y) * sg.z;
+                if (tau >= 1.0f) {
+                    qx = vert[jb + 1].x;
+                    qy = vert[jb + 1].y;
+                } else if (tau > 0.0f) {
+                    qx = fmaf(tau, sg.x, a.x);
+                    qy = fmaf(tau, sg.y, a.y);
+                }
+            }
+            const float dx = (nx - qx) - px_c, dy = (ny - qy) - py_c;
+            d2r = fmaf(dx, dx, dy * dy);
+        }
         // Eq. (13): progress towards the target point
-        const float tnx = nx - tp.x, tny = ny - tp.y, tpx = px - tp.x, tpy = py - tp.y;
-        const float c_target = fmaf(tnx, tnx, tny * tny) > fmaf(tpx, tpx, tpy * tpy) ? 1.0f : 0.0f;
-        const float dyaw = wrap_pi(nth - thr);
-        const float dv = nv - pc.v_ref;
+        const float tx = (nx - tp.x) - px_c, ty = (ny - tp.y) - py_c;
+        const float tdn = fmaf(tx, tx, ty * ty);
+        const float c_target = tdn > tdp ? 1.0f : 0.0f;
+        tdp = tdn;
+        const float dyaw = wrap_pi((th - thr) - th_c);
+        const float dv = (v - pc.v_ref) - v_c;
 
         // Eq. (16)-(17): ego circles against obstacle circles
-        const float ds = fmaf(pc.d_safe_c, nv, pc.d_safe_0);
-        const float mband = m_off != 0.0f ? fmaxf(ds, 0.0f) : ds;
-        float ex[8], ey[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            ex[e] = fmaf(pc.ego_off[e], cnth, nx);
-            ey[e] = fmaf(pc.ego_off[e], snth, ny);
-        }
-        const float st = (float)(t + 1) * pc.dt;
+        const float ds = fmaf(pc.d_safe_c, v - v_c, pc.d_safe_0);
+        const float mband = pc.collision_only ? fmaxf(ds, 0.0f) : ds;
         float dobj = INFINITY;
-        for (int kc = lane_g; kc < L.n_circ; kc += G) {
-            const float4 c = circ[kc];
-            float cx, cy;
-            if (pc.has_table) {
-                const float2 q = b.table[(size_t)t * L.n_circ + kc];
-                cx = q.x;
-                cy = q.y;
-            } else {
-                const float2 vv = vel[kc];
-                cx = fmaf(vv.x, st, c.x);
-                cy = fmaf(vv.y, st, c.y);
-            }
-            if (dconst) {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    if (e < pc.n_ego) {
-                        const float dx = ex[e] - cx, dy = ey[e] - cy;
-                        const float d2 = fmaf(dx, dx, dy * dy);
-                        if (d2 <= c.w) dobj = fminf(dobj, sqrtf(d2) - (c.z + pc.ego_rad[e]));
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    if (e < pc.n_ego) {
-                        const float R = c.z + pc.ego_rad[e];
-                        const float lim = mband + R;
-                        const float dx = ex[e] - cx, dy = ey[e] - cy;
-                        const float d2 = fmaf(dx, dx, dy * dy);
-                        if (lim > 0.0f && d2 <= lim * lim) dobj = fminf(dobj, sqrtf(d2) - R);
-                    }
-                }
-            }
-        }
-        dobj = group_min<G>(dobj, mask);
+        if (L.n_circ > 0)
+            dobj = obstacle_min<G>(pc, circ, vel, b.table, L.n_circ, t, has_table, moving, dconst, nx, ny, cnth,
+                                   snth, mband, lane, lane_g, mask);
         const float gap = ds - dobj;
         float c_safe = gap > 0.0f ? gap * gap : 0.0f;
         if (pc.collision_only && !(dobj <= 0.0f)) c_safe = 0.0f;
@@ -407,13 +545,10 @@ __global__ void __launch_bounds__(256) rollout_kernel(PlanConst pc, SceneLayout 
                               fmaf(pc.w_target, c_target,
                                    fmaf(pc.w_yaw, dyaw * dyaw, fmaf(pc.w_speed, dv * dv, pc.w_safe * c_safe))));
         const float qu = fmaf(ct.z, pe.ea, fmaf(ct.w, pe.ed, c0[t]));
-        // compensated (Kahan) sum of the step costs, Eq. (6)
-        const float y = (qx + qu) - s_c;
-        const float tsum = s_hi + y;
-        s_c = (tsum - s_hi) - y;
-        s_hi = tsum;
+        kahan_add(s_hi, s_c, qx + qu);          // Eq. (6)
         q_last = qx;
-        px = nx; py = ny; th = nth; v = nv; sth = snth; cth = cnth;
+        sth = snth;
+        cth = cnth;
     }
     if (lane_g == 0 && k < K) {
         double S = (double)s_hi - (double)s_c;
@@ -660,6 +795,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(PlanConst pc, PlanBuffer
         if (t == 0) {
             st->status = s_status;
             st->flags = 0;
+            st->moving = 0;
             st->jkey = ~0ull;
         }
         return;
@@ -744,6 +880,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(PlanConst pc, PlanBuffer
         st->iter_used = st->iter;
         st->iter += 1ull;
         st->flags = 0;
+        st->moving = 0;
         st->jkey = ~0ull;
     }
 }
@@ -752,7 +889,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(PlanConst pc, PlanBuffer
 // host-side launchers
 // -----------------------------------------------------------------------------
 template <int G, bool BF16>
-static cudaError_t launch_rollout_t(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
+static cudaError_t launch_rollout_t(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int threads,
                                     cudaStream_t st) {
     const size_t smem = rollout_smem_bytes(L);
     static int configured_smem = -1;
@@ -762,7 +899,6 @@ static cudaError_t launch_rollout_t(const PlanConst& pc, const SceneLayout& L, c
         if (e != cudaSuccess) return e;
         configured_smem = (int)(smem < 48 * 1024 ? 48 * 1024 : smem);
     }
-    const int threads = 256;
     const long long total = (long long)pc.K * G;
     const int blocks = (int)((total + threads - 1) / threads);
     rollout_kernel<G, BF16><<<blocks, threads, smem, st>>>(
@@ -772,25 +908,58 @@ static cudaError_t launch_rollout_t(const PlanConst& pc, const SceneLayout& L, c
 
 template <bool BF16>
 static cudaError_t launch_rollout_b(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int group,
-                                    cudaStream_t st) {
+                                    int threads, cudaStream_t st) {
     switch (group) {
-        case 1: return launch_rollout_t<1, BF16>(pc, L, b, st);
-        case 2: return launch_rollout_t<2, BF16>(pc, L, b, st);
-        case 4: return launch_rollout_t<4, BF16>(pc, L, b, st);
-        case 8: return launch_rollout_t<8, BF16>(pc, L, b, st);
-        case 16: return launch_rollout_t<16, BF16>(pc, L, b, st);
-        case 32: return launch_rollout_t<32, BF16>(pc, L, b, st);
+        case 1: return launch_rollout_t<1, BF16>(pc, L, b, threads, st);
+        case 2: return launch_rollout_t<2, BF16>(pc, L, b, threads, st);
+        case 4: return launch_rollout_t<4, BF16>(pc, L, b, threads, st);
+        case 8: return launch_rollout_t<8, BF16>(pc, L, b, threads, st);
+        case 16: return launch_rollout_t<16, BF16>(pc, L, b, threads, st);
+        case 32: return launch_rollout_t<32, BF16>(pc, L, b, threads, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_rollout(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int group,
-                           int noise_bf16, cudaStream_t st) {
-    return noise_bf16 ? launch_rollout_b<true>(pc, L, b, group, st) : launch_rollout_b<false>(pc, L, b, group, st);
+                           int threads, int noise_bf16, cudaStream_t st) {
+    if (threads != 64 && threads != 128 && threads != 256) return cudaErrorInvalidValue;
+    return noise_bf16 ? launch_rollout_b<true>(pc, L, b, group, threads, st)
+                      : launch_rollout_b<false>(pc, L, b, group, threads, st);
+}
+
+cudaError_t launch_prep_noise(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
+                              const PlanInputs& in, int noise_bf16, cudaStream_t st) {
+    int items = L.n_ref;
+    items = max(items, L.T);
+    items = max(items, L.n_circ);
+    if (in.centres) items = max(items, L.T * L.n_circ);
+    const int blocks = min(max((items + 255) / 256, 1), 148);
+    prep_kernel<<<blocks, 256, 0, st>>>(pc, L, in, b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 grid((pc.K + 255) / 256, (pc.T + 1) / 2);
+    if (noise_bf16)
+        noise_kernel<true><<<grid, 256, 0, st>>>(pc, b.state, reinterpret_cast<__nv_bfloat162*>(b.z));
+    else
+        noise_kernel<false><<<grid, 256, 0, st>>>(pc, b.state, reinterpret_cast<float2*>(b.z));
+    return cudaGetLastError();
+}
+
+// resets the per-iteration fields that prep accumulates into (after a prep without finalize)
+__global__ void reset_state_kernel(DevState* st) {
+    st->flags = 0;
+    st->moving = 0;
+    st->jkey = ~0ull;
+}
+
+cudaError_t launch_reset_state(DevState* st, cudaStream_t s) {
+    reset_state_kernel<<<1, 1, 0, s>>>(st);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
-                             const PlanInputs& in, int group, int noise_bf16, cudaStream_t st, cudaEvent_t* ev) {
+                             const PlanInputs& in, int group, int threads, int noise_bf16, cudaStream_t st,
+                             cudaEvent_t* ev) {
     cudaError_t e;
     int stage = 0;
     auto mark = [&]() -> cudaError_t {
@@ -817,7 +986,7 @@ cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const Pl
             noise_kernel<false><<<grid, 256, 0, st>>>(pc, b.state, reinterpret_cast<float2*>(b.z));
         if ((e = mark()) != cudaSuccess) return e;
     }
-    if ((e = launch_rollout(pc, L, b, group, noise_bf16, st)) != cudaSuccess) return e;
+    if ((e = launch_rollout(pc, L, b, group, threads, noise_bf16, st)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
     argmin_kernel<<<b.n_mblk, 256, 0, st>>>(pc.K, b);
     if ((e = mark()) != cudaSuccess) return e;

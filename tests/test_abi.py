@@ -50,7 +50,8 @@ def test_binding_covers_every_declared_symbol():
 def test_struct_layouts_match_the_header():
     # sizes follow from the field lists of include/mppi.h on an LP64 ABI
     assert ctypes.sizeof(mp.MppiInfo) == 32
-    assert ctypes.sizeof(mp.MppiParams) == 4 * 2 + 8 * 2 + 8 * 6 + 8 * 4 + 8 * 6 + 8 * 2 + 8 * 2 + 4 * 2 + 8 * 16 + 4 * 4 + 8 + 8
+    assert ctypes.sizeof(mp.MppiParams) == (4 * 2 + 8 * 2 + 8 * 6 + 8 * 4 + 8 * 6 + 8 * 2 + 8 * 2 + 4 * 2 + 8 * 16
+                                            + 4 * 4 + 8 + 4 * 3 + 4)
 
 
 def test_default_params_are_the_papers_weights():
@@ -65,7 +66,7 @@ def test_status_strings():
 
 
 @pytest.mark.parametrize("bad", [dict(K=0), dict(T=0), dict(T=5000), dict(dt=0.0), dict(lam=-1.0),
-                                 dict(n_ego=9), dict(sigma=[-0.1, 0.1]), dict(group=3)])
+                                 dict(n_ego=9), dict(sigma=[-0.1, 0.1]), dict(group=3), dict(block=96)])
 def test_invalid_params_are_rejected_before_any_cuda_call(bad):
     from paper_2308_01654_gb300 import scenarios
     p = scenarios.default_params(64, 10, 0.05)
