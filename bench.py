@@ -54,6 +54,34 @@ def rollout_ops_per_step(prob) -> float:
     return 60.0 + 6.0 * n_e * n_c + 5.0 * math.ceil((n_ref - 1) / 32.0) + 11.0 * 64.0
 
 
+KERNEL_SOURCES = ("paper_2308_01654_gb300/csrc/mppi_kernels.cu", "paper_2308_01654_gb300/csrc/mppi_device.cuh",
+                  "paper_2308_01654_gb300/csrc/mppi_internal.h")
+TRAFFIC_PROFILE = {"roofline": "profiles/rollout_kernel_roofline_K65536_T200.md"}
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per rollout launch from the committed ncu summary, if taken on the current kernel source."""
+    import re
+    path = TRAFFIC_PROFILE.get(workload)
+    if not path or not os.path.exists(os.path.join(ROOT, path)):
+        return None
+    txt = open(os.path.join(ROOT, path)).read()
+    m_h = re.search(r"sha256\[:16\]\): `([0-9a-f]+)`", txt)
+    m_b = re.search(r"dram_bytes_per_launch = (\d+)", txt)
+    if not m_h or not m_b or m_h.group(1) != kernel_source_hash():
+        return None
+    return int(m_b.group(1))
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -273,7 +301,8 @@ def run_gpu(args, world, rank, local):
     ops = rollout_ops_per_step(prob) * K * T
     achieved = ops / (ms_roll * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TOP/s",
-                "frac": achieved / peak_tops, "traffic": args.traffic,
+                "frac": achieved / peak_tops,
+                "traffic": args.traffic if args.traffic is not None else profiled_traffic(args.workload),
                 "kernel": "rollout_kernel", "ops_per_rollout_step": rollout_ops_per_step(prob),
                 "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {f_max:.0f} MHz (max SM clock)",
                 "kernel_ms": ms_roll}
