@@ -183,6 +183,29 @@ int mppi_philox(uint64_t seed, const uint32_t* ctr, int32_t n, uint32_t* out);
 int mppi_set_profiling(mppi_ctx* ctx, int32_t on);
 int mppi_kernel_times(mppi_ctx* ctx, float* ms, int32_t n);
 
+/* Allocation-free lowest-cost search.  The paper has no counterpart: this is a
+   service for callers that cannot allocate GPU memory while they plan, such as a
+   vehicle control cycle that must not stall on cudaMalloc (which can synchronise
+   the device or fail under memory pressure) or software that may only use memory
+   reserved at start-up.  It does what the argmin step of mppi_plan does, on device
+   costs d_S[K] (binary64, caller-owned): *d_s_min = the lowest finite cost,
+   *d_argmin = its index (ties: lowest index; -1 if none is finite), *d_n_finite =
+   the number of finite costs (all three caller-owned device memory).  The work is
+   queued on cuda_stream (NULL: the legacy default stream); wait on it before
+   reading the outputs.
+   Its scratch is a fixed 16 KB array inside the library, reserved on every GPU that
+   loads the library until the process exits; nothing is allocated per call.  The
+   first call on a device looks up that array's device address (once per device,
+   with the device current): make that first call before any stream capture.  All
+   calls on a device share the array, so calls that may overlap on the GPU (on
+   different streams without ordering) race; serialise them.
+   Errors are returned as status codes only (no message is stored, since storing
+   one could allocate): MPPI_ERR_ARG for NULL pointers or K < 1, MPPI_ERR_CAPACITY
+   for K > MPPI_NOALLOC_MAX_K, MPPI_ERR_CUDA when a CUDA call fails. */
+#define MPPI_NOALLOC_MAX_K (1 << 28)
+int mppi_argmin_noalloc(const double* d_S, int32_t K, double* d_s_min, int32_t* d_argmin,
+                        int32_t* d_n_finite, void* cuda_stream);
+
 const char* mppi_status_string(int status);
 const char* mppi_last_error(mppi_ctx* ctx);
 

@@ -86,6 +86,7 @@ SIGNATURES = {
     "mppi_philox": (C.c_int, [C.c_uint64, _U32P, C.c_int32, _U32P]),
     "mppi_set_profiling": (C.c_int, [_VP, C.c_int32]),
     "mppi_kernel_times": (C.c_int, [_VP, _FP, C.c_int32]),
+    "mppi_argmin_noalloc": (C.c_int, [_VP, C.c_int32, _VP, _VP, _VP, _VP]),
     "mppi_status_string": (C.c_char_p, [C.c_int]),
     "mppi_last_error": (C.c_char_p, [_VP]),
 }
