@@ -92,7 +92,7 @@ typedef struct {
     uint64_t seed;              /* Philox key */
     uint32_t session;           /* Philox counter word 3: independent streams per session */
     int32_t group;              /* lanes per sample in the rollout kernel: 0 = choose, else 1,2,4,8,16,32 */
-    int32_t block;              /* threads per block of the rollout kernel: 0 = choose, else 64, 128, 256 */
+    int32_t block;              /* threads per block of the rollout kernel: 0 = choose, else a multiple of 32 up to 512 */
 } mppi_params;
 
 /* Results of one iteration. */
@@ -148,7 +148,8 @@ int mppi_plan_device(mppi_ctx* ctx, const double* d_x0, const double* d_ref_xy, 
                      double* d_u_out, double* d_x_out, mppi_info* info);
 
 /* Autotuner: times the rollout kernel for every lanes-per-sample group (1..32) and
-   block size (64, 128, 256) on the given inputs (host arrays, as for mppi_plan) and
+   block size (64, 128, 256, and sizes that spread the lanes evenly over the SMs with
+   1 to 4 resident blocks each) on the given inputs (host arrays, as for mppi_plan) and
    keeps the fastest for this context; *group and *block receive the choice (either
    may be NULL).  The warm start and the iteration counter are not changed.  With a
    cache_path (may be NULL) the choice is looked up first and stored after tuning,
@@ -157,6 +158,18 @@ int mppi_plan_device(mppi_ctx* ctx, const double* d_x0, const double* d_ref_xy, 
 int mppi_autotune(mppi_ctx* ctx, const double* x0, const double* ref_xy, int32_t n_ref,
                   const mppi_circle* circ, int32_t n_circ, const double* centres,
                   const char* cache_path, int32_t* group, int32_t* block);
+
+/* Work counters of the rollout kernel's pruned searches for one iteration on the given
+   inputs (host arrays, as for mppi_plan), summed over all samples and steps, in this
+   order: level-2 boxes tested, level-1 boxes tested, segments evaluated, binary64
+   near-tie refinements, circles tested by the broad phase, candidate circles
+   evaluated, (ego, obstacle) pairs inside the safety band.  Divide by K*T for
+   per-rollout-step figures.  Runs an instrumented copy of the rollout kernel; the
+   warm start and the iteration counter are not changed. */
+#define MPPI_N_STATS 7
+int mppi_rollout_stats(mppi_ctx* ctx, const double* x0, const double* ref_xy, int32_t n_ref,
+                       const mppi_circle* circ, int32_t n_circ, const double* centres,
+                       uint64_t* counters);
 
 /* Waits for the context's queued work and returns the status of the last iteration. */
 int mppi_sync(mppi_ctx* ctx, mppi_info* info);

@@ -77,6 +77,7 @@ SIGNATURES = {
     "mppi_plan": (C.c_int, [_VP, _DP, _DP, C.c_int32, _DP, C.c_int32, _DP, _DP, _DP, C.POINTER(MppiInfo)]),
     "mppi_plan_device": (C.c_int, [_VP, _VP, _VP, C.c_int32, _VP, C.c_int32, _VP, _VP, _VP, C.POINTER(MppiInfo)]),
     "mppi_sync": (C.c_int, [_VP, C.POINTER(MppiInfo)]),
+    "mppi_rollout_stats": (C.c_int, [_VP, _DP, _DP, C.c_int32, _DP, C.c_int32, _DP, C.POINTER(C.c_uint64)]),
     "mppi_autotune": (C.c_int, [_VP, _DP, _DP, C.c_int32, _DP, C.c_int32, _DP, C.c_char_p,
                                 C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "mppi_set_controls": (C.c_int, [_VP, _DP, C.c_uint64]),
@@ -227,6 +228,22 @@ class Planner:
                                  C.byref(g), C.byref(b))
         _check(rc, self._h)
         return g.value, b.value
+
+    STAT_NAMES = ("l2_boxes", "l1_boxes", "segments", "refinements", "circles_tested", "candidates",
+                  "pairs_in_band")
+
+    def rollout_stats(self, x0, ref, circles=None, centres=None) -> Dict[str, float]:
+        """Work counters of the pruned searches, per rollout-step."""
+        x0 = _f64(x0)
+        ref = _f64(ref).reshape(-1, 2)
+        circ = _f64(np.zeros((0, 5)) if circles is None else circles).reshape(-1, 5)
+        cen = None if centres is None else _f64(centres)
+        out = (C.c_uint64 * len(self.STAT_NAMES))()
+        rc = lib().mppi_rollout_stats(self._h, _dp(x0), _dp(ref), ref.shape[0], _dp(circ) if circ.shape[0] else None,
+                                      circ.shape[0], _dp(cen), out)
+        _check(rc, self._h)
+        steps = float(self.K) * float(self.T)
+        return {n: out[i] / steps for i, n in enumerate(self.STAT_NAMES)}
 
     def sync(self) -> Dict[str, object]:
         info = MppiInfo()

@@ -87,8 +87,8 @@ static int check_params(const mppi_params* p, std::string& why) {
         why = "group must be 0, 1, 2, 4, 8, 16 or 32";
         return MPPI_ERR_ARG;
     }
-    if (!(p->block == 0 || p->block == 64 || p->block == 128 || p->block == 256)) {
-        why = "block must be 0, 64, 128 or 256";
+    if (!(p->block == 0 || (p->block >= 32 && p->block <= 512 && p->block % 32 == 0))) {
+        why = "block must be 0 or a multiple of 32 in [32, 512]";
         return MPPI_ERR_ARG;
     }
     return MPPI_OK;
@@ -167,7 +167,7 @@ static PlanConst make_const(const mppi_params& p) {
 static void free_all(mppi_ctx* c) {
     PlanBuffers& b = c->b;
     void* dev[] = {b.state, b.scene, b.table, b.z, b.S, b.w, b.eta_part, b.min_part, b.min_idx_part,
-                   b.min_cnt_part, b.du_part, b.U, c->d_in, c->d_out};
+                   b.min_cnt_part, b.du_part, b.U, b.stats, c->d_in, c->d_out};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_in) cudaFreeHost(c->h_in);
@@ -275,6 +275,7 @@ int mppi_create(const mppi_params* params, int device, void* cuda_stream, int32_
         {(void**)&b.min_cnt_part, sizeof(int) * b.n_mblk},
         {(void**)&b.du_part, sizeof(double) * 2 * (size_t)T * b.n_kt},
         {(void**)&b.U, sizeof(double) * 2 * (size_t)T},
+        {(void**)&b.stats, sizeof(unsigned long long) * 8},
         {(void**)&c->d_in, sizeof(double) * c->in_elems},
         {(void**)&c->d_out, sizeof(double) * c->out_elems},
     };
@@ -506,25 +507,44 @@ int mppi_autotune(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n
         CK(cudaEventCreate(&e1), "cudaEventCreate");
         float best = INFINITY;
         int bg = c->group, bt = c->threads;
+        int n_sm = 0;
+        CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
+        const size_t smem = rollout_smem_bytes(L);
         const int groups[] = {1, 2, 4, 8, 16, 32};
-        const int blocks[] = {64, 128, 256};
         cudaError_t err = cudaSuccess;
         for (int gi = 0; gi < 6 && err == cudaSuccess; ++gi) {
-            for (int bi = 0; bi < 3 && err == cudaSuccess; ++bi) {
-                const long long lanes = (long long)c->p.K * groups[gi];
-                if (groups[gi] > 1 && lanes > 4LL * 152 * 2048) continue;   // far more lanes than the GPU holds
-                err = launch_rollout(pc, L, c->b, groups[gi], blocks[bi], c->p.noise_bf16, c->stream);  // warm-up
+            const int G = groups[gi];
+            const long long lanes = (long long)c->p.K * G;
+            if (G > 1 && lanes > 4LL * n_sm * 2048) continue;   // far more lanes than the GPU holds
+            // candidate block sizes: fixed ones, and "balanced" ones that give every SM the same
+            // number of lanes when m blocks per SM are resident together
+            int cand[8], nc = 0;
+            cand[nc++] = 64;
+            cand[nc++] = 128;
+            cand[nc++] = 256;
+            for (int m = 1; m <= 4; ++m) {
+                long long per = (lanes + (long long)n_sm * m - 1) / ((long long)n_sm * m);
+                int th = (int)(((per + 31) / 32) * 32);
+                if (th < 32 || th > 512) continue;
+                if (rollout_max_blocks_per_sm(G, th, c->p.noise_bf16, smem) < m) continue;
+                bool dup = false;
+                for (int i = 0; i < nc; ++i) dup |= cand[i] == th;
+                if (!dup) cand[nc++] = th;
+            }
+            for (int bi = 0; bi < nc && err == cudaSuccess; ++bi) {
+                if (rollout_max_blocks_per_sm(G, cand[bi], c->p.noise_bf16, smem) < 1) continue;
+                err = launch_rollout(pc, L, c->b, G, cand[bi], c->p.noise_bf16, c->stream);  // warm-up
                 if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
                 for (int r = 0; r < 3 && err == cudaSuccess; ++r)
-                    err = launch_rollout(pc, L, c->b, groups[gi], blocks[bi], c->p.noise_bf16, c->stream);
+                    err = launch_rollout(pc, L, c->b, G, cand[bi], c->p.noise_bf16, c->stream);
                 if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
                 if (err == cudaSuccess) err = cudaEventSynchronize(e1);
                 float ms = 0.0f;
                 if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
                 if (err == cudaSuccess && ms < best) {
                     best = ms;
-                    bg = groups[gi];
-                    bt = blocks[bi];
+                    bg = G;
+                    bt = cand[bi];
                 }
             }
         }
@@ -539,6 +559,26 @@ int mppi_autotune(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n
     }
     if (group) *group = c->group;
     if (block) *block = c->threads;
+    return MPPI_OK;
+}
+
+int mppi_rollout_stats(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n_ref, const mppi_circle* circ,
+                       int32_t n_circ, const double* centres, uint64_t* counters) {
+    if (!c || !counters) return fail(c, MPPI_ERR_ARG, "NULL argument");
+    PlanInputs in;
+    int rc = stage_host_inputs(c, x0, ref_xy, n_ref, circ, n_circ, centres, in);
+    if (rc != MPPI_OK) return rc;
+    const SceneLayout L = make_layout(c->p.T, n_ref, n_circ);
+    PlanConst pc = c->pc;
+    pc.has_table = in.centres ? 1 : 0;
+    CK(cudaMemsetAsync(c->b.stats, 0, sizeof(unsigned long long) * 8, c->stream), "stats reset");
+    CK(launch_prep_noise(pc, L, c->b, in, c->p.noise_bf16, c->stream), "prep/noise launch");
+    CK(launch_rollout_stats(pc, L, c->b, c->p.noise_bf16, c->stream), "rollout launch");
+    CK(launch_reset_state(c->b.state, c->stream), "state reset");
+    unsigned long long h[8] = {};
+    CK(cudaMemcpyAsync(h, c->b.stats, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "stats copy");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    for (int i = 0; i < MPPI_N_STATS; ++i) counters[i] = h[i];
     return MPPI_OK;
 }
 

@@ -134,21 +134,14 @@ __device__ __forceinline__ float wrap_pi(float d) {
     return fmaf(-6.283185307179586f, k, d);
 }
 
-// Squared distance from p to segment (a, b = next vertex), the closest point being an
-// endpoint exactly when the projection parameter leaves (0, 1).  seg = (ex, ey, 1/|e|^2, heading).
-__device__ __forceinline__ float seg_dist2(float px, float py, float2 a, float2 b, float4 seg) {
+// Squared distance from p to the segment from a along e, s = (ex, ey, ex/|e|^2, ey/|e|^2):
+// the projection parameter is clamped to [0, 1] and d = (p - a) - tau e.  (Whether the
+// clamped end equals the next vertex bit for bit does not matter here: ties between two
+// segments that share a vertex are settled in binary64, see nearest_segment.)
+__device__ __forceinline__ float seg_dist2(float px, float py, float2 a, float4 s) {
     const float dax = px - a.x, day = py - a.y;
-    const float tau = fmaf(dax, seg.x, day * seg.y) * seg.z;
-    float qx, qy;
-    if (tau <= 0.0f) {
-        qx = a.x; qy = a.y;
-    } else if (tau >= 1.0f) {
-        qx = b.x; qy = b.y;
-    } else {
-        qx = fmaf(tau, seg.x, a.x);
-        qy = fmaf(tau, seg.y, a.y);
-    }
-    const float dx = px - qx, dy = py - qy;
+    const float tau = __saturatef(fmaf(dax, s.z, day * s.w));
+    const float dx = fmaf(-tau, s.x, dax), dy = fmaf(-tau, s.y, day);
     return fmaf(dx, dx, dy * dy);
 }
 

@@ -31,7 +31,8 @@ struct SceneLayout {
     int off_ctl;     // float4 [T]       (u_a, u_d, g_a, g_d): nominal controls and control-cost slopes
     int off_c0;      // float  [T]       1/2 u^T R u
     int off_vert;    // float2 [n_ref]   vertices, local frame
-    int off_seg;     // float4 [n_seg]   (ex, ey, 1/|e|^2, heading)
+    int off_seg;     // float4 [n_seg]   (ex, ey, ex/|e|^2, ey/|e|^2)
+    int off_head;    // float  [n_seg]   heading of each segment
     int off_l1;      // float4 [n_l1]    level-1 chunk boxes
     int off_l2;      // float4 [n_l2]    level-2 group boxes
     int off_circ;    // float4 [n_circ]  (x, y, r, (d_safe_0 + r + r_ego)^2 when d_safe is constant)
@@ -78,6 +79,7 @@ struct PlanBuffers {
     int* min_cnt_part;       // [n_mblk]
     double* du_part;         // [n_kt][T][2]
     double* U;               // [T][2] nominal controls (the warm start)
+    unsigned long long* stats;  // [7] work counters (STATS launches only)
     int n_mblk, n_wblk, n_kt, n_tt, kt_size;
 };
 
@@ -111,6 +113,13 @@ cudaError_t launch_philox(uint2 key, const uint4* ctr, uint4* out, int n, cudaSt
 cudaError_t launch_rollout(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int group,
                            int threads, int noise_bf16, cudaStream_t st);
 
+// Rollout with work counters (1 lane per sample): accumulates into b.stats.
+cudaError_t launch_rollout_stats(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int noise_bf16,
+                                 cudaStream_t st);
+
 size_t rollout_smem_bytes(const SceneLayout& L);
+
+// Resident rollout blocks per SM for a launch shape (0 if it cannot launch).
+int rollout_max_blocks_per_sm(int group, int threads, int noise_bf16, size_t smem);
 
 }  // namespace mppi

@@ -29,6 +29,7 @@ SceneLayout make_layout(int T, int n_ref, int n_circ) {
     L.off_c0 = o;   o = align16(o + 4 * T);
     L.off_vert = o; o = align16(o + 8 * n_ref);
     L.off_seg = o;  o = align16(o + 16 * L.n_seg);
+    L.off_head = o; o = align16(o + 4 * L.n_seg);
     L.off_l1 = o;   o = align16(o + 16 * L.n_l1);
     L.off_l2 = o;   o = align16(o + 16 * L.n_l2);
     L.off_circ = o; o = align16(o + 16 * n_circ);
@@ -53,8 +54,12 @@ __device__ __forceinline__ float4 seg_record(const double* ref, int i, double ox
     const float ex = b.x - a.x, ey = b.y - a.y;
     const float l2 = fmaf(ex, ex, ey * ey);
     const float inv = l2 > 0.0f ? 1.0f / l2 : 0.0f;
+    return make_float4(ex, ey, ex * inv, ey * inv);
+}
+
+__device__ __forceinline__ float seg_heading(const double* ref, int i) {
     const double hx = ref[2 * i + 2] - ref[2 * i], hy = ref[2 * i + 3] - ref[2 * i + 1];
-    return make_float4(ex, ey, inv, (float)atan2(hy, hx));
+    return (float)atan2(hy, hx);
 }
 
 __device__ __forceinline__ float4 vertex_box(const double* ref, int v0, int v1, double ox, double oy) {
@@ -74,6 +79,7 @@ __global__ void __launch_bounds__(256) prep_kernel(PlanConst pc, SceneLayout L, 
     float* c0 = reinterpret_cast<float*>(sc + L.off_c0);
     float2* vert = reinterpret_cast<float2*>(sc + L.off_vert);
     float4* seg = reinterpret_cast<float4*>(sc + L.off_seg);
+    float* head = reinterpret_cast<float*>(sc + L.off_head);
     float4* l1 = reinterpret_cast<float4*>(sc + L.off_l1);
     float4* l2 = reinterpret_cast<float4*>(sc + L.off_l2);
     float4* circ = reinterpret_cast<float4*>(sc + L.off_circ);
@@ -98,9 +104,10 @@ __global__ void __launch_bounds__(256) prep_kernel(PlanConst pc, SceneLayout L, 
     for (int i = tid; i < L.n_seg; i += nth) {
         const float4 s = seg_record(in.ref, i, ox, oy);
         seg[i] = s;
+        head[i] = seg_heading(in.ref, i);
         // closest segment (or vertex) to x0 itself: the rollouts' first warm start
-        const float2 a = local_vertex(in.ref, i, ox, oy), bv = local_vertex(in.ref, i + 1, ox, oy);
-        const float d2 = pc.ref_mode == 0 ? seg_dist2(0.0f, 0.0f, a, bv, s) : fmaf(a.x, a.x, a.y * a.y);
+        const float2 a = local_vertex(in.ref, i, ox, oy);
+        const float d2 = pc.ref_mode == 0 ? seg_dist2(0.0f, 0.0f, a, s) : fmaf(a.x, a.x, a.y * a.y);
         const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)i;
         atomicMin(&b.state->jkey, key);
     }
@@ -228,18 +235,6 @@ __device__ __forceinline__ unsigned group_mask() {
     }
 }
 
-template <int G>
-__device__ __forceinline__ void group_argmin(float& d2, int& idx, unsigned mask) {
-#pragma unroll
-    for (int o = G / 2; o >= 1; o >>= 1) {
-        const float od = __shfl_xor_sync(mask, d2, o, G);
-        const int oi = __shfl_xor_sync(mask, idx, o, G);
-        if (od < d2 || (od == d2 && oi < idx)) {
-            d2 = od;
-            idx = oi;
-        }
-    }
-}
 
 template <int G>
 __device__ __forceinline__ float group_min(float v, unsigned mask) {
@@ -253,64 +248,121 @@ __device__ __forceinline__ float group_min(float v, unsigned mask) {
 // far (with a relative slack far above binary32 rounding), so no segment that can be
 // the closest is missed.  The scan keeps the two best distinct segments; when their
 // binary32 distances are within 4e-6 relative, the pair is re-ordered in binary64.
-struct Best2 {
-    float b2, c2;
-    int bi, ci;
+// Work done by the pruned searches of one lane (only counted in the STATS instantiation).
+struct Counters {
+    unsigned l2, l1, seg, refine, circ, cand, pair;
 };
 
-__device__ __forceinline__ bool better(float d, int i, float e, int j) { return d < e || (d == e && i < j); }
-
-__device__ __forceinline__ void best2_insert(Best2& r, float d, int i) {
-    if (i == r.bi) return;
-    if (better(d, i, r.b2, r.bi)) {
-        r.c2 = r.b2;
-        r.ci = r.bi;
-        r.b2 = d;
-        r.bi = i;
-    } else if (i != r.ci && better(d, i, r.c2, r.ci)) {
-        r.c2 = d;
-        r.ci = i;
-    }
+// (squared distance, index) as one ordered 64-bit key: the minimum key is the smallest
+// distance and, among equal distances, the lowest index.
+__device__ __forceinline__ unsigned long long dkey(float d2, int i) {
+    return ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)i;
 }
 
 template <int G>
-__device__ __forceinline__ void group_best2(Best2& r, unsigned mask) {
+__device__ __forceinline__ unsigned long long group_min_key(unsigned long long k, unsigned mask) {
 #pragma unroll
     for (int o = G / 2; o >= 1; o >>= 1) {
-        const float ob = __shfl_xor_sync(mask, r.b2, o, G), oc = __shfl_xor_sync(mask, r.c2, o, G);
-        const int obi = __shfl_xor_sync(mask, r.bi, o, G), oci = __shfl_xor_sync(mask, r.ci, o, G);
-        best2_insert(r, ob, obi);
-        if (oci >= 0) best2_insert(r, oc, oci);
+        const unsigned long long ok = __shfl_xor_sync(mask, k, o, G);
+        k = ok < k ? ok : k;
+    }
+    return k;
+}
+
+// One level-1 chunk; the lanes of a group split its REF_L1 segments.
+template <int G, bool STATS>
+__device__ __forceinline__ void scan_chunk(float px, float py, const float2* vert, const float4* seg, int c,
+                                           int n_seg, int lane_g, unsigned long long& best, Counters& cnt) {
+    constexpr int PER = (REF_L1 + G - 1) / G;
+    const int i0 = c * REF_L1;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int o = lane_g + q * G;
+        const int i = i0 + o;
+        if (o < REF_L1 && i < n_seg) {
+            if (STATS) cnt.seg++;
+            const unsigned long long k = dkey(seg_dist2(px, py, vert[i], seg[i]), i);
+            best = k < best ? k : best;
+        }
     }
 }
 
-template <int G>
+// Closest point of the polyline (ties -> lowest segment).  The chunk of the previous
+// step's segment is scanned first; the two-level boxes then skip every chunk whose lower
+// bound exceeds the best distance (with a relative slack far above binary32 rounding), so
+// no segment that can be the closest is missed.  Two segments that share a vertex can be
+// closer than binary32 resolves (next to the vertex on the outside of a bend their
+// distances differ by a second-order term): the winner's neighbours of another heading are
+// re-ordered against it in binary64 when their binary32 distances are within 4e-6.
+template <int G, bool STATS>
 __device__ __forceinline__ void nearest_segment(float px, float py, const float2* vert, const float4* seg,
-                                                const float4* l1, const float4* l2, int n_seg, int n_l1,
-                                                int n_l2, int lane_g, unsigned mask, int& jb, float& best2) {
+                                                const float* head, const float4* l1, const float4* l2, int n_seg,
+                                                int n_l1, int n_l2, int lane_g, unsigned mask, int& jb,
+                                                float& best2, Counters& cnt) {
     constexpr float SLACK = 1.0f + 1.0f / 1024.0f;
-    Best2 r{seg_dist2(px, py, vert[jb], vert[jb + 1], seg[jb]), INFINITY, jb, -1};
-    for (int g = 0; g < n_l2; ++g) {
-        if (box_dist2(px, py, l2[g]) > r.b2 * SLACK) continue;
-        const int c1 = min((g + 1) * REF_L2, n_l1);
-        for (int c = g * REF_L2; c < c1; ++c) {
-            if (box_dist2(px, py, l1[c]) > r.b2 * SLACK) continue;
-            const int i1 = min((c + 1) * REF_L1, n_seg);
-            for (int i = c * REF_L1 + lane_g; i < i1; i += G)
-                best2_insert(r, seg_dist2(px, py, vert[i], vert[i + 1], seg[i]), i);
-            group_best2<G>(r, mask);
+    const int cw = jb / REF_L1;
+    unsigned long long best = ~0ull;
+    scan_chunk<G, STATS>(px, py, vert, seg, cw, n_seg, lane_g, best, cnt);
+    best = group_min_key<G>(best, mask);
+    float b2 = __uint_as_float((unsigned)(best >> 32));
+#pragma unroll 1
+    for (int g0 = 0; g0 < n_l2; g0 += 8) {
+        unsigned m2 = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (g0 + q < n_l2 && box_dist2(px, py, l2[g0 + q]) <= b2 * SLACK) m2 |= 1u << q;
+        if (STATS) cnt.l2 += min(8, n_l2 - g0);
+        while (m2) {
+            const int c0 = (g0 + __ffs(m2) - 1) * REF_L2;
+            m2 &= m2 - 1;
+            unsigned m1 = 0;
+#pragma unroll
+            for (int j = 0; j < REF_L2; ++j)
+                if (c0 + j < n_l1 && c0 + j != cw && box_dist2(px, py, l1[c0 + j]) <= b2 * SLACK) m1 |= 1u << j;
+            if (STATS) cnt.l1 += min(REF_L2, n_l1 - c0);
+            while (m1) {
+                const int c = c0 + __ffs(m1) - 1;
+                m1 &= m1 - 1;
+                if (box_dist2(px, py, l1[c]) > b2 * SLACK) continue;   // the bound may have tightened
+                scan_chunk<G, STATS>(px, py, vert, seg, c, n_seg, lane_g, best, cnt);
+                best = group_min_key<G>(best, mask);
+                b2 = __uint_as_float((unsigned)(best >> 32));
+            }
         }
     }
-    if (r.ci >= 0 && r.c2 - r.b2 <= 4e-6f * r.b2 + 1e-20f && seg[r.bi].w != seg[r.ci].w) {
-        const double db = seg_dist2_f64(px, py, vert[r.bi], vert[r.bi + 1]);
-        const double dc = seg_dist2_f64(px, py, vert[r.ci], vert[r.ci + 1]);
-        if (dc < db || (dc == db && r.ci < r.bi)) {
-            r.bi = r.ci;
-            r.b2 = r.c2;
+    int bi = (int)(best & 0xffffffffu);
+    const int b0 = bi;
+    const float hb = head[b0];
+#pragma unroll
+    for (int dlt = -1; dlt <= 1; dlt += 2) {
+        const int j = b0 + dlt;
+        if (j < 0 || j >= n_seg || head[j] == hb) continue;
+        const float dj = seg_dist2(px, py, vert[j], seg[j]);
+        if (fabsf(dj - b2) <= 4e-6f * b2 + 1e-20f) {
+            if (STATS) cnt.refine++;
+            const double db = seg_dist2_f64(px, py, vert[bi], vert[bi + 1]);
+            const double dd = seg_dist2_f64(px, py, vert[j], vert[j + 1]);
+            if (dd < db || (dd == db && j < bi)) {
+                bi = j;
+                b2 = dj;
+            }
         }
     }
-    jb = r.bi;
-    best2 = r.b2;
+    jb = bi;
+    best2 = b2;
+}
+
+template <int G>
+__device__ __forceinline__ void group_argmin(float& d2, int& idx, unsigned mask) {
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) {
+        const float od = __shfl_xor_sync(mask, d2, o, G);
+        const int oi = __shfl_xor_sync(mask, idx, o, G);
+        if (od < d2 || (od == d2 && oi < idx)) {
+            d2 = od;
+            idx = oi;
+        }
+    }
 }
 
 // Closest vertex (ties -> lowest index), same hierarchy (chunk c covers vertices c*L1 .. c*L1+L1).
@@ -379,11 +431,11 @@ __device__ __forceinline__ float warp_max_f(float v) {
 // circles that pass (ballot) get the exact per-pair test.  A circle is skipped only
 // when no ego circle of the warp can come within the band of it, so the result equals
 // the brute-force minimum over all in-band pairs.
-template <int G>
+template <int G, bool STATS>
 __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4* circ, const float2* vel,
                                               const float2* table, int n_circ, int t, bool has_table, bool moving,
                                               bool dconst, float nx, float ny, float cnth, float snth, float mband,
-                                              int lane, int lane_g, unsigned mask) {
+                                              int lane, int lane_g, unsigned mask, Counters& cnt) {
     float ex[8], ey[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -403,6 +455,7 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4*
         const int kc = base + lane;
         bool hit = false;
         if (kc < n_circ) {
+            if (STATS) cnt.circ++;
             const float2 cc = circle_centre(circ, vel, table, n_circ, t, kc, st, has_table, moving);
             const float lim = (mmax + circ[kc].z + pc.ego_rmax) * 1.0001f + 1e-4f;
             const float dx = fmaxf(fmaxf(bx0 - cc.x, cc.x - bx1), 0.0f);
@@ -414,6 +467,7 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4*
             const int bit = __ffs(m) - 1;
             m &= m - 1;
             if ((j & (G - 1)) != lane_g) continue;
+            if (STATS) cnt.cand++;
             const int kc2 = base + bit;
             const float4 c = circ[kc2];
             const float2 cc = circle_centre(circ, vel, table, n_circ, t, kc2, st, has_table, moving);
@@ -423,7 +477,10 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4*
                     if (e >= pc.n_ego) break;
                     const float dx = ex[e] - cc.x, dy = ey[e] - cc.y;
                     const float d2 = fmaf(dx, dx, dy * dy);
-                    if (d2 <= c.w) dobj = fminf(dobj, sqrtf(d2) - (c.z + pc.ego_rad[e]));
+                    if (d2 <= c.w) {
+                        if (STATS) cnt.pair++;
+                        dobj = fminf(dobj, sqrtf(d2) - (c.z + pc.ego_rad[e]));
+                    }
                 }
             } else {
 #pragma unroll
@@ -433,7 +490,10 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4*
                     const float lim = mband + R;
                     const float dx = ex[e] - cc.x, dy = ey[e] - cc.y;
                     const float d2 = fmaf(dx, dx, dy * dy);
-                    if (lim > 0.0f && d2 <= lim * lim) dobj = fminf(dobj, sqrtf(d2) - R);
+                    if (lim > 0.0f && d2 <= lim * lim) {
+                        if (STATS) cnt.pair++;
+                        dobj = fminf(dobj, sqrtf(d2) - R);
+                    }
                 }
             }
         }
@@ -441,8 +501,8 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4*
     return group_min<G>(dobj, mask);
 }
 
-template <int G, bool BF16>
-__global__ void __launch_bounds__(256) rollout_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
+template <int G, bool BF16, bool STATS>
+__global__ void __launch_bounds__(512, 1) rollout_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
                                                       const typename NoiseT<BF16>::type* __restrict__ z) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long bar;
@@ -452,6 +512,7 @@ __global__ void __launch_bounds__(256) rollout_kernel(PlanConst pc, SceneLayout 
     const float* c0 = reinterpret_cast<const float*>(smem + L.off_c0);
     const float2* vert = reinterpret_cast<const float2*>(smem + L.off_vert);
     const float4* seg = reinterpret_cast<const float4*>(smem + L.off_seg);
+    const float* head = reinterpret_cast<const float*>(smem + L.off_head);
     const float4* l1 = reinterpret_cast<const float4*>(smem + L.off_l1);
     const float4* l2 = reinterpret_cast<const float4*>(smem + L.off_l2);
     const float4* circ = reinterpret_cast<const float4*>(smem + L.off_circ);
@@ -478,6 +539,7 @@ __global__ void __launch_bounds__(256) rollout_kernel(PlanConst pc, SceneLayout 
     float tdp = fmaf(tp.x, tp.x, tp.y * tp.y);   // |P_0 - T_P|^2 with P_0 = (0, 0)
     int jb = (int)(b.state->jkey & 0xffffffffu);
     float s_hi = 0.0f, s_c = 0.0f, q_last = 0.0f;
+    Counters cnt{0, 0, 0, 0, 0, 0, 0};
 
     for (int t = 0; t < T; ++t) {
         const float4 ct = ctl[t];
@@ -499,17 +561,18 @@ __global__ void __launch_bounds__(256) rollout_kernel(PlanConst pc, SceneLayout 
         // Eq. (12), (14): closest waypoint (search on the binary32 position) and reference yaw
         float d2r;
         if (pc.ref_mode == 0)
-            nearest_segment<G>(nx, ny, vert, seg, l1, l2, L.n_seg, L.n_l1, L.n_l2, lane_g, mask, jb, d2r);
+            nearest_segment<G, STATS>(nx, ny, vert, seg, head, l1, l2, L.n_seg, L.n_l1, L.n_l2, lane_g, mask, jb,
+                                      d2r, cnt);
         else
             nearest_vertex<G>(nx, ny, vert, l1, l2, L.n_ref, L.n_l1, L.n_l2, lane_g, mask, jb, d2r);
-        const float thr = seg[min(jb, L.n_seg - 1)].w;
+        const float thr = head[min(jb, L.n_seg - 1)];
         {
             // c_dist on the compensated position: closest point of the winning segment or vertex
             const float2 a = vert[jb];
             float qx = a.x, qy = a.y;
             if (pc.ref_mode == 0) {
                 const float4 sg = seg[jb];
-                const float tau = fmaf(nx - a.x, sg.x, (ny - a.y) * sg.y) * sg.z;
+                const float tau = fmaf(nx - a.x, sg.z, (ny - a.y) * sg.w);
                 if (tau >= 1.0f) {
                     qx = vert[jb + 1].x;
                     qy = vert[jb + 1].y;
@@ -534,8 +597,8 @@ __global__ void __launch_bounds__(256) rollout_kernel(PlanConst pc, SceneLayout 
         const float mband = pc.collision_only ? fmaxf(ds, 0.0f) : ds;
         float dobj = INFINITY;
         if (L.n_circ > 0)
-            dobj = obstacle_min<G>(pc, circ, vel, b.table, L.n_circ, t, has_table, moving, dconst, nx, ny, cnth,
-                                   snth, mband, lane, lane_g, mask);
+            dobj = obstacle_min<G, STATS>(pc, circ, vel, b.table, L.n_circ, t, has_table, moving, dconst, nx, ny,
+                                          cnth, snth, mband, lane, lane_g, mask, cnt);
         const float gap = ds - dobj;
         float c_safe = gap > 0.0f ? gap * gap : 0.0f;
         if (pc.collision_only && !(dobj <= 0.0f)) c_safe = 0.0f;
@@ -554,6 +617,10 @@ __global__ void __launch_bounds__(256) rollout_kernel(PlanConst pc, SceneLayout 
         double S = (double)s_hi - (double)s_c;
         if (pc.w_terminal != 0.0f) S += (double)pc.w_terminal * (double)q_last;
         b.S[k] = S;
+    }
+    if (STATS && k < K) {
+        const unsigned v7[7] = {cnt.l2, cnt.l1, cnt.seg, cnt.refine, cnt.circ, cnt.cand, cnt.pair};
+        for (int i = 0; i < 7; ++i) atomicAdd(b.stats + i, (unsigned long long)v7[i]);
     }
 }
 
@@ -888,20 +955,20 @@ __global__ void __launch_bounds__(1024) finalize_kernel(PlanConst pc, PlanBuffer
 // -----------------------------------------------------------------------------
 // host-side launchers
 // -----------------------------------------------------------------------------
-template <int G, bool BF16>
+template <int G, bool BF16, bool STATS = false>
 static cudaError_t launch_rollout_t(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int threads,
                                     cudaStream_t st) {
     const size_t smem = rollout_smem_bytes(L);
     static int configured_smem = -1;
     if (configured_smem < (int)smem) {
-        cudaError_t e = cudaFuncSetAttribute(rollout_kernel<G, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(rollout_kernel<G, BF16, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(smem < 48 * 1024 ? 48 * 1024 : smem));
         if (e != cudaSuccess) return e;
         configured_smem = (int)(smem < 48 * 1024 ? 48 * 1024 : smem);
     }
     const long long total = (long long)pc.K * G;
     const int blocks = (int)((total + threads - 1) / threads);
-    rollout_kernel<G, BF16><<<blocks, threads, smem, st>>>(
+    rollout_kernel<G, BF16, STATS><<<blocks, threads, smem, st>>>(
         pc, L, b, reinterpret_cast<const typename NoiseT<BF16>::type*>(b.z));
     return cudaGetLastError();
 }
@@ -920,9 +987,44 @@ static cudaError_t launch_rollout_b(const PlanConst& pc, const SceneLayout& L, c
     }
 }
 
+template <int G, bool BF16>
+static int max_blocks_t(int threads, size_t smem) {
+    int n = 0;
+    if (cudaFuncSetAttribute(rollout_kernel<G, BF16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(smem < 48 * 1024 ? 48 * 1024 : smem)) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_kernel<G, BF16, false>, threads, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+int rollout_max_blocks_per_sm(int group, int threads, int noise_bf16, size_t smem) {
+    switch (group * 2 + (noise_bf16 ? 1 : 0)) {
+        case 2: return max_blocks_t<1, false>(threads, smem);
+        case 3: return max_blocks_t<1, true>(threads, smem);
+        case 4: return max_blocks_t<2, false>(threads, smem);
+        case 5: return max_blocks_t<2, true>(threads, smem);
+        case 8: return max_blocks_t<4, false>(threads, smem);
+        case 9: return max_blocks_t<4, true>(threads, smem);
+        case 16: return max_blocks_t<8, false>(threads, smem);
+        case 17: return max_blocks_t<8, true>(threads, smem);
+        case 32: return max_blocks_t<16, false>(threads, smem);
+        case 33: return max_blocks_t<16, true>(threads, smem);
+        case 64: return max_blocks_t<32, false>(threads, smem);
+        case 65: return max_blocks_t<32, true>(threads, smem);
+        default: return 0;
+    }
+}
+
+cudaError_t launch_rollout_stats(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int noise_bf16,
+                                 cudaStream_t st) {
+    return noise_bf16 ? launch_rollout_t<1, true, true>(pc, L, b, 128, st)
+                      : launch_rollout_t<1, false, true>(pc, L, b, 128, st);
+}
+
 cudaError_t launch_rollout(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int group,
                            int threads, int noise_bf16, cudaStream_t st) {
-    if (threads != 64 && threads != 128 && threads != 256) return cudaErrorInvalidValue;
+    if (threads < 32 || threads > 512 || threads % 32 != 0) return cudaErrorInvalidValue;
     return noise_bf16 ? launch_rollout_b<true>(pc, L, b, group, threads, st)
                       : launch_rollout_b<false>(pc, L, b, group, threads, st);
 }

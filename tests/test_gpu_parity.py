@@ -299,3 +299,25 @@ def test_checkpoint_resume_reproduces_the_stream():
         u2, x2, i2 = b.plan(prob.x0, prob.ref, prob.circles)
     np.testing.assert_array_equal(u1, u2)
     assert i1["iter"] == i2["iter"] == 1
+
+
+def test_rollout_stats_are_consistent_and_leave_state():
+    prob = sc.roofline()
+    prob.params.update(K=4096, T=40)
+    with mp.Planner(prob.params) as pl:
+        U0 = np.full((40, 2), 0.01)
+        pl.set_controls(U0, 3)
+        st = pl.rollout_stats(prob.x0, prob.ref, prob.circles)
+        U, it = pl.get_controls()
+        np.testing.assert_array_equal(U, U0)
+        assert it == 3
+        n_l2 = math.ceil(math.ceil((prob.ref.shape[0] - 1) / 16) / 16)
+        assert st["l2_boxes"] == pytest.approx(n_l2)            # every level-2 box is tested every step
+        assert 1 <= st["segments"] <= prob.ref.shape[0]
+        # the broad phase tests one circle per lane per 32-circle chunk
+        assert st["circles_tested"] == pytest.approx(math.ceil(prob.circles.shape[0] / 32), rel=1e-9)
+        assert st["pairs_in_band"] <= 3 * st["candidates"]
+        # the plan after the stats run still matches the oracle
+        u, x, info = pl.plan(prob.x0, prob.ref, prob.circles)
+        orc = oracle.plan(prob, U=U0, iter_=3)
+        check_iteration(prob, (u, x, info, pl.get_costs()), orc)
