@@ -41,17 +41,29 @@ KERNEL_LAUNCHES_PER_STEP = 7   # prep, noise, rollout, argmin, weights, wsum, fi
 
 # ------------------------------------------------------------------------ helpers
 
-def rollout_ops_per_step(prob) -> float:
-    """Algorithmic FP32-pipe operations per rollout-step of the fused rollout+cost kernel.
-
-    The per-step model: ~60 operations for the dynamics, the five cost terms and the
-    control cost; 6 per (ego circle, obstacle circle) pair (every pair is tested,
-    as d_obj = min over all circles defines); and the exact nearest-segment search:
-    5 per 32-segment chunk bound plus ~11 per segment of ~2 scanned chunks.
-    """
+def brute_force_ops_per_step(prob) -> float:
+    """FP32 operations per rollout-step if every obstacle pair were tested and the reference
+    scanned with 32-segment chunk bounds: ~60 for dynamics and costs, 6 per (ego, obstacle)
+    pair, 5 per chunk bound and ~11 per segment of ~2 scanned chunks."""
     p = prob.params
     n_e, n_c, n_ref = int(p["n_ego"]), int(prob.circles.shape[0]), int(prob.ref.shape[0])
     return 60.0 + 6.0 * n_e * n_c + 5.0 * math.ceil((n_ref - 1) / 32.0) + 11.0 * 64.0
+
+
+# Arithmetic (FP32/ALU pipe) operations of one unit of each piece of work the rollout
+# kernel does, counted from its source: the per-step core (perturbation, Euler step with
+# compensated sums, sincos and tan, cost terms, control cost, ego circles and the warp
+# box of the broad phase) and, per unit counted by mppi_rollout_stats, a box bound, a
+# segment distance with its key minimum, a broad-phase circle test, a candidate circle
+# (three pair distances and band tests) and an in-band pair (sqrt, subtract, min).
+OPS_CORE = 150.0
+OPS_PER = {"l2_boxes": 12.0, "l1_boxes": 12.0, "segments": 13.0, "refinements": 40.0,
+           "circles_tested": 15.0, "candidates": 17.0, "pairs_in_band": 4.0}
+
+
+def executed_ops_per_step(stats) -> float:
+    """Arithmetic operations per rollout-step of the pruned exact algorithm, from its work counters."""
+    return OPS_CORE + sum(OPS_PER[k] * stats[k] for k in OPS_PER)
 
 
 KERNEL_SOURCES = ("paper_2308_01654_gb300/csrc/mppi_kernels.cu", "paper_2308_01654_gb300/csrc/mppi_device.cuh",
@@ -218,6 +230,7 @@ def run_gpu(args, world, rank, local):
     torch.cuda.set_stream(stream)
     pl = mp.Planner(prob.params, device=local, stream=stream.cuda_stream)
     group, block = pl.autotune(prob.x0, prob.ref, prob.circles, prob.centres, cache_path=args.tune_cache)
+    work = pl.rollout_stats(prob.x0, prob.ref, prob.circles, prob.centres)     # untimed, instrumented copy
     pl.set_profiling(True)
     x0 = torch.tensor(prob.x0, dtype=torch.float64, device=dev)
     ref = torch.tensor(prob.ref, dtype=torch.float64, device=dev)
@@ -298,14 +311,18 @@ def run_gpu(args, world, rank, local):
     peaks = measured_peaks()
     f_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tops = n_sm * 128 * f_max * 1e6 / 1e12
-    ops = rollout_ops_per_step(prob) * K * T
-    achieved = ops / (ms_roll * 1e-3) / 1e12
+    ops_step = executed_ops_per_step(work)
+    achieved = ops_step * K * T / (ms_roll * 1e-3) / 1e12
+    bf_step = brute_force_ops_per_step(prob)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TOP/s",
                 "frac": achieved / peak_tops,
                 "traffic": args.traffic if args.traffic is not None else profiled_traffic(args.workload),
-                "kernel": "rollout_kernel", "ops_per_rollout_step": rollout_ops_per_step(prob),
+                "kernel": "rollout_kernel", "ops_per_rollout_step": ops_step,
+                "work_per_rollout_step": {k: round(v, 4) for k, v in work.items()},
                 "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {f_max:.0f} MHz (max SM clock)",
-                "kernel_ms": ms_roll}
+                "kernel_ms": ms_roll,
+                "brute_force_equivalent": {"ops_per_rollout_step": bf_step,
+                                           "TOPs": bf_step * K * T / (ms_roll * 1e-3) / 1e12}}
     kmean = {k: statistics.mean(d[k] for d in ktimes) for k in ktimes[0]}
 
     out = {

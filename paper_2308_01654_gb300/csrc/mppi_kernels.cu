@@ -413,17 +413,18 @@ __device__ __forceinline__ float2 circle_centre(const float4* circ, const float2
     return make_float2(fmaf(vv.x, st, c.x), fmaf(vv.y, st, c.y));
 }
 
-__device__ __forceinline__ float warp_min_f(float v) {
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+// Warp min / max of a float with one redux.sync on an order-preserving integer image
+// (non-negative floats keep their bits, negative ones have their magnitude bits flipped).
+__device__ __forceinline__ int f32_ord(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
 }
 
-__device__ __forceinline__ float warp_max_f(float v) {
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
+__device__ __forceinline__ float ord_f32(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__device__ __forceinline__ float warp_min_f(float v) { return ord_f32(__reduce_min_sync(0xffffffffu, f32_ord(v))); }
+
+__device__ __forceinline__ float warp_max_f(float v) { return ord_f32(__reduce_max_sync(0xffffffffu, f32_ord(v))); }
 
 // d_obj of Eq. (16) restricted to the pairs that can lie inside the safety band (the
 // only pairs that change c_safe), with a warp-wide broad phase: the lanes test the
