@@ -196,6 +196,57 @@ int mppi_philox(uint64_t seed, const uint32_t* ctr, int32_t n, uint32_t* out);
 int mppi_set_profiling(mppi_ctx* ctx, int32_t on);
 int mppi_kernel_times(mppi_ctx* ctx, float* ms, int32_t n);
 
+/* ------------------------------------------------------------------------------------
+   Batched planning: many independent iterations (different K, T, references, obstacles)
+   computed together by one fixed kernel sequence captured in a CUDA graph, with one
+   persistent rollout kernel over all plans' samples (the longest plans first).  Each
+   plan's warm start lives in a device slot of the batch object; a plan's result does not
+   depend on the other plans of its submission.  Several submissions may be in flight
+   (one per pipeline); the caller must not use a slot in two submissions in flight.
+   ------------------------------------------------------------------------------------ */
+typedef struct mppi_batch mppi_batch;
+
+typedef struct {
+    const mppi_params* params;  /* this plan's hyper-parameters (noise_bf16 must be the batch's) */
+    int32_t slot;               /* warm-start slot, 0 .. max_slots-1, distinct within a submission */
+    const double* x0;           /* [4] */
+    const double* ref_xy;       /* [n_ref][2] */
+    int32_t n_ref;
+    const mppi_circle* circ;    /* [n_circ] */
+    int32_t n_circ;
+    const double* centres;      /* optional [T][n_circ][2] */
+    double* u_out;              /* [T][2], written by mppi_batch_wait when status is MPPI_OK */
+    double* x_out;              /* [T+1][4] */
+    mppi_info* info;            /* optional */
+    int32_t status;             /* written by mppi_batch_wait: this plan's mppi_status */
+} mppi_request;
+
+/* Capacities: max_slots warm-start slots; at most max_batch plans, max_samples samples
+   (sum of K) and max_rollout_steps rollout steps (sum of K*T) per submission; T, n_ref and
+   n_circ of any plan up to max_T, max_ref, max_circ; pipelines = submissions that may be
+   in flight at once (1..16).  All device and pinned memory is allocated here. */
+int mppi_batch_create(int32_t max_slots, int32_t max_batch, int64_t max_samples, int64_t max_rollout_steps,
+                      int32_t max_T, int32_t max_ref, int32_t max_circ, int32_t noise_bf16, int32_t pipelines,
+                      int device, mppi_batch** out);
+int mppi_batch_destroy(mppi_batch* batch);
+
+/* Queues one iteration of each of the n plans (inputs are copied before it returns) on
+   a free pipeline and returns its ticket; MPPI_ERR_CAPACITY when every pipeline is busy.
+   mppi_batch_wait(ticket) waits and writes the outputs, status and info of every plan;
+   it returns MPPI_OK, or the status of the first failed plan.  mppi_batch_plan does both. */
+int mppi_batch_submit(mppi_batch* batch, mppi_request* req, int32_t n, int32_t* ticket);
+int mppi_batch_wait(mppi_batch* batch, int32_t ticket);
+int mppi_batch_plan(mppi_batch* batch, mppi_request* req, int32_t n);
+
+/* Times the persistent rollout kernel for every lanes-per-sample group and block size on
+   this submission's plans (without changing any slot) and keeps the fastest. */
+int mppi_batch_autotune(mppi_batch* batch, mppi_request* req, int32_t n, int32_t* group, int32_t* block);
+
+/* Warm start of one slot: U[T][2] and its iteration index (the Philox counter word 2). */
+int mppi_batch_set_controls(mppi_batch* batch, int32_t slot, const double* U, int32_t T, uint64_t iter);
+int mppi_batch_get_controls(mppi_batch* batch, int32_t slot, double* U, int32_t T, uint64_t* iter);
+const char* mppi_batch_last_error(mppi_batch* batch);
+
 /* Allocation-free lowest-cost search.  The paper has no counterpart: this is a
    service for callers that cannot allocate GPU memory while they plan, such as a
    vehicle control cycle that must not stall on cudaMalloc (which can synchronise

@@ -88,6 +88,16 @@ SIGNATURES = {
     "mppi_set_profiling": (C.c_int, [_VP, C.c_int32]),
     "mppi_kernel_times": (C.c_int, [_VP, _FP, C.c_int32]),
     "mppi_argmin_noalloc": (C.c_int, [_VP, C.c_int32, _VP, _VP, _VP, _VP]),
+    "mppi_batch_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_int32,
+                                    C.c_int32, C.c_int32, C.c_int, C.POINTER(_VP)]),
+    "mppi_batch_destroy": (C.c_int, [_VP]),
+    "mppi_batch_submit": (C.c_int, [_VP, _VP, C.c_int32, C.POINTER(C.c_int32)]),
+    "mppi_batch_wait": (C.c_int, [_VP, C.c_int32]),
+    "mppi_batch_plan": (C.c_int, [_VP, _VP, C.c_int32]),
+    "mppi_batch_autotune": (C.c_int, [_VP, _VP, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "mppi_batch_set_controls": (C.c_int, [_VP, C.c_int32, _DP, C.c_int32, C.c_uint64]),
+    "mppi_batch_get_controls": (C.c_int, [_VP, C.c_int32, _DP, C.c_int32, C.POINTER(C.c_uint64)]),
+    "mppi_batch_last_error": (C.c_char_p, [_VP]),
     "mppi_status_string": (C.c_char_p, [C.c_int]),
     "mppi_last_error": (C.c_char_p, [_VP]),
 }
@@ -307,3 +317,112 @@ def default_params(K: int, T: int, dt: float) -> MppiParams:
 
 
 INF = math.inf
+
+
+class MppiRequest(C.Structure):
+    _fields_ = [("params", C.POINTER(MppiParams)), ("slot", C.c_int32),
+                ("x0", _DP), ("ref_xy", _DP), ("n_ref", C.c_int32), ("circ", _DP), ("n_circ", C.c_int32),
+                ("centres", _DP), ("u_out", _DP), ("x_out", _DP), ("info", C.POINTER(MppiInfo)),
+                ("status", C.c_int32)]
+
+
+class BatchPlan:
+    """One plan of a batch submission: inputs, warm-start slot and output buffers (kept alive)."""
+
+    def __init__(self, params: Dict[str, object], slot: int, x0, ref, circles=None, centres=None):
+        self.params = dict(params)
+        self.slot = int(slot)
+        self.T = int(params["T"])
+        self.cparams = make_params(params)
+        self.x0 = _f64(x0)
+        self.ref = _f64(ref).reshape(-1, 2)
+        self.circ = _f64(np.zeros((0, 5)) if circles is None else circles).reshape(-1, 5)
+        self.centres = None if centres is None else _f64(centres)
+        self.u = np.zeros((self.T, 2))
+        self.x = np.zeros((self.T + 1, 4))
+        self.info = MppiInfo()
+
+    def fill(self, r: MppiRequest):
+        r.params = C.pointer(self.cparams)
+        r.slot = self.slot
+        r.x0, r.ref_xy, r.n_ref = _dp(self.x0), _dp(self.ref), self.ref.shape[0]
+        r.circ, r.n_circ = (_dp(self.circ) if self.circ.shape[0] else None), self.circ.shape[0]
+        r.centres = _dp(self.centres)
+        r.u_out, r.x_out = _dp(self.u), _dp(self.x)
+        r.info = C.pointer(self.info)
+        r.status = 0
+
+
+class BatchPlanner:
+    """Many independent plans per launch (mppi_batch_*): device warm-start slots, pipelines of
+    graph-captured kernel sequences, one persistent rollout kernel across all plans."""
+
+    def __init__(self, max_slots: int, max_batch: int, max_samples: int, max_rollout_steps: int, max_T: int,
+                 max_ref: int, max_circ: int, noise_bf16: int = 0, pipelines: int = 2, device: int = 0):
+        h = _VP()
+        rc = lib().mppi_batch_create(max_slots, max_batch, max_samples, max_rollout_steps, max_T, max_ref, max_circ,
+                                     noise_bf16, pipelines, device, C.byref(h))
+        self._check(rc, None)
+        self._h = h
+
+    def _check(self, rc, h):
+        if rc != 0:
+            msg = lib().mppi_batch_last_error(h)
+            raise MppiError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mppi_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def requests(plans):
+        arr = (MppiRequest * len(plans))()
+        for r, p in zip(arr, plans):
+            p.fill(r)
+        return arr
+
+    def submit(self, reqs) -> int:
+        t = C.c_int32()
+        self._check(lib().mppi_batch_submit(self._h, C.cast(reqs, _VP), len(reqs), C.byref(t)), self._h)
+        return t.value
+
+    def wait(self, ticket: int, check: bool = True) -> int:
+        rc = lib().mppi_batch_wait(self._h, ticket)
+        if check:
+            self._check(rc, self._h)
+        return rc
+
+    def plan(self, plans, reqs=None):
+        """One iteration of every plan; outputs land in each BatchPlan's u, x, info."""
+        reqs = self.requests(plans) if reqs is None else reqs
+        self._check(lib().mppi_batch_plan(self._h, C.cast(reqs, _VP), len(reqs)), self._h)
+        return reqs
+
+    def autotune(self, plans):
+        reqs = self.requests(plans)
+        g, b = C.c_int32(), C.c_int32()
+        self._check(lib().mppi_batch_autotune(self._h, C.cast(reqs, _VP), len(reqs), C.byref(g), C.byref(b)), self._h)
+        return g.value, b.value
+
+    def set_controls(self, slot: int, U, iter_: int = 0):
+        U = _f64(U).reshape(-1, 2)
+        self._check(lib().mppi_batch_set_controls(self._h, slot, _dp(U), U.shape[0], int(iter_)), self._h)
+
+    def get_controls(self, slot: int, T: int):
+        U = np.empty((T, 2))
+        it = C.c_uint64()
+        self._check(lib().mppi_batch_get_controls(self._h, slot, _dp(U), T, C.byref(it)), self._h)
+        return U, it.value

@@ -164,6 +164,12 @@ static PlanConst make_const(const mppi_params& p) {
     return c;
 }
 
+// Shared with the batched planner (same validation and conversion for every plan).
+namespace mppi {
+int check_params_shared(const mppi_params* p, std::string& why) { return check_params(p, why); }
+PlanConst make_const_shared(const mppi_params& p) { return make_const(p); }
+}  // namespace mppi
+
 static void free_all(mppi_ctx* c) {
     PlanBuffers& b = c->b;
     void* dev[] = {b.state, b.scene, b.table, b.z, b.S, b.w, b.eta_part, b.min_part, b.min_idx_part,

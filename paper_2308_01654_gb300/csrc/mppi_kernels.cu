@@ -11,6 +11,7 @@
 
 #include "mppi_device.cuh"
 #include "mppi_internal.h"
+#include "mppi_iter.cuh"
 
 namespace mppi {
 
@@ -45,122 +46,13 @@ size_t rollout_smem_bytes(const SceneLayout& L) { return (size_t)L.bytes; }
 // (x0, y0) in binary64 before rounding, so binary32 keeps its resolution where
 // the rollouts happen.
 // -----------------------------------------------------------------------------
-__device__ __forceinline__ float2 local_vertex(const double* ref, int i, double ox, double oy) {
-    return make_float2((float)(ref[2 * i] - ox), (float)(ref[2 * i + 1] - oy));
-}
-
-__device__ __forceinline__ float4 seg_record(const double* ref, int i, double ox, double oy) {
-    const float2 a = local_vertex(ref, i, ox, oy), b = local_vertex(ref, i + 1, ox, oy);
-    const float ex = b.x - a.x, ey = b.y - a.y;
-    const float l2 = fmaf(ex, ex, ey * ey);
-    const float inv = l2 > 0.0f ? 1.0f / l2 : 0.0f;
-    return make_float4(ex, ey, ex * inv, ey * inv);
-}
-
-__device__ __forceinline__ float seg_heading(const double* ref, int i) {
-    const double hx = ref[2 * i + 2] - ref[2 * i], hy = ref[2 * i + 3] - ref[2 * i + 1];
-    return (float)atan2(hy, hx);
-}
-
-__device__ __forceinline__ float4 vertex_box(const double* ref, int v0, int v1, double ox, double oy) {
-    float4 bb = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
-    for (int j = v0; j <= v1; ++j) {
-        const float2 p = local_vertex(ref, j, ox, oy);
-        bb.x = fminf(bb.x, p.x); bb.y = fminf(bb.y, p.y);
-        bb.z = fmaxf(bb.z, p.x); bb.w = fmaxf(bb.w, p.y);
-    }
-    return bb;
-}
-
 __global__ void __launch_bounds__(256) prep_kernel(PlanConst pc, SceneLayout L, PlanInputs in, PlanBuffers b) {
-    const double ox = in.x0[0], oy = in.x0[1];
-    unsigned char* sc = b.scene;
-    float4* ctl = reinterpret_cast<float4*>(sc + L.off_ctl);
-    float* c0 = reinterpret_cast<float*>(sc + L.off_c0);
-    float2* vert = reinterpret_cast<float2*>(sc + L.off_vert);
-    float4* seg = reinterpret_cast<float4*>(sc + L.off_seg);
-    float* head = reinterpret_cast<float*>(sc + L.off_head);
-    float4* l1 = reinterpret_cast<float4*>(sc + L.off_l1);
-    float4* l2 = reinterpret_cast<float4*>(sc + L.off_l2);
-    float4* circ = reinterpret_cast<float4*>(sc + L.off_circ);
-    float2* vel = reinterpret_cast<float2*>(sc + L.off_vel);
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nth = gridDim.x * blockDim.x;
-    bool bad = false;
-
-    if (tid == 0) {
-        for (int i = 0; i < 4; ++i) bad |= !isfinite(in.x0[i]);
-        b.state->x0f = make_float4(0.0f, 0.0f, (float)in.x0[2], (float)in.x0[3]);
-    }
-    for (int t = tid; t < L.T; t += nth) {
-        const double ua = b.U[2 * t], ud = b.U[2 * t + 1];
-        ctl[t] = make_float4((float)ua, (float)ud, (float)(pc.g_a * ua), (float)(pc.g_d * ud));
-        c0[t] = (float)(pc.half_Ra * ua * ua + pc.half_Rd * ud * ud);
-    }
-    for (int i = tid; i < L.n_ref; i += nth) {
-        bad |= !isfinite(in.ref[2 * i]) || !isfinite(in.ref[2 * i + 1]);
-        vert[i] = local_vertex(in.ref, i, ox, oy);
-    }
-    for (int i = tid; i < L.n_seg; i += nth) {
-        const float4 s = seg_record(in.ref, i, ox, oy);
-        seg[i] = s;
-        head[i] = seg_heading(in.ref, i);
-        // closest segment (or vertex) to x0 itself: the rollouts' first warm start
-        const float2 a = local_vertex(in.ref, i, ox, oy);
-        const float d2 = pc.ref_mode == 0 ? seg_dist2(0.0f, 0.0f, a, s) : fmaf(a.x, a.x, a.y * a.y);
-        const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)i;
-        atomicMin(&b.state->jkey, key);
-    }
-    for (int c = tid; c < L.n_l1; c += nth) {
-        const int v0 = c * REF_L1, v1 = min(v0 + REF_L1, L.n_seg);
-        l1[c] = vertex_box(in.ref, v0, v1, ox, oy);
-    }
-    for (int g = tid; g < L.n_l2; g += nth) {
-        const int v0 = g * REF_L1 * REF_L2, v1 = min(v0 + REF_L1 * REF_L2, L.n_seg);
-        l2[g] = vertex_box(in.ref, v0, v1, ox, oy);
-    }
-    for (int k = tid; k < L.n_circ; k += nth) {
-        const double* c = in.circ + 5 * k;
-        for (int j = 0; j < 5; ++j) bad |= !isfinite(c[j]);
-        const float r = (float)c[2];
-        // band limit (m + r + r_ego)^2 for the constant-d_safe, equal-ego-radius case
-        const float m = pc.collision_only ? fmaxf(pc.d_safe_0, 0.0f) : pc.d_safe_0;
-        const float lim = m + r + pc.ego_rad[0];
-        circ[k] = make_float4((float)(c[0] - ox), (float)(c[1] - oy), r, lim > 0.0f ? lim * lim : -1.0f);
-        vel[k] = make_float2((float)c[3], (float)c[4]);
-        if (c[3] != 0.0 || c[4] != 0.0) atomicOr(&b.state->moving, 1);
-    }
-    if (in.centres) {
-        for (int i = tid; i < L.T * L.n_circ; i += nth) {
-            const double cx = in.centres[2 * i], cy = in.centres[2 * i + 1];
-            bad |= !isfinite(cx) || !isfinite(cy);
-            b.table[i] = make_float2((float)(cx - ox), (float)(cy - oy));
-        }
-    }
-    if (bad) atomicOr(&b.state->flags, FLAG_NONFINITE_INPUT);
+    prep_scene(pc, L, in, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // -----------------------------------------------------------------------------
 // noise: one thread per (step pair j, sample k); coalesced stores along k.
-// The bfloat16 store is a rounding decision: it is taken on the exact normal
-// (binary64 Box-Muller) whenever the binary32 normal lies within its error bound
-// of a rounding midpoint, so the stored code is the one of the exact value.
 // -----------------------------------------------------------------------------
-template <bool BF16>
-__device__ __forceinline__ typename NoiseT<BF16>::type make_noise(float u0, float u1) {
-    const float2 zf = box_muller(u0, u1);
-    if constexpr (BF16) {
-        if (near_bf16_midpoint(zf.x) || near_bf16_midpoint(zf.y)) {
-            const double2 zd = box_muller_f64(u0, u1);
-            __nv_bfloat162 r;
-            r.x = bf16_from_f64(zd.x);
-            r.y = bf16_from_f64(zd.y);
-            return r;
-        }
-    }
-    return NoiseT<BF16>::pack(zf);
-}
-
 template <bool BF16>
 __global__ void __launch_bounds__(256) noise_kernel(PlanConst pc, const DevState* st,
                                                     typename NoiseT<BF16>::type* z) {
@@ -179,506 +71,20 @@ __global__ void philox_kernel(uint2 key, const uint4* ctr, uint4* out, int n) {
     if (i < n) out[i] = philox4x32_10(ctr[i], key);
 }
 
-// -----------------------------------------------------------------------------
-// 1-D bulk (TMA) copy global -> shared, completion on an mbarrier, bounded wait.
-// -----------------------------------------------------------------------------
-__device__ __forceinline__ bool stage_to_smem(unsigned char* dst, const unsigned char* src, int bytes,
-                                              unsigned long long* bar, int* flags) {
-    const uint32_t bar_a = (uint32_t)__cvta_generic_to_shared(bar);
-    const uint32_t dst_a = (uint32_t)__cvta_generic_to_shared(dst);
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(bytes) : "memory");
-        constexpr int CHUNK = 32768;
-        for (int off = 0; off < bytes; off += CHUNK) {
-            const int n = min(CHUNK, bytes - off);
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    dst_a + off),
-                "l"(src + off), "r"(n), "r"(bar_a)
-                : "memory");
-        }
-    }
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar_a), "r"(0u)
-            : "memory");
-    }
-    if (!done) {
-        if (threadIdx.x == 0) atomicOr(flags, FLAG_TIMEOUT);
-        return false;
-    }
-    return true;
-}
-
-// -----------------------------------------------------------------------------
-// rollout + cost.  G lanes (a power of two <= 32) work on one sample: they run the
-// dynamics redundantly (identical bits) and split the reference search and the
-// obstacle pairs, combining with shuffles inside the group.
-// -----------------------------------------------------------------------------
-template <int G>
-__device__ __forceinline__ unsigned group_mask() {
-    if constexpr (G == 32) {
-        return 0xffffffffu;
-    } else {
-        const unsigned lane = threadIdx.x & 31u;
-        return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
-    }
-}
-
-
-template <int G>
-__device__ __forceinline__ float group_min(float v, unsigned mask) {
-#pragma unroll
-    for (int o = G / 2; o >= 1; o >>= 1) v = fminf(v, __shfl_xor_sync(mask, v, o, G));
-    return v;
-}
-
-// Closest point of the polyline (ties -> lowest segment) with a two-level box
-// hierarchy; a box is skipped only when its lower bound exceeds the best distance so
-// far (with a relative slack far above binary32 rounding), so no segment that can be
-// the closest is missed.  The scan keeps the two best distinct segments; when their
-// binary32 distances are within 4e-6 relative, the pair is re-ordered in binary64.
-// Work done by the pruned searches of one lane (only counted in the STATS instantiation).
-struct Counters {
-    unsigned l2, l1, seg, refine, circ, cand, pair;
-};
-
-// (squared distance, index) as one ordered 64-bit key: the minimum key is the smallest
-// distance and, among equal distances, the lowest index.
-__device__ __forceinline__ unsigned long long dkey(float d2, int i) {
-    return ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)i;
-}
-
-template <int G>
-__device__ __forceinline__ unsigned long long group_min_key(unsigned long long k, unsigned mask) {
-#pragma unroll
-    for (int o = G / 2; o >= 1; o >>= 1) {
-        const unsigned long long ok = __shfl_xor_sync(mask, k, o, G);
-        k = ok < k ? ok : k;
-    }
-    return k;
-}
-
-// One level-1 chunk; the lanes of a group split its REF_L1 segments.
-template <int G, bool STATS>
-__device__ __forceinline__ void scan_chunk(float px, float py, const float2* vert, const float4* seg, int c,
-                                           int n_seg, int lane_g, unsigned long long& best, Counters& cnt) {
-    constexpr int PER = (REF_L1 + G - 1) / G;
-    const int i0 = c * REF_L1;
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int o = lane_g + q * G;
-        const int i = i0 + o;
-        if (o < REF_L1 && i < n_seg) {
-            if (STATS) cnt.seg++;
-            const unsigned long long k = dkey(seg_dist2(px, py, vert[i], seg[i]), i);
-            best = k < best ? k : best;
-        }
-    }
-}
-
-// Closest point of the polyline (ties -> lowest segment).  The chunk of the previous
-// step's segment is scanned first; the two-level boxes then skip every chunk whose lower
-// bound exceeds the best distance (with a relative slack far above binary32 rounding), so
-// no segment that can be the closest is missed.  Two segments that share a vertex can be
-// closer than binary32 resolves (next to the vertex on the outside of a bend their
-// distances differ by a second-order term): the winner's neighbours of another heading are
-// re-ordered against it in binary64 when their binary32 distances are within 4e-6.
-template <int G, bool STATS>
-__device__ __forceinline__ void nearest_segment(float px, float py, const float2* vert, const float4* seg,
-                                                const float* head, const float4* l1, const float4* l2, int n_seg,
-                                                int n_l1, int n_l2, int lane_g, unsigned mask, int& jb,
-                                                float& best2, Counters& cnt) {
-    constexpr float SLACK = 1.0f + 1.0f / 1024.0f;
-    const int cw = jb / REF_L1;
-    unsigned long long best = ~0ull;
-    scan_chunk<G, STATS>(px, py, vert, seg, cw, n_seg, lane_g, best, cnt);
-    best = group_min_key<G>(best, mask);
-    float b2 = __uint_as_float((unsigned)(best >> 32));
-#pragma unroll 1
-    for (int g0 = 0; g0 < n_l2; g0 += 8) {
-        unsigned m2 = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (g0 + q < n_l2 && box_dist2(px, py, l2[g0 + q]) <= b2 * SLACK) m2 |= 1u << q;
-        if (STATS) cnt.l2 += min(8, n_l2 - g0);
-        while (m2) {
-            const int c0 = (g0 + __ffs(m2) - 1) * REF_L2;
-            m2 &= m2 - 1;
-            unsigned m1 = 0;
-#pragma unroll
-            for (int j = 0; j < REF_L2; ++j)
-                if (c0 + j < n_l1 && c0 + j != cw && box_dist2(px, py, l1[c0 + j]) <= b2 * SLACK) m1 |= 1u << j;
-            if (STATS) cnt.l1 += min(REF_L2, n_l1 - c0);
-            while (m1) {
-                const int c = c0 + __ffs(m1) - 1;
-                m1 &= m1 - 1;
-                if (box_dist2(px, py, l1[c]) > b2 * SLACK) continue;   // the bound may have tightened
-                scan_chunk<G, STATS>(px, py, vert, seg, c, n_seg, lane_g, best, cnt);
-                best = group_min_key<G>(best, mask);
-                b2 = __uint_as_float((unsigned)(best >> 32));
-            }
-        }
-    }
-    int bi = (int)(best & 0xffffffffu);
-    const int b0 = bi;
-    const float hb = head[b0];
-#pragma unroll
-    for (int dlt = -1; dlt <= 1; dlt += 2) {
-        const int j = b0 + dlt;
-        if (j < 0 || j >= n_seg || head[j] == hb) continue;
-        const float dj = seg_dist2(px, py, vert[j], seg[j]);
-        if (fabsf(dj - b2) <= 4e-6f * b2 + 1e-20f) {
-            if (STATS) cnt.refine++;
-            const double db = seg_dist2_f64(px, py, vert[bi], vert[bi + 1]);
-            const double dd = seg_dist2_f64(px, py, vert[j], vert[j + 1]);
-            if (dd < db || (dd == db && j < bi)) {
-                bi = j;
-                b2 = dj;
-            }
-        }
-    }
-    jb = bi;
-    best2 = b2;
-}
-
-template <int G>
-__device__ __forceinline__ void group_argmin(float& d2, int& idx, unsigned mask) {
-#pragma unroll
-    for (int o = G / 2; o >= 1; o >>= 1) {
-        const float od = __shfl_xor_sync(mask, d2, o, G);
-        const int oi = __shfl_xor_sync(mask, idx, o, G);
-        if (od < d2 || (od == d2 && oi < idx)) {
-            d2 = od;
-            idx = oi;
-        }
-    }
-}
-
-// Closest vertex (ties -> lowest index), same hierarchy (chunk c covers vertices c*L1 .. c*L1+L1).
-template <int G>
-__device__ __forceinline__ void nearest_vertex(float px, float py, const float2* vert, const float4* l1,
-                                               const float4* l2, int n_ref, int n_l1, int n_l2, int lane_g,
-                                               unsigned mask, int& jb, float& best2) {
-    constexpr float SLACK = 1.0f + 1.0f / 1024.0f;
-    float dx = px - vert[jb].x, dy = py - vert[jb].y;
-    float b2 = fmaf(dx, dx, dy * dy);
-    int bi = jb;
-    for (int g = 0; g < n_l2; ++g) {
-        if (box_dist2(px, py, l2[g]) > b2 * SLACK) continue;
-        const int c1 = min((g + 1) * REF_L2, n_l1);
-        for (int c = g * REF_L2; c < c1; ++c) {
-            if (box_dist2(px, py, l1[c]) > b2 * SLACK) continue;
-            const int i1 = min((c + 1) * REF_L1 + 1, n_ref);
-            for (int i = c * REF_L1 + lane_g; i < i1; i += G) {
-                const float ex = px - vert[i].x, ey = py - vert[i].y;
-                const float d2 = fmaf(ex, ex, ey * ey);
-                if (d2 < b2 || (d2 == b2 && i < bi)) {
-                    b2 = d2;
-                    bi = i;
-                }
-            }
-            group_argmin<G>(b2, bi, mask);
-        }
-    }
-    jb = bi;
-    best2 = b2;
-}
-
-// Kahan-compensated accumulator: the value is hi - lo.
-__device__ __forceinline__ void kahan_add(float& hi, float& lo, float inc) {
-    const float y = inc - lo;
-    const float t = hi + y;
-    lo = (t - hi) - y;
-    hi = t;
-}
-
-// Centre of circle kc at rollout step t (state x_{t+1}).
-__device__ __forceinline__ float2 circle_centre(const float4* circ, const float2* vel, const float2* table, int n_circ,
-                                                int t, int kc, float st, bool has_table, bool moving) {
-    if (has_table) return table[(size_t)t * n_circ + kc];
-    const float4 c = circ[kc];
-    if (!moving) return make_float2(c.x, c.y);
-    const float2 vv = vel[kc];
-    return make_float2(fmaf(vv.x, st, c.x), fmaf(vv.y, st, c.y));
-}
-
-// Warp min / max of a float with one redux.sync on an order-preserving integer image
-// (non-negative floats keep their bits, negative ones have their magnitude bits flipped).
-__device__ __forceinline__ int f32_ord(float f) {
-    const int i = __float_as_int(f);
-    return i >= 0 ? i : i ^ 0x7fffffff;
-}
-
-__device__ __forceinline__ float ord_f32(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
-
-__device__ __forceinline__ float warp_min_f(float v) { return ord_f32(__reduce_min_sync(0xffffffffu, f32_ord(v))); }
-
-__device__ __forceinline__ float warp_max_f(float v) { return ord_f32(__reduce_max_sync(0xffffffffu, f32_ord(v))); }
-
-// d_obj of Eq. (16) restricted to the pairs that can lie inside the safety band (the
-// only pairs that change c_safe), with a warp-wide broad phase: the lanes test the
-// circles against the bounding box of every ego circle of the warp, and only the
-// circles that pass (ballot) get the exact per-pair test.  A circle is skipped only
-// when no ego circle of the warp can come within the band of it, so the result equals
-// the brute-force minimum over all in-band pairs.
-template <int G, bool STATS>
-__device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4* circ, const float2* vel,
-                                              const float2* table, int n_circ, int t, bool has_table, bool moving,
-                                              bool dconst, float nx, float ny, float cnth, float snth, float mband,
-                                              int lane, int lane_g, unsigned mask, Counters& cnt) {
-    float ex[8], ey[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        if (e >= pc.n_ego) break;
-        ex[e] = fmaf(pc.ego_off[e], cnth, nx);
-        ey[e] = fmaf(pc.ego_off[e], snth, ny);
-    }
-    // box of the ego circle centres of the whole warp
-    const float xa = fmaf(pc.ego_omin, cnth, nx), xb = fmaf(pc.ego_omax, cnth, nx);
-    const float ya = fmaf(pc.ego_omin, snth, ny), yb = fmaf(pc.ego_omax, snth, ny);
-    const float bx0 = warp_min_f(fminf(xa, xb)), bx1 = warp_max_f(fmaxf(xa, xb));
-    const float by0 = warp_min_f(fminf(ya, yb)), by1 = warp_max_f(fmaxf(ya, yb));
-    const float mmax = dconst ? mband : warp_max_f(mband);
-    const float st = (float)(t + 1) * pc.dt;
-    float dobj = INFINITY;
-    for (int base = 0; base < n_circ; base += 32) {
-        const int kc = base + lane;
-        bool hit = false;
-        if (kc < n_circ) {
-            if (STATS) cnt.circ++;
-            const float2 cc = circle_centre(circ, vel, table, n_circ, t, kc, st, has_table, moving);
-            const float lim = (mmax + circ[kc].z + pc.ego_rmax) * 1.0001f + 1e-4f;
-            const float dx = fmaxf(fmaxf(bx0 - cc.x, cc.x - bx1), 0.0f);
-            const float dy = fmaxf(fmaxf(by0 - cc.y, cc.y - by1), 0.0f);
-            hit = lim > 0.0f && fmaf(dx, dx, dy * dy) <= lim * lim;
-        }
-        unsigned m = __ballot_sync(0xffffffffu, hit);
-        for (int j = 0; m; ++j) {
-            const int bit = __ffs(m) - 1;
-            m &= m - 1;
-            if ((j & (G - 1)) != lane_g) continue;
-            if (STATS) cnt.cand++;
-            const int kc2 = base + bit;
-            const float4 c = circ[kc2];
-            const float2 cc = circle_centre(circ, vel, table, n_circ, t, kc2, st, has_table, moving);
-            if (dconst) {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    if (e >= pc.n_ego) break;
-                    const float dx = ex[e] - cc.x, dy = ey[e] - cc.y;
-                    const float d2 = fmaf(dx, dx, dy * dy);
-                    if (d2 <= c.w) {
-                        if (STATS) cnt.pair++;
-                        dobj = fminf(dobj, sqrtf(d2) - (c.z + pc.ego_rad[e]));
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    if (e >= pc.n_ego) break;
-                    const float R = c.z + pc.ego_rad[e];
-                    const float lim = mband + R;
-                    const float dx = ex[e] - cc.x, dy = ey[e] - cc.y;
-                    const float d2 = fmaf(dx, dx, dy * dy);
-                    if (lim > 0.0f && d2 <= lim * lim) {
-                        if (STATS) cnt.pair++;
-                        dobj = fminf(dobj, sqrtf(d2) - R);
-                    }
-                }
-            }
-        }
-    }
-    return group_min<G>(dobj, mask);
-}
-
 template <int G, bool BF16, bool STATS>
 __global__ void __launch_bounds__(512, 1) rollout_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
-                                                      const typename NoiseT<BF16>::type* __restrict__ z) {
+                                                        const typename NoiseT<BF16>::type* __restrict__ z) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long bar;
     if (!stage_to_smem(smem, b.scene, L.bytes, &bar, &b.state->flags)) return;
-
-    const float4* ctl = reinterpret_cast<const float4*>(smem + L.off_ctl);
-    const float* c0 = reinterpret_cast<const float*>(smem + L.off_c0);
-    const float2* vert = reinterpret_cast<const float2*>(smem + L.off_vert);
-    const float4* seg = reinterpret_cast<const float4*>(smem + L.off_seg);
-    const float* head = reinterpret_cast<const float*>(smem + L.off_head);
-    const float4* l1 = reinterpret_cast<const float4*>(smem + L.off_l1);
-    const float4* l2 = reinterpret_cast<const float4*>(smem + L.off_l2);
-    const float4* circ = reinterpret_cast<const float4*>(smem + L.off_circ);
-    const float2* vel = reinterpret_cast<const float2*>(smem + L.off_vel);
-
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k = gtid / G;
-    const int lane = threadIdx.x & 31;
-    const int lane_g = threadIdx.x & (G - 1);
-    const unsigned mask = group_mask<G>();
-    const int K = pc.K, T = pc.T;
-    const int kk = min(k, K - 1);               // whole groups past K run along (shuffle safety)
-    const float4 x0 = b.state->x0f;
-    const bool moving = b.state->moving != 0;
-    const bool has_table = pc.has_table != 0;
-    const float2 tp = vert[L.n_ref - 1];        // target point T_P: last vertex
-    const bool dconst = pc.d_safe_c == 0.0f && pc.ego_same_radius;
-
-    // x_t with compensated (Kahan) accumulation; the value of each coordinate is hi - lo
-    float px = x0.x, py = x0.y, th = x0.z, v = x0.w;
-    float px_c = 0.0f, py_c = 0.0f, th_c = 0.0f, v_c = 0.0f;
-    float sth, cth;
-    sincosf(th, &sth, &cth);
-    float tdp = fmaf(tp.x, tp.x, tp.y * tp.y);   // |P_0 - T_P|^2 with P_0 = (0, 0)
-    int jb = (int)(b.state->jkey & 0xffffffffu);
-    float s_hi = 0.0f, s_c = 0.0f, q_last = 0.0f;
-    Counters cnt{0, 0, 0, 0, 0, 0, 0};
-
-    for (int t = 0; t < T; ++t) {
-        const float4 ct = ctl[t];
-        const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
-        const Perturbed pe = perturb(ct.x, ct.y, zz, pc.sig_a, pc.sig_d, pc.amin, pc.amax, pc.dmin, pc.dmax);
-        const float vt = v - v_c;
-        float acc = pe.va;
-        if (pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt) / pc.dt), pc.amin);
-        // Eq. (5), explicit Euler from x_t
-        const float tn = tanf(pe.vd);
-        kahan_add(px, px_c, vt * cth * pc.dt);
-        kahan_add(py, py_c, vt * sth * pc.dt);
-        kahan_add(th, th_c, vt * tn * pc.dt_over_L);
-        kahan_add(v, v_c, acc * pc.dt);
-        const float nx = px, ny = py;
-        float snth, cnth;
-        sincosf(th, &snth, &cnth);
-
-        // Eq. (12), (14): closest waypoint (search on the binary32 position) and reference yaw
-        float d2r;
-        if (pc.ref_mode == 0)
-            nearest_segment<G, STATS>(nx, ny, vert, seg, head, l1, l2, L.n_seg, L.n_l1, L.n_l2, lane_g, mask, jb,
-                                      d2r, cnt);
-        else
-            nearest_vertex<G>(nx, ny, vert, l1, l2, L.n_ref, L.n_l1, L.n_l2, lane_g, mask, jb, d2r);
-        const float thr = head[min(jb, L.n_seg - 1)];
-        {
-            // c_dist on the compensated position: closest point of the winning segment or vertex
-            const float2 a = vert[jb];
-            float qx = a.x, qy = a.y;
-            if (pc.ref_mode == 0) {
-                const float4 sg = seg[jb];
-                const float tau = fmaf(nx - a.x, sg.z, (ny - a.y) * sg.w);
-                if (tau >= 1.0f) {
-                    qx = vert[jb + 1].x;
-                    qy = vert[jb + 1].y;
-                } else if (tau > 0.0f) {
-                    qx = fmaf(tau, sg.x, a.x);
-                    qy = fmaf(tau, sg.y, a.y);
-                }
-            }
-            const float dx = (nx - qx) - px_c, dy = (ny - qy) - py_c;
-            d2r = fmaf(dx, dx, dy * dy);
-        }
-        // Eq. (13): progress towards the target point
-        const float tx = (nx - tp.x) - px_c, ty = (ny - tp.y) - py_c;
-        const float tdn = fmaf(tx, tx, ty * ty);
-        const float c_target = tdn > tdp ? 1.0f : 0.0f;
-        tdp = tdn;
-        const float dyaw = wrap_pi((th - thr) - th_c);
-        const float dv = (v - pc.v_ref) - v_c;
-
-        // Eq. (16)-(17): ego circles against obstacle circles
-        const float ds = fmaf(pc.d_safe_c, v - v_c, pc.d_safe_0);
-        const float mband = pc.collision_only ? fmaxf(ds, 0.0f) : ds;
-        float dobj = INFINITY;
-        if (L.n_circ > 0)
-            dobj = obstacle_min<G, STATS>(pc, circ, vel, b.table, L.n_circ, t, has_table, moving, dconst, nx, ny,
-                                          cnth, snth, mband, lane, lane_g, mask, cnt);
-        const float gap = ds - dobj;
-        float c_safe = gap > 0.0f ? gap * gap : 0.0f;
-        if (pc.collision_only && !(dobj <= 0.0f)) c_safe = 0.0f;
-
-        // Eq. (18) weighted state cost, Eq. (8) control cost
-        const float qx = fmaf(pc.w_dist, d2r,
-                              fmaf(pc.w_target, c_target,
-                                   fmaf(pc.w_yaw, dyaw * dyaw, fmaf(pc.w_speed, dv * dv, pc.w_safe * c_safe))));
-        const float qu = fmaf(ct.z, pe.ea, fmaf(ct.w, pe.ed, c0[t]));
-        kahan_add(s_hi, s_c, qx + qu);          // Eq. (6)
-        q_last = qx;
-        sth = snth;
-        cth = cnth;
-    }
-    if (lane_g == 0 && k < K) {
-        double S = (double)s_hi - (double)s_c;
-        if (pc.w_terminal != 0.0f) S += (double)pc.w_terminal * (double)q_last;
-        b.S[k] = S;
-    }
-    if (STATS && k < K) {
-        const unsigned v7[7] = {cnt.l2, cnt.l1, cnt.seg, cnt.refine, cnt.circ, cnt.cand, cnt.pair};
-        for (int i = 0; i < 7; ++i) atomicAdd(b.stats + i, (unsigned long long)v7[i]);
-    }
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    rollout_sample<G, BF16, STATS>(pc, L, smem, z, b.table, b.state->x0f, b.state->moving != 0,
+                                   (int)(b.state->jkey & 0xffffffffu), k, b.S, b.stats);
 }
 
 // -----------------------------------------------------------------------------
 // argmin over S with ties to the lowest index; non-finite costs are skipped.
 // -----------------------------------------------------------------------------
-struct MinRec {
-    double v;
-    int i;
-    int n;
-};
-
-__device__ __forceinline__ MinRec min_combine(MinRec a, MinRec b) {
-    MinRec r;
-    r.n = a.n + b.n;
-    if (b.v < a.v || (b.v == a.v && b.i < a.i)) {
-        r.v = b.v;
-        r.i = b.i;
-    } else {
-        r.v = a.v;
-        r.i = a.i;
-    }
-    return r;
-}
-
-__device__ __forceinline__ MinRec warp_min(MinRec a) {
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        MinRec b;
-        b.v = __shfl_xor_sync(0xffffffffu, a.v, o);
-        b.i = __shfl_xor_sync(0xffffffffu, a.i, o);
-        b.n = __shfl_xor_sync(0xffffffffu, a.n, o);
-        a = min_combine(a, b);
-    }
-    return a;
-}
-
-__device__ MinRec block_min(MinRec a) {
-    __shared__ double sv[32];
-    __shared__ int si[32], sn[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    a = warp_min(a);
-    if (lane == 0) {
-        sv[w] = a.v;
-        si[w] = a.i;
-        sn[w] = a.n;
-    }
-    __syncthreads();
-    if (w == 0) {
-        MinRec r{INFINITY, 0x7fffffff, 0};
-        if (lane < nw) r = MinRec{sv[lane], si[lane], sn[lane]};
-        a = warp_min(r);
-    }
-    __syncthreads();
-    return a;
-}
-
 __global__ void __launch_bounds__(256) argmin_kernel(int K, PlanBuffers b) {
     MinRec r{INFINITY, 0x7fffffff, 0};
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
@@ -721,22 +127,6 @@ __global__ void __launch_bounds__(256) argmin_kernel(int K, PlanBuffers b) {
 // -----------------------------------------------------------------------------
 // softmin weights in binary64 (Eq. (11)); eta partial sums per block.
 // -----------------------------------------------------------------------------
-__device__ double block_sum_d(double v) {
-    __shared__ double sh[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        v = lane < nw ? sh[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    }
-    __syncthreads();
-    return v;
-}
-
 __global__ void __launch_bounds__(256) weights_kernel(int K, double lam, PlanBuffers b) {
     const double smin = b.state->s_min;
     double acc = 0.0;
@@ -756,201 +146,18 @@ __global__ void __launch_bounds__(256) weights_kernel(int K, double lam, PlanBuf
 // its J samples and its warp (32 x J products), and the per-warp partials are
 // added in binary64.
 // -----------------------------------------------------------------------------
-constexpr int WS_J = 8;
-constexpr int WS_TT = 32;
-
 template <bool BF16>
 __global__ void __launch_bounds__(256) wsum_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
                                                    const typename NoiseT<BF16>::type* __restrict__ z) {
-    __shared__ float red[8][WS_TT][2];
-    const int K = pc.K, T = pc.T;
-    const int kt = blockIdx.x;
-    const int t0 = blockIdx.y * WS_TT, t1 = min(T, t0 + WS_TT);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float4* ctl = reinterpret_cast<const float4*>(b.scene + L.off_ctl);
-    float wj[WS_J];
-    int kj[WS_J];
-#pragma unroll
-    for (int j = 0; j < WS_J; ++j) {
-        kj[j] = kt * b.kt_size + j * blockDim.x + threadIdx.x;
-        wj[j] = kj[j] < K ? b.w[kj[j]] : 0.0f;
-    }
-    for (int t = t0; t < t1; ++t) {
-        const float4 ct = ctl[t];
-        float aa = 0.0f, ad = 0.0f;
-#pragma unroll
-        for (int j = 0; j < WS_J; ++j) {
-            if (kj[j] < K) {
-                const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kj[j]);
-                const Perturbed pe =
-                    perturb(ct.x, ct.y, zz, pc.sig_a, pc.sig_d, pc.amin, pc.amax, pc.dmin, pc.dmax);
-                aa = fmaf(wj[j], pe.ea, aa);
-                ad = fmaf(wj[j], pe.ed, ad);
-            }
-        }
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            aa += __shfl_xor_sync(0xffffffffu, aa, o);
-            ad += __shfl_xor_sync(0xffffffffu, ad, o);
-        }
-        if (lane == 0) {
-            red[warp][t - t0][0] = aa;
-            red[warp][t - t0][1] = ad;
-        }
-    }
-    __syncthreads();
-    const int nw = blockDim.x >> 5;
-    for (int i = threadIdx.x; i < (t1 - t0) * 2; i += blockDim.x) {
-        double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += (double)red[w][i >> 1][i & 1];
-        b.du_part[((size_t)kt * T + t0 + (i >> 1)) * 2 + (i & 1)] = s;
-    }
+    wsum_tile<BF16>(pc, ctl, z, b.w, blockIdx.x, blockIdx.y * WS_TT, b.kt_size, b.du_part);
 }
 
 // -----------------------------------------------------------------------------
-// finalize: u <- clamp(u + du), u* = clamp(SG(u)), x* = F-rollout of u*, warm start.
-// One block, one thread per step (T <= 1024).  x* is a chain of prefix sums:
-// v_t from sum a dt, yaw from sum v tan(delta)/L dt, x and y from sum v (cos, sin) dt.
+// finalize (see finalize_block)
 // -----------------------------------------------------------------------------
-__device__ double block_scan_incl(double v, double* sh) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double n = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += n;
-    }
-    if (lane == 31) sh[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        double s = lane < nw ? sh[lane] : 0.0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const double n = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += n;
-        }
-        sh[lane] = s;
-    }
-    __syncthreads();
-    if (w > 0) v += sh[w - 1];
-    __syncthreads();
-    return v;
-}
-
-__device__ __forceinline__ double clampd(double x, double lo, double hi) { return fmin(fmax(x, lo), hi); }
-
 __global__ void __launch_bounds__(1024) finalize_kernel(PlanConst pc, PlanBuffers b, PlanInputs in) {
-    __shared__ double s_un[2 * 1024];
-    __shared__ double s_us[2 * 1024];
-    __shared__ double s_scan[32];
-    __shared__ double s_eta;
-    __shared__ int s_status;
-    DevState* st = b.state;
-    const int T = pc.T;
-    const int t = threadIdx.x;
-    if (t == 0) {
-        const int flags = st->flags;
-        int status = 0;
-        if (flags & FLAG_NONFINITE_INPUT) status = -1;
-        else if (flags & FLAG_TIMEOUT) status = -5;
-        else if (st->n_finite == 0) status = -4;
-        s_status = status;
-        double e = 0.0;
-        for (int i = 0; i < b.n_wblk; ++i) e += b.eta_part[i];
-        s_eta = e;
-    }
-    __syncthreads();
-    if (s_status != 0) {
-        if (t == 0) {
-            st->status = s_status;
-            st->flags = 0;
-            st->moving = 0;
-            st->jkey = ~0ull;
-        }
-        return;
-    }
-    const double eta = s_eta;
-    for (int i = t; i < 2 * T; i += blockDim.x) {
-        double num = 0.0;
-        for (int kt = 0; kt < b.n_kt; ++kt) num += b.du_part[(size_t)kt * 2 * T + i];
-        const bool ch = i & 1;
-        s_un[i] = clampd(b.U[i] + num / eta, ch ? pc.dmin_d : pc.amin_d, ch ? pc.dmax_d : pc.amax_d);
-    }
-    __syncthreads();
-    for (int i = t; i < 2 * T; i += blockDim.x) {
-        const int tt = i >> 1, ch = i & 1;
-        double val;
-        if (pc.sg_enable) {
-            const double cf[5] = {-3.0, 12.0, 17.0, 12.0, -3.0};
-            double acc = 0.0;
-#pragma unroll
-            for (int j = -2; j <= 2; ++j) {
-                const int s = min(max(tt + j, 0), T - 1);
-                acc += cf[j + 2] * s_un[2 * s + ch];
-            }
-            val = clampd(acc / 35.0, ch ? pc.dmin_d : pc.amin_d, ch ? pc.dmax_d : pc.amax_d);
-        } else {
-            val = s_un[i];
-        }
-        s_us[i] = val;
-        in.u_out[i] = val;
-    }
-    __syncthreads();
-
-    // x*: prefix sums in binary64 (sequential when the speed cap makes v nonlinear)
-    const double x0 = in.x0[0], y0 = in.x0[1], th0 = in.x0[2], v0 = in.x0[3];
-    if (t == 0) {
-        in.x_out[0] = x0; in.x_out[1] = y0; in.x_out[2] = th0; in.x_out[3] = v0;
-    }
-    const double dt = pc.dt_d;
-    if (pc.vcap) {
-        if (t == 0) {
-            double x = x0, y = y0, th = th0, v = v0;
-            for (int s = 0; s < T; ++s) {
-                double a = s_us[2 * s];
-                const double lim = (pc.v_max_d - v) / dt;
-                if (a > lim) a = lim;
-                if (a < pc.amin_d) a = pc.amin_d;
-                const double nx = x + v * cos(th) * dt, ny = y + v * sin(th) * dt;
-                const double nth = th + v * tan(s_us[2 * s + 1]) / pc.wheelbase_d * dt;
-                const double nv = v + a * dt;
-                x = nx; y = ny; th = nth; v = nv;
-                in.x_out[4 * (s + 1)] = x; in.x_out[4 * (s + 1) + 1] = y;
-                in.x_out[4 * (s + 1) + 2] = th; in.x_out[4 * (s + 1) + 3] = v;
-            }
-        }
-    } else {
-        const bool on = t < T;
-        const double a = on ? s_us[2 * t] : 0.0, dl = on ? s_us[2 * t + 1] : 0.0;
-        const double pv = block_scan_incl(on ? a * dt : 0.0, s_scan);          // v_{t+1} - v0
-        const double vt = v0 + (pv - (on ? a * dt : 0.0));                      // v_t
-        const double dth = on ? vt * tan(dl) / pc.wheelbase_d * dt : 0.0;
-        const double pth = block_scan_incl(dth, s_scan);                         // yaw_{t+1} - yaw0
-        const double tht = th0 + (pth - dth);                                    // yaw_t
-        const double dx = on ? vt * cos(tht) * dt : 0.0, dy = on ? vt * sin(tht) * dt : 0.0;
-        const double px = block_scan_incl(dx, s_scan);
-        const double py = block_scan_incl(dy, s_scan);
-        if (on) {
-            in.x_out[4 * (t + 1)] = x0 + px;
-            in.x_out[4 * (t + 1) + 1] = y0 + py;
-            in.x_out[4 * (t + 1) + 2] = th0 + pth;
-            in.x_out[4 * (t + 1) + 3] = v0 + pv;
-        }
-    }
-    // warm start for the next iteration (Algorithm 1, last loop)
-    for (int i = t; i < 2 * T; i += blockDim.x) {
-        const int tt = i >> 1, ch = i & 1;
-        const int src = pc.shift ? min(tt + 1, T - 1) : tt;
-        b.U[i] = s_us[2 * src + ch];
-    }
-    if (t == 0) {
-        st->status = 0;
-        st->eta = eta;
-        st->iter_used = st->iter;
-        st->iter += 1ull;
-        st->flags = 0;
-        st->moving = 0;
-        st->jkey = ~0ull;
-    }
+    finalize_block(pc, b, in);
 }
 
 // -----------------------------------------------------------------------------
