@@ -353,6 +353,228 @@ def run_gpu(args, world, rank, local):
         torch.distributed.destroy_process_group()
 
 
+# ------------------------------------------------------------------------ batched uneven plans
+
+def run_batched(args, world, rank, local):
+    """256 uneven plans per submission through mppi_batch_plan, against the plain per-plan loop."""
+    import numpy as np
+    import torch
+
+    import paper_2308_01654_gb300 as mp
+    from paper_2308_01654_gb300 import scenarios
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    probs = scenarios.batched(seed=0, n=args.batch_size)
+    for p in probs:
+        p.params["session"] = rank * 100000 + int(p.params["session"])
+    n = len(probs)
+    sum_k = sum(p.K for p in probs)
+    sum_kt = sum(p.K * p.T for p in probs)
+    max_t = max(p.T for p in probs)
+    max_ref = max(p.ref.shape[0] for p in probs)
+    max_circ = max(max(p.circles.shape[0] for p in probs), 1)
+    bp = mp.BatchPlanner(max_slots=n, max_batch=n, max_samples=sum_k, max_rollout_steps=sum_kt, max_T=max_t,
+                         max_ref=max_ref, max_circ=max_circ, pipelines=2, device=local)
+    plans = [mp.BatchPlan(p.params, i, p.x0, p.ref, p.circles, p.centres) for i, p in enumerate(probs)]
+    group, block = bp.autotune(plans)
+    reqs = bp.requests(plans)
+    for _ in range(args.warmup):
+        bp.plan(plans, reqs)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    barrier()
+    lat = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        a = time.perf_counter()
+        bp.plan(plans, reqs)
+        lat.append(time.perf_counter() - a)
+    t_batch = (time.perf_counter() - t0) / args.steps
+    barrier()
+    bad = sum(p.info.n_finite == 0 for p in plans)
+    bp.close()
+
+    # the plain path: one context per plan, plans one after another on one stream
+    ctxs = [mp.Planner(p.params, device=local, max_ref=max_ref, max_circ=max_circ) for p in probs]
+    for pl, p in zip(ctxs, probs):
+        pl.plan(p.x0, p.ref, p.circles, p.centres)
+    barrier()
+    t0 = time.perf_counter()
+    reps = max(1, min(args.steps, 3))
+    for _ in range(reps):
+        for pl, p in zip(ctxs, probs):
+            pl.plan(p.x0, p.ref, p.circles, p.centres)
+    t_plain = (time.perf_counter() - t0) / reps
+    for pl in ctxs:
+        pl.close()
+    if world > 1:
+        t = torch.tensor([t_batch, t_plain], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_batch, t_plain = float(t[0]), float(t[1])
+    out = {"metric": f"plans/s ({n} uneven plans per submission, batched)", "value": world * n / t_batch,
+           "unit": "plans/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64-reduce", "data": "synthetic (uneven plans: K in 2^10..2^14, T 30..150, 0..32 obstacles)",
+           "config": {"workload": f"batched: {n} plans, sum K = {sum_k}, sum K*T = {sum_kt}",
+                      "rollout_launch": {"lanes_per_sample": group, "threads_per_block": block},
+                      "timing": "wall clock of mppi_batch_plan (host packing, H2D, graph, D2H, unpacking)"},
+           "rollout_steps_per_s": world * sum_kt / t_batch,
+           "submission_ms": {"p50": float(np.percentile(lat, 50)) * 1e3, "p99": float(np.percentile(lat, 99)) * 1e3},
+           "plain_per_plan_loop": {"value": world * n / t_plain, "unit": "plans/s", "ms_per_pass": t_plain * 1e3,
+                                   "rollout_steps_per_s": world * sum_kt / t_plain},
+           "speedup_vs_plain": t_plain / t_batch, "plans_without_finite_cost": int(bad)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------------ serving
+
+def serving_trace(sessions, rate: float, seconds: float, seed: int = 5, variants: int = 4):
+    """Poisson arrivals at `rate` plans/s, sessions drawn uniformly, obstacles redrawn per request
+    (one of `variants` perturbed copies of the session's obstacle set)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    obst = []
+    for p in sessions:
+        vs = []
+        for _ in range(variants):
+            c = p.circles.copy()
+            if c.shape[0]:
+                c[:, :2] += rng.normal(scale=0.5, size=(c.shape[0], 2))
+            vs.append(np.ascontiguousarray(c))
+        obst.append(vs)
+    t, out = 0.0, []
+    while t < seconds:
+        t += rng.exponential(1.0 / rate)
+        s = int(rng.integers(0, len(sessions)))
+        out.append((t, s, obst[s][int(rng.integers(0, variants))]))
+    return out
+
+
+def run_serving(args, world, rank, local):
+    """Continuous batching of 512 sessions at a Poisson 2000 plans/s against the plain FIFO loop."""
+    import queue as queue_mod
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_2308_01654_gb300 as mp
+    from paper_2308_01654_gb300 import scenarios
+
+    torch.cuda.set_device(local)
+    sessions = scenarios.serving_sessions(seed=0, n=args.sessions)
+    for p in sessions:
+        p.params["shift"] = 1
+    cparams = [mp.make_params(p.params) for p in sessions]
+    warm, meas = args.serve_warmup_s, args.serve_seconds
+    trace = serving_trace(sessions, args.rate, warm + meas)
+    max_t = max(p.T for p in sessions)
+    max_ref = max(p.ref.shape[0] for p in sessions)
+    max_circ = max(max(p.circles.shape[0] for p in sessions), 1)
+
+    def summarise(lat_arr, t_arr, done_t, label):
+        lat_arr, t_arr, done_t = np.asarray(lat_arr), np.asarray(t_arr), np.asarray(done_t)
+        m = (t_arr >= warm) & (t_arr < warm + meas)
+        completed = int(np.sum((done_t >= warm) & (done_t < warm + meas)))
+        return {"plans_per_s": completed / meas, "p50_ms": float(np.percentile(lat_arr[m], 50)) / 1e3,
+                "p99_ms": float(np.percentile(lat_arr[m], 99)) / 1e3, "max_ms": float(lat_arr[m].max()) / 1e3,
+                "requests": int(m.sum()), "label": label}
+
+    # --- continuous batching server
+    srv = mp.Server(max_sessions=len(sessions), max_batch=256, max_samples=2_000_000, max_rollout_steps=200_000_000,
+                    max_T=max_t, max_ref=max_ref, max_circ=max_circ, pipelines=args.pipelines,
+                    hbm_budget_bytes=args.hbm_budget_gb << 30, max_wait_us=args.max_wait_us, device=local)
+    big = max(sessions, key=lambda p: p.K * p.T)
+    group, block = srv.autotune(cparams[sessions.index(big)], big.x0, big.ref, big.circles, 64)
+    ids, lat, arr_t, done_t = {}, {}, {}, {}
+    t0 = [0.0]
+    stop = threading.Event()
+
+    def collector():
+        while not stop.is_set() or len(done_t) < len(trace):
+            for r in srv.poll(1024, wait_ms=20):
+                j = ids.get(r["request_id"])
+                if j is None:
+                    continue
+                lat[j] = r["latency_us"]
+                done_t[j] = time.perf_counter() - t0[0]
+            if stop.is_set() and len(done_t) >= len(ids):
+                break
+
+    th = threading.Thread(target=collector, daemon=True)
+    t0[0] = time.perf_counter()
+    th.start()
+    for j, (t, s, circ) in enumerate(trace):
+        now = time.perf_counter() - t0[0]
+        if t > now:
+            time.sleep(t - now)
+        p = sessions[s]
+        rid = srv.enqueue(cparams[s], s, p.x0, p.ref, circ if circ.shape[0] else None)
+        ids[rid] = j
+        arr_t[j] = t
+    stop.set()
+    th.join(timeout=60)
+    st = srv.pending()
+    srv.close()
+    order = sorted(lat)
+    served = summarise([lat[j] for j in order], [arr_t[j] for j in order], [done_t[j] for j in order], "server")
+    served.update(batches=st["batches"], plans=st["plans"], mean_batch=st["plans"] / max(st["batches"], 1),
+                  rollout_launch={"lanes_per_sample": group, "threads_per_block": block})
+
+    # --- plain loop: one context per session, one request at a time in arrival order
+    ctxs = [mp.Planner(p.params, device=local, max_ref=max_ref, max_circ=max_circ) for p in sessions]
+    q = queue_mod.Queue()
+    plat, parr, pdone = [], [], []
+
+    def worker():
+        while True:
+            item = q.get()
+            if item is None:
+                return
+            j, ta = item
+            t, s, circ = trace[j]
+            p = sessions[s]
+            ctxs[s].plan(p.x0, p.ref, circ if circ.shape[0] else None)
+            tdone = time.perf_counter() - t0[0]
+            plat.append((tdone - ta) * 1e6)
+            parr.append(t)
+            pdone.append(tdone)
+
+    w = threading.Thread(target=worker, daemon=True)
+    t0[0] = time.perf_counter()
+    w.start()
+    for j, (t, s, circ) in enumerate(trace):
+        now = time.perf_counter() - t0[0]
+        if t > now:
+            time.sleep(t - now)
+        q.put((j, time.perf_counter() - t0[0]))
+    q.put(None)
+    w.join(timeout=600)
+    for c in ctxs:
+        c.close()
+    plain = summarise(plat, parr, pdone, "plain FIFO mppi_plan loop")
+    mean_kt = float(np.mean([sessions[s].K * sessions[s].T for _, s, _ in trace]))
+    out = {"metric": f"served plans/s ({len(sessions)} sessions, Poisson {args.rate:.0f} plans/s offered)",
+           "value": served["plans_per_s"], "unit": "plans/s", "n_gpus": world, "steps": len(trace), "warmup": 0,
+           "ms_per_step": served["p50_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64-reduce", "data": "synthetic sessions (K 2^10..2^14, T 30..150, 0..32 obstacles)",
+           "config": {"workload": f"serving: {warm:.0f} s warm-up + {meas:.0f} s measured, mean K*T {mean_kt:.0f}",
+                      "pipelines": args.pipelines, "max_wait_us": args.max_wait_us},
+           "latency_ms": {"p50": served["p50_ms"], "p99": served["p99_ms"], "max": served["max_ms"]},
+           "server": served, "plain_per_plan_loop": plain}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------------------ the reference arm (the oracle)
 
 def run_reference(args, world, rank, local):
@@ -386,7 +608,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="roofline",
-                    choices=["roofline", "roofline_bf16", "closed_loop", "single_plan"])
+                    choices=["roofline", "roofline_bf16", "closed_loop", "single_plan", "batched", "serving"])
+    ap.add_argument("--batch-size", type=int, default=256)
+    ap.add_argument("--sessions", type=int, default=512)
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--serve-warmup-s", type=float, default=2.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--pipelines", type=int, default=3)
+    ap.add_argument("--max-wait-us", type=float, default=0.0)
+    ap.add_argument("--hbm-budget-gb", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -401,6 +631,10 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank, local)
+    elif args.workload == "batched":
+        run_batched(args, world, rank, local)
+    elif args.workload == "serving":
+        run_serving(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
 

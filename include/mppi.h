@@ -247,6 +247,70 @@ int mppi_batch_set_controls(mppi_batch* batch, int32_t slot, const double* U, in
 int mppi_batch_get_controls(mppi_batch* batch, int32_t slot, double* U, int32_t T, uint64_t* iter);
 const char* mppi_batch_last_error(mppi_batch* batch);
 
+/* ------------------------------------------------------------------------------------
+   Serving: a continuous-batching planning server for many vehicle sessions.  Requests
+   arrive at any time (mppi_server_enqueue copies the inputs and returns at once).  A
+   scheduler thread forms a micro-batch whenever one of the `pipelines` is free, taking
+   queued requests in arrival order while their device footprint (noise K*T*8 bytes, or
+   *4 with bfloat16 noise, costs and weights K*12 bytes, the scene) fits the free part of
+   hbm_budget_bytes and the per-batch capacities; a session is never in two batches in
+   flight, so its requests run in order against its device-resident warm start (session
+   id = warm-start slot).  Up to `pipelines` batches overlap on the GPU; requests that
+   arrive meanwhile join the next batch.  Results, with the latency from enqueue to
+   completion, are collected with mppi_server_poll.
+   ------------------------------------------------------------------------------------ */
+typedef struct mppi_server mppi_server;
+
+typedef struct {
+    int32_t max_sessions;       /* sessions (and warm-start slots), ids 0 .. max_sessions-1 */
+    int32_t max_batch;          /* plans per micro-batch (<= 1024) */
+    int64_t max_samples;        /* sum of K per micro-batch */
+    int64_t max_rollout_steps;  /* sum of K*T per micro-batch */
+    int32_t max_T, max_ref, max_circ;
+    int32_t pipelines;          /* micro-batches in flight at once (1..16) */
+    int32_t noise_bf16;
+    int32_t device;
+    int64_t hbm_budget_bytes;   /* admission limit on the footprint of all requests in flight */
+    double max_wait_us;         /* a batch may wait this long to grow while others run (0: never waits) */
+} mppi_server_config;
+
+typedef struct {
+    uint64_t request_id;
+    int32_t session;
+    int32_t status;             /* mppi_status of the plan */
+    int32_t T;
+    double latency_us;          /* completion - enqueue */
+    double queue_us;            /* submission to the GPU - enqueue */
+    mppi_info info;
+} mppi_result;
+
+int mppi_server_create(const mppi_server_config* cfg, mppi_server** out);
+int mppi_server_destroy(mppi_server* server);   /* waits for the batches in flight */
+
+/* Tunes the batch engine's rollout launch shape on n_plans copies of one request
+   (the server must be idle). */
+int mppi_server_autotune(mppi_server* server, const mppi_params* params, const double* x0, const double* ref_xy,
+                         int32_t n_ref, const mppi_circle* circ, int32_t n_circ, int32_t n_plans,
+                         int32_t* group, int32_t* block);
+
+/* Thread-safe; the arrays are copied before it returns. */
+int mppi_server_enqueue(mppi_server* server, const mppi_params* params, int32_t session, const double* x0,
+                        const double* ref_xy, int32_t n_ref, const mppi_circle* circ, int32_t n_circ,
+                        const double* centres, uint64_t* request_id);
+
+/* Moves up to max completed results into out[] (waiting up to wait_ms for the first);
+   with u_out / x_out (may be NULL) also their u* [max_T][2] and x* [max_T+1][4] per result. */
+int mppi_server_poll(mppi_server* server, mppi_result* out, int32_t max, double* u_out, double* x_out,
+                     int32_t max_T, int32_t wait_ms, int32_t* n_out);
+
+/* Queue depth, requests in flight, micro-batches submitted and plans completed so far. */
+int mppi_server_pending(mppi_server* server, int32_t* queued, int32_t* in_flight, uint64_t* batches,
+                        uint64_t* plans);
+
+/* Warm start of an idle session (checkpoint / resume). */
+int mppi_server_set_controls(mppi_server* server, int32_t session, const double* U, int32_t T, uint64_t iter);
+const char* mppi_server_last_error(mppi_server* server);
+
 /* Allocation-free lowest-cost search.  The paper has no counterpart: this is a
    service for callers that cannot allocate GPU memory while they plan, such as a
    vehicle control cycle that must not stall on cudaMalloc (which can synchronise

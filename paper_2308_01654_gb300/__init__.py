@@ -98,6 +98,17 @@ SIGNATURES = {
     "mppi_batch_set_controls": (C.c_int, [_VP, C.c_int32, _DP, C.c_int32, C.c_uint64]),
     "mppi_batch_get_controls": (C.c_int, [_VP, C.c_int32, _DP, C.c_int32, C.POINTER(C.c_uint64)]),
     "mppi_batch_last_error": (C.c_char_p, [_VP]),
+    "mppi_server_create": (C.c_int, [_VP, C.POINTER(_VP)]),
+    "mppi_server_destroy": (C.c_int, [_VP]),
+    "mppi_server_autotune": (C.c_int, [_VP, _VP, _DP, _DP, C.c_int32, _DP, C.c_int32, C.c_int32,
+                                       C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "mppi_server_enqueue": (C.c_int, [_VP, _VP, C.c_int32, _DP, _DP, C.c_int32, _DP, C.c_int32, _DP,
+                                      C.POINTER(C.c_uint64)]),
+    "mppi_server_poll": (C.c_int, [_VP, _VP, C.c_int32, _DP, _DP, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
+    "mppi_server_pending": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_uint64),
+                                      C.POINTER(C.c_uint64)]),
+    "mppi_server_set_controls": (C.c_int, [_VP, C.c_int32, _DP, C.c_int32, C.c_uint64]),
+    "mppi_server_last_error": (C.c_char_p, [_VP]),
     "mppi_status_string": (C.c_char_p, [C.c_int]),
     "mppi_last_error": (C.c_char_p, [_VP]),
 }
@@ -426,3 +437,99 @@ class BatchPlanner:
         it = C.c_uint64()
         self._check(lib().mppi_batch_get_controls(self._h, slot, _dp(U), T, C.byref(it)), self._h)
         return U, it.value
+
+
+class MppiServerConfig(C.Structure):
+    _fields_ = [("max_sessions", C.c_int32), ("max_batch", C.c_int32), ("max_samples", C.c_int64),
+                ("max_rollout_steps", C.c_int64), ("max_T", C.c_int32), ("max_ref", C.c_int32),
+                ("max_circ", C.c_int32), ("pipelines", C.c_int32), ("noise_bf16", C.c_int32), ("device", C.c_int32),
+                ("hbm_budget_bytes", C.c_int64), ("max_wait_us", C.c_double)]
+
+
+class MppiResult(C.Structure):
+    _fields_ = [("request_id", C.c_uint64), ("session", C.c_int32), ("status", C.c_int32), ("T", C.c_int32),
+                ("latency_us", C.c_double), ("queue_us", C.c_double), ("info", MppiInfo)]
+
+
+class Server:
+    """Continuous-batching planning server (mppi_server_*): enqueue from any thread, poll results."""
+
+    def __init__(self, max_sessions: int, max_batch: int, max_samples: int, max_rollout_steps: int, max_T: int,
+                 max_ref: int, max_circ: int, pipelines: int = 3, hbm_budget_bytes: int = 8 << 30,
+                 noise_bf16: int = 0, max_wait_us: float = 0.0, device: int = 0):
+        self.cfg = MppiServerConfig(max_sessions, max_batch, max_samples, max_rollout_steps, max_T, max_ref,
+                                    max_circ, pipelines, noise_bf16, device, hbm_budget_bytes, max_wait_us)
+        self.max_T = max_T
+        h = _VP()
+        self._check(lib().mppi_server_create(C.byref(self.cfg), C.byref(h)), None)
+        self._h = h
+
+    def _check(self, rc, h):
+        if rc != 0:
+            msg = lib().mppi_server_last_error(h)
+            raise MppiError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mppi_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def autotune(self, params: MppiParams, x0, ref, circles, n_plans: int):
+        x0, ref = _f64(x0), _f64(ref).reshape(-1, 2)
+        circ = _f64(np.zeros((0, 5)) if circles is None else circles).reshape(-1, 5)
+        g, b = C.c_int32(), C.c_int32()
+        self._check(lib().mppi_server_autotune(self._h, C.byref(params), _dp(x0), _dp(ref), ref.shape[0],
+                                               _dp(circ) if circ.shape[0] else None, circ.shape[0], n_plans,
+                                               C.byref(g), C.byref(b)), self._h)
+        return g.value, b.value
+
+    def enqueue(self, params: MppiParams, session: int, x0, ref, circles=None, centres=None) -> int:
+        """params: an MppiParams built once per session (make_params); arrays: float64 C-contiguous."""
+        rid = C.c_uint64()
+        n_circ = 0 if circles is None else circles.shape[0]
+        rc = lib().mppi_server_enqueue(self._h, C.byref(params), session, _dp(x0), _dp(ref), ref.shape[0],
+                                       _dp(circles) if n_circ else None, n_circ, _dp(centres), C.byref(rid))
+        self._check(rc, self._h)
+        return rid.value
+
+    def poll(self, max_results: int = 1024, wait_ms: int = 0, with_outputs: bool = False):
+        out = (MppiResult * max_results)()
+        n = C.c_int32()
+        U = X = None
+        if with_outputs:
+            U = np.zeros((max_results, self.max_T, 2))
+            X = np.zeros((max_results, self.max_T + 1, 4))
+        self._check(lib().mppi_server_poll(self._h, C.cast(out, _VP), max_results, _dp(U), _dp(X), self.max_T,
+                                           wait_ms, C.byref(n)), self._h)
+        res = []
+        for i in range(n.value):
+            r = out[i]
+            d = dict(request_id=r.request_id, session=r.session, status=r.status, T=r.T,
+                     latency_us=r.latency_us, queue_us=r.queue_us, info=r.info.as_dict())
+            if with_outputs:
+                d["u"] = U[i, :r.T].copy()
+                d["x"] = X[i, :r.T + 1].copy()
+            res.append(d)
+        return res
+
+    def pending(self):
+        q, f = C.c_int32(), C.c_int32()
+        b, p = C.c_uint64(), C.c_uint64()
+        self._check(lib().mppi_server_pending(self._h, C.byref(q), C.byref(f), C.byref(b), C.byref(p)), self._h)
+        return dict(queued=q.value, in_flight=f.value, batches=b.value, plans=p.value)
+
+    def set_controls(self, session: int, U, iter_: int = 0):
+        U = _f64(U).reshape(-1, 2)
+        self._check(lib().mppi_server_set_controls(self._h, session, _dp(U), U.shape[0], int(iter_)), self._h)

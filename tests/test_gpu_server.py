@@ -1,0 +1,127 @@
+"""The continuous-batching server (mppi_server_*) (needs a GB300).
+
+Each result must be the same whether its request ran alone or mixed with others in
+micro-batches: requests of one session run in arrival order against the session's
+device-resident warm start, and a plan's arithmetic does not depend on its batch.
+"""
+import numpy as np
+import pytest
+
+import paper_2308_01654_gb300 as mp
+from paper_2308_01654_gb300 import scenarios as sc
+
+pytestmark = pytest.mark.gpu
+
+
+def sessions(n=10, seed=7):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        p = sc.uneven_instance(rng, i, seed=seed)
+        p.params["K"] = int(rng.choice([512, 1024, 3000]))
+        p.params["T"] = int(rng.integers(8, 50))
+        p.params["shift"] = 1
+        out.append(p)
+    return out
+
+
+def trace(probs, n_req=30, seed=1):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for _ in range(n_req):
+        s = int(rng.integers(0, len(probs)))
+        p = probs[s]
+        circ = p.circles.copy()
+        if circ.shape[0]:
+            circ[:, :2] += rng.normal(scale=0.3, size=(circ.shape[0], 2))      # obstacles redrawn per request
+        reqs.append((s, np.ascontiguousarray(circ)))
+    return reqs
+
+
+def server_for(probs, **kw):
+    cfg = dict(max_sessions=len(probs), max_batch=64, max_samples=200000, max_rollout_steps=8_000_000,
+               max_T=64, max_ref=1024, max_circ=128, pipelines=3, hbm_budget_bytes=1 << 30)
+    cfg.update(kw)
+    return mp.Server(**cfg)
+
+
+def run(srv, probs, reqs, params, alone):
+    ids = {}
+    results = {}
+    for j, (s, circ) in enumerate(reqs):
+        p = probs[s]
+        rid = srv.enqueue(params[s], s, p.x0, p.ref, circ if circ.shape[0] else None)
+        ids[rid] = j
+        if alone:
+            got = []
+            while not got:
+                got = srv.poll(16, wait_ms=1000, with_outputs=True)
+            for r in got:
+                results[ids[r["request_id"]]] = r
+    while len(results) < len(reqs):
+        for r in srv.poll(64, wait_ms=1000, with_outputs=True):
+            results[ids[r["request_id"]]] = r
+    return [results[j] for j in range(len(reqs))]
+
+
+def test_results_are_the_same_alone_and_in_the_mix():
+    probs = sessions()
+    reqs = trace(probs)
+    params = [mp.make_params(p.params) for p in probs]
+    with server_for(probs) as srv:
+        alone = run(srv, probs, reqs, params, alone=True)
+        for s, p in enumerate(probs):
+            srv.set_controls(s, np.zeros((p.T, 2)), 0)
+        mix = run(srv, probs, reqs, params, alone=False)
+        stats = srv.pending()
+    assert stats["batches"] < 2 * len(reqs)           # the mixed run did batch requests together
+    for a, b in zip(alone, mix):
+        assert a["status"] == 0 and b["status"] == 0
+        np.testing.assert_array_equal(a["u"], b["u"])
+        np.testing.assert_array_equal(a["x"], b["x"])
+        assert a["info"] == b["info"]
+
+
+def test_server_agrees_with_the_single_plan_path():
+    probs = sessions(n=4)
+    reqs = [(0, probs[0].circles), (1, probs[1].circles), (0, probs[0].circles), (3, probs[3].circles)]
+    params = [mp.make_params(p.params) for p in probs]
+    with server_for(probs) as srv:
+        res = run(srv, probs, reqs, params, alone=False)
+    ctx = {s: mp.Planner(probs[s].params) for s in (0, 1, 3)}
+    try:
+        for (s, circ), r in zip(reqs, res):
+            p = probs[s]
+            u, x, info = ctx[s].plan(p.x0, p.ref, circ if circ.shape[0] else None)
+            assert r["info"]["argmin"] == info["argmin"] and r["info"]["iter"] == info["iter"]
+            np.testing.assert_allclose(r["u"], u, rtol=1e-12, atol=1e-14)
+    finally:
+        for c in ctx.values():
+            c.close()
+
+
+def test_hbm_budget_limits_what_is_in_flight():
+    probs = sessions(n=6)
+    params = [mp.make_params(p.params) for p in probs]
+    # room for the largest request (noise, costs and weights, ~60 KB for its scene) but not for all six
+    biggest = max(p.K * p.T * 8 + p.K * 12 for p in probs)
+    budget = biggest + 60_000
+    assert sum(p.K * p.T * 8 for p in probs) > budget
+    reqs = [(s, probs[s].circles) for s in range(6)]
+    with server_for(probs, hbm_budget_bytes=budget) as srv:
+        res = run(srv, probs, reqs, params, alone=False)
+        st = srv.pending()
+    assert all(r["status"] == 0 for r in res)
+    assert st["batches"] >= 2                         # the budget split the six requests
+
+
+def test_request_above_capacity_is_refused():
+    probs = sessions(n=2)
+    params = [mp.make_params(p.params) for p in probs]
+    with server_for(probs, hbm_budget_bytes=10_000) as srv:
+        with pytest.raises(mp.MppiError) as e:
+            srv.enqueue(params[0], 0, probs[0].x0, probs[0].ref, probs[0].circles if probs[0].circles.shape[0] else None)
+        assert e.value.status == -6
+        with pytest.raises(mp.MppiError) as e:
+            srv.enqueue(params[0], 5, probs[0].x0, probs[0].ref, None)      # session out of range
+        assert e.value.status == -1
