@@ -435,6 +435,37 @@ def run_batched(args, world, rank, local):
         torch.distributed.destroy_process_group()
 
 
+# ------------------------------------------------------------------------ closed loop
+
+def run_closed_loop(args, world, rank, local):
+    """The 200-cycle receding-horizon loop on the curved lane through mppi_plan (host buffers)."""
+    import numpy as np
+    import torch
+
+    from paper_2308_01654_gb300 import closed_loop, scenarios
+
+    torch.cuda.set_device(local)
+    prob = scenarios.closed_loop()
+    prob.params["session"] = rank
+    res = closed_loop.run(prob, cycles=args.cycles, device=local)
+    t = res.plan_ms[3:] if len(res.plan_ms) > 6 else res.plan_ms
+    K, T = prob.K, prob.T
+    out = {"metric": "rollout-steps/s (K*T) of one MPPI iteration per control cycle, closed loop",
+           "value": world * K * T / (float(np.median(t)) * 1e-3), "unit": "rollout-steps/s", "n_gpus": world,
+           "steps": args.cycles, "warmup": 3, "ms_per_step": float(np.median(t)), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64-reduce", "data": "synthetic",
+           "config": {"workload": f"closed_loop: K={K} T={T}, {args.cycles} cycles, sinusoidal lane, 8 obstacles "
+                                  f"(4 moving, per-step centre table)",
+                      "timing": "wall clock of mppi_plan per cycle (host buffers, CUDA graph replay)"},
+           "cycle_ms": {"p50": float(np.median(t)), "p99": float(np.percentile(t, 99)), "mean": float(np.mean(t))},
+           "run": {"min_clearance_m": res.min_clearance, "max_abs_steer": float(np.abs(res.controls[:, 1]).max()),
+                   "max_abs_accel": float(np.abs(res.controls[:, 0]).max()),
+                   "final_state": [float(v) for v in res.states[-1]],
+                   "max_speed": float(res.states[:, 3].max())}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------------------ serving
 
 def serving_trace(sessions, rate: float, seconds: float, seed: int = 5, variants: int = 4):
@@ -608,7 +639,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="roofline",
-                    choices=["roofline", "roofline_bf16", "closed_loop", "single_plan", "batched", "serving"])
+                    choices=["roofline", "roofline_bf16", "closed_loop", "single_plan", "batched", "serving",
+                             "closed_loop_run"])
+    ap.add_argument("--cycles", type=int, default=200)
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--sessions", type=int, default=512)
     ap.add_argument("--rate", type=float, default=2000.0)
@@ -635,6 +668,8 @@ def main():
         run_batched(args, world, rank, local)
     elif args.workload == "serving":
         run_serving(args, world, rank, local)
+    elif args.workload == "closed_loop_run":
+        run_closed_loop(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
 

@@ -30,6 +30,10 @@ struct mppi_ctx {
     int group = 1;
     int threads = 128;
     int profiling = 0;
+    // the host-buffer iteration captured as a CUDA graph, per input shape
+    cudaGraphExec_t graph = nullptr;
+    long long graph_key = -1, seen_key = -1;
+    size_t graph_n_in = 0;
     cudaEvent_t ev[N_KERNELS + 1] = {};
     std::string err;
 };
@@ -181,6 +185,7 @@ static void free_all(mppi_ctx* c) {
     if (c->h_state) cudaFreeHost(c->h_state);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
 }
 
@@ -362,9 +367,10 @@ static void fill_info(const DevState& s, mppi_info* info) {
     info->iter = s.iter_used;
 }
 
-static int wait_status(mppi_ctx* c, mppi_info* info, double eta_unused) {
-    (void)eta_unused;
-    CK(cudaMemcpyAsync(c->h_state, c->b.state, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "state copy");
+static int wait_status(mppi_ctx* c, mppi_info* info, bool state_copied = false) {
+    if (!state_copied)
+        CK(cudaMemcpyAsync(c->h_state, c->b.state, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream),
+           "state copy");
     CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
     const DevState& s = *c->h_state;
     if (info) {
@@ -377,9 +383,11 @@ static int wait_status(mppi_ctx* c, mppi_info* info, double eta_unused) {
     return s.status;
 }
 
-// Validates host inputs and queues their copy into the context's device input buffer.
+// Validates host inputs, packs them into the pinned staging buffer and (with copy) queues
+// their copy into the context's device input buffer; n_in receives the staged doubles.
 static int stage_host_inputs(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n_ref,
-                             const mppi_circle* circ, int32_t n_circ, const double* centres, PlanInputs& in) {
+                             const mppi_circle* circ, int32_t n_circ, const double* centres, PlanInputs& in,
+                             bool copy = true, size_t* n_in_out = nullptr) {
     if (!x0 || !ref_xy || (n_circ > 0 && !circ)) return fail(c, MPPI_ERR_ARG, "NULL array argument");
     int rc = check_sizes(c, n_ref, n_circ);
     if (rc != MPPI_OK) return rc;
@@ -394,8 +402,10 @@ static int stage_host_inputs(mppi_ctx* c, const double* x0, const double* ref_xy
     if (nc) memcpy(h + 4 + nr, circ, nc * sizeof(double));
     if (nt) memcpy(h + 4 + nr + nc, centres, nt * sizeof(double));
     const size_t n_in = 4 + nr + nc + nt;
+    if (n_in_out) *n_in_out = n_in;
     CK(cudaSetDevice(c->device), "cudaSetDevice");
-    CK(cudaMemcpyAsync(c->d_in, h, n_in * sizeof(double), cudaMemcpyHostToDevice, c->stream), "input copy");
+    if (copy)
+        CK(cudaMemcpyAsync(c->d_in, h, n_in * sizeof(double), cudaMemcpyHostToDevice, c->stream), "input copy");
     in.x0 = c->d_in;
     in.ref = c->d_in + 4;
     in.circ = c->d_in + 4 + nr;
@@ -407,19 +417,70 @@ static int stage_host_inputs(mppi_ctx* c, const double* x0, const double* ref_xy
     return MPPI_OK;
 }
 
+// The whole host-buffer iteration (input copy, kernels, output and status copies) in
+// stream order; captured into a graph by mppi_plan.
+static cudaError_t plan_sequence(mppi_ctx* c, const PlanInputs& in, size_t n_in) {
+    cudaError_t e = cudaMemcpyAsync(c->d_in, c->h_in, n_in * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    const SceneLayout L = make_layout(c->p.T, in.n_ref, in.n_circ);
+    PlanConst pc = c->pc;
+    pc.has_table = in.centres ? 1 : 0;
+    e = launch_iteration(pc, L, c->b, in, c->group, c->threads, c->p.noise_bf16, c->stream, nullptr);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(c->h_out, c->d_out, c->out_elems * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(c->h_state, c->b.state, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream);
+}
+
 int mppi_plan(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n_ref, const mppi_circle* circ,
               int32_t n_circ, const double* centres, double* u_out, double* x_out, mppi_info* info) {
     if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
     if (!u_out || !x_out) return fail(c, MPPI_ERR_ARG, "NULL array argument");
     const int T = c->p.T;
     PlanInputs in;
-    int rc = stage_host_inputs(c, x0, ref_xy, n_ref, circ, n_circ, centres, in);
+    size_t n_in = 0;
+    int rc = stage_host_inputs(c, x0, ref_xy, n_ref, circ, n_circ, centres, in, false, &n_in);
     if (rc != MPPI_OK) return rc;
-    rc = enqueue(c, in, in.centres ? 1 : 0);
-    if (rc != MPPI_OK) return rc;
-    CK(cudaMemcpyAsync(c->h_out, c->d_out, c->out_elems * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
-       "output copy");
-    rc = wait_status(c, info, 0.0);
+    if (c->profiling) {
+        CK(cudaMemcpyAsync(c->d_in, c->h_in, n_in * sizeof(double), cudaMemcpyHostToDevice, c->stream), "input copy");
+        rc = enqueue(c, in, in.centres ? 1 : 0);
+        if (rc != MPPI_OK) return rc;
+        CK(cudaMemcpyAsync(c->h_out, c->d_out, c->out_elems * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+           "output copy");
+        rc = wait_status(c, info);
+    } else {
+        // shape key: the graph bakes in sizes, the layout and the launch shape
+        const long long key = ((((long long)n_ref * 2048 + n_circ) * 2 + (in.centres ? 1 : 0)) * 64 + c->group) * 1024 +
+                              c->threads;
+        if (c->graph && key == c->graph_key && n_in == c->graph_n_in) {
+            CK(cudaGraphLaunch(c->graph, c->stream), "graph launch");
+        } else if (key == c->seen_key) {
+            // second iteration with this shape: capture it (the first ran uncaptured and set up
+            // every kernel attribute outside the capture)
+            if (c->graph) {
+                cudaGraphExecDestroy(c->graph);
+                c->graph = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            const cudaError_t es = plan_sequence(c, in, n_in);
+            const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+            if (es != cudaSuccess || ee != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return cuda_fail(c, es != cudaSuccess ? es : ee, "graph capture");
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&c->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) return cuda_fail(c, ei, "graph instantiate");
+            c->graph_key = key;
+            c->graph_n_in = n_in;
+            CK(cudaGraphLaunch(c->graph, c->stream), "graph launch");
+        } else {
+            CK(plan_sequence(c, in, n_in), "kernel launch");
+            c->seen_key = key;
+        }
+        rc = wait_status(c, info, true);
+    }
     if (rc != MPPI_OK) return rc;
     memcpy(u_out, c->h_out, 2 * (size_t)T * sizeof(double));
     memcpy(x_out, c->h_out + 2 * (size_t)T, 4 * (size_t)(T + 1) * sizeof(double));
@@ -444,7 +505,7 @@ int mppi_plan_device(mppi_ctx* c, const double* d_x0, const double* d_ref_xy, in
     in.x_out = d_x_out;
     rc = enqueue(c, in, d_centres ? 1 : 0);
     if (rc != MPPI_OK) return rc;
-    if (info) return wait_status(c, info, 0.0);
+    if (info) return wait_status(c, info);
     return MPPI_OK;
 }
 
@@ -591,7 +652,7 @@ int mppi_rollout_stats(mppi_ctx* c, const double* x0, const double* ref_xy, int3
 int mppi_sync(mppi_ctx* c, mppi_info* info) {
     if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
-    return wait_status(c, info, 0.0);
+    return wait_status(c, info);
 }
 
 int mppi_set_controls(mppi_ctx* c, const double* U, uint64_t iter) {
