@@ -67,8 +67,14 @@ def executed_ops_per_step(stats) -> float:
 
 
 KERNEL_SOURCES = ("paper_2308_01654_gb300/csrc/mppi_kernels.cu", "paper_2308_01654_gb300/csrc/mppi_device.cuh",
-                  "paper_2308_01654_gb300/csrc/mppi_internal.h")
+                  "paper_2308_01654_gb300/csrc/mppi_internal.h", "paper_2308_01654_gb300/csrc/mppi_iter.cuh")
 TRAFFIC_PROFILE = {"roofline": "profiles/rollout_kernel_roofline_K65536_T200.md"}
+
+
+def launch_desc(group: int, block: int) -> dict:
+    """The rollout launch shape: lanes per sample and what they split."""
+    return {"lanes_per_sample": abs(int(group)), "lanes_split": "steps" if group < 0 else "work of each step",
+            "threads_per_block": int(block)}
 
 
 def kernel_source_hash() -> str:
@@ -334,7 +340,7 @@ def run_gpu(args, world, rank, local):
                                f"n_circ={prob.circles.shape[0]}", "K": K, "T": T,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed between steps (256 MB write)",
-                   "rollout_launch": {"lanes_per_sample": group, "threads_per_block": block}},
+                   "rollout_launch": launch_desc(group, block)},
         "e2e": e2e, "roofline": roofline, "gpu_launches": KERNEL_LAUNCHES_PER_STEP * args.steps,
         "kernel_ms": kmean, "clocks": clocks,
     }
@@ -422,7 +428,7 @@ def run_batched(args, world, rank, local):
            "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64-reduce", "data": "synthetic (uneven plans: K in 2^10..2^14, T 30..150, 0..32 obstacles)",
            "config": {"workload": f"batched: {n} plans, sum K = {sum_k}, sum K*T = {sum_kt}",
-                      "rollout_launch": {"lanes_per_sample": group, "threads_per_block": block},
+                      "rollout_launch": launch_desc(group, block),
                       "timing": "wall clock of mppi_batch_plan (host packing, H2D, graph, D2H, unpacking)"},
            "rollout_steps_per_s": world * sum_kt / t_batch,
            "submission_ms": {"p50": float(np.percentile(lat, 50)) * 1e3, "p99": float(np.percentile(lat, 99)) * 1e3},
@@ -559,7 +565,7 @@ def run_serving(args, world, rank, local):
     order = sorted(lat)
     served = summarise([lat[j] for j in order], [arr_t[j] for j in order], [done_t[j] for j in order], "server")
     served.update(batches=st["batches"], plans=st["plans"], mean_batch=st["plans"] / max(st["batches"], 1),
-                  rollout_launch={"lanes_per_sample": group, "threads_per_block": block})
+                  rollout_launch=launch_desc(group, block))
 
     # --- plain loop: one context per session, one request at a time in arrival order
     ctxs = [mp.Planner(p.params, device=local, max_ref=max_ref, max_circ=max_circ) for p in sessions]

@@ -91,8 +91,10 @@ typedef struct {
     int32_t noise_bf16;         /* 1: store the noise as bfloat16 (half the bytes) */
     uint64_t seed;              /* Philox key */
     uint32_t session;           /* Philox counter word 3: independent streams per session */
-    int32_t group;              /* lanes per sample in the rollout kernel: 0 = choose, else 1,2,4,8,16,32 */
-    int32_t block;              /* threads per block of the rollout kernel: 0 = choose, else a multiple of 32 up to 512 */
+    int32_t group;              /* lanes per sample in the rollout kernel: 0 = choose; 1,2,4,8,16,32 = the
+                                   lanes split the search and obstacle work of each step; -2,-4 = 2 or 4
+                                   lanes split the steps (each evaluates every 2nd / 4th step's cost) */
+    int32_t block;              /* threads per block of the rollout kernel: 0 = choose, else a multiple of 32 up to 448 */
 } mppi_params;
 
 /* Results of one iteration. */
@@ -147,7 +149,7 @@ int mppi_plan_device(mppi_ctx* ctx, const double* d_x0, const double* d_ref_xy, 
                      const double* d_circ, int32_t n_circ, const double* d_centres,
                      double* d_u_out, double* d_x_out, mppi_info* info);
 
-/* Autotuner: times the rollout kernel for every lanes-per-sample group (1..32) and
+/* Autotuner: times the rollout kernel for every lanes-per-sample group (1..32, -2, -4) and
    block size (64, 128, 256, and sizes that spread the lanes evenly over the SMs with
    1 to 4 resident blocks each) on the given inputs (host arrays, as for mppi_plan) and
    keeps the fastest for this context; *group and *block receive the choice (either

@@ -62,6 +62,12 @@ static bool finite_all(const double* v, size_t n) {
     return true;
 }
 
+static bool valid_group(int g) {
+    return g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32 || g == -2 || g == -4;
+}
+
+static bool valid_block(int b) { return b >= 32 && b <= MAX_ROLLOUT_THREADS && b % 32 == 0; }
+
 static int check_params(const mppi_params* p, std::string& why) {
     if (!p) { why = "params is NULL"; return MPPI_ERR_ARG; }
     if (p->K < 1) { why = "K must be >= 1"; return MPPI_ERR_ARG; }
@@ -86,13 +92,12 @@ static int check_params(const mppi_params* p, std::string& why) {
     for (int e = 0; e < p->n_ego; ++e)
         if (!isfinite(p->ego_offset[e]) || !isfinite(p->ego_radius[e])) { why = "ego circles must be finite"; return MPPI_ERR_ARG; }
     if (p->ref_mode != 0 && p->ref_mode != 1) { why = "ref_mode must be 0 or 1"; return MPPI_ERR_ARG; }
-    const int g = p->group;
-    if (!(g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32)) {
-        why = "group must be 0, 1, 2, 4, 8, 16 or 32";
+    if (!valid_group(p->group)) {
+        why = "group must be 0, 1, 2, 4, 8, 16, 32, -2 or -4";
         return MPPI_ERR_ARG;
     }
-    if (!(p->block == 0 || (p->block >= 32 && p->block <= 512 && p->block % 32 == 0))) {
-        why = "block must be 0 or a multiple of 32 in [32, 512]";
+    if (!(p->block == 0 || valid_block(p->block))) {
+        why = "block must be 0 or a multiple of 32 in [32, 448]";
         return MPPI_ERR_ARG;
     }
     return MPPI_OK;
@@ -450,8 +455,8 @@ int mppi_plan(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n_ref
         rc = wait_status(c, info);
     } else {
         // shape key: the graph bakes in sizes, the layout and the launch shape
-        const long long key = ((((long long)n_ref * 2048 + n_circ) * 2 + (in.centres ? 1 : 0)) * 64 + c->group) * 1024 +
-                              c->threads;
+        const long long key =
+            ((((long long)n_ref * 2048 + n_circ) * 2 + (in.centres ? 1 : 0)) * 64 + (c->group + 8)) * 1024 + c->threads;
         if (c->graph && key == c->graph_key && n_in == c->graph_n_in) {
             CK(cudaGraphLaunch(c->graph, c->stream), "graph launch");
         } else if (key == c->seen_key) {
@@ -520,7 +525,7 @@ static std::string gpu_name(int device) {
 
 static std::string tune_key(mppi_ctx* c, int n_ref, int n_circ) {
     char buf[256];
-    snprintf(buf, sizeof(buf), "%s|%d|%d|%d|%d|%d", gpu_name(c->device).c_str(), c->p.K, c->p.T, n_ref, n_circ,
+    snprintf(buf, sizeof(buf), "%s|%d|%d|%d|%d|%d|r2", gpu_name(c->device).c_str(), c->p.K, c->p.T, n_ref, n_circ,
              c->p.noise_bf16);
     return buf;
 }
@@ -558,7 +563,7 @@ int mppi_autotune(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n
     if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
     const std::string key = tune_key(c, n_ref, n_circ);
     int g = 0, t = 0;
-    if (cache_lookup(cache_path, key, g, t)) {
+    if (cache_lookup(cache_path, key, g, t) && g != 0 && valid_group(g) && valid_block(t)) {
         c->group = g;
         c->threads = t;
     } else {
@@ -577,12 +582,13 @@ int mppi_autotune(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n
         int n_sm = 0;
         CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
         const size_t smem = rollout_smem_bytes(L);
-        const int groups[] = {1, 2, 4, 8, 16, 32};
+        // lanes per sample: > 0 split the work of each step, < 0 split the steps
+        const int groups[] = {1, 2, 4, 8, 16, 32, -2, -4};
         cudaError_t err = cudaSuccess;
-        for (int gi = 0; gi < 6 && err == cudaSuccess; ++gi) {
+        for (int gi = 0; gi < 8 && err == cudaSuccess; ++gi) {
             const int G = groups[gi];
-            const long long lanes = (long long)c->p.K * G;
-            if (G > 1 && lanes > 4LL * n_sm * 2048) continue;   // far more lanes than the GPU holds
+            const long long lanes = (long long)c->p.K * (G < 0 ? -G : G);
+            if (G != 1 && lanes > 4LL * n_sm * 2048) continue;  // far more lanes than the GPU holds
             // candidate block sizes: fixed ones, and "balanced" ones that give every SM the same
             // number of lanes when m blocks per SM are resident together
             int cand[8], nc = 0;
@@ -592,7 +598,7 @@ int mppi_autotune(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n
             for (int m = 1; m <= 4; ++m) {
                 long long per = (lanes + (long long)n_sm * m - 1) / ((long long)n_sm * m);
                 int th = (int)(((per + 31) / 32) * 32);
-                if (th < 32 || th > 512) continue;
+                if (th < 32 || th > MAX_ROLLOUT_THREADS) continue;
                 if (rollout_max_blocks_per_sm(G, th, c->p.noise_bf16, smem) < m) continue;
                 bool dup = false;
                 for (int i = 0; i < nc; ++i) dup |= cand[i] == th;

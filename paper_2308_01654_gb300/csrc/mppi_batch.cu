@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(512, 1) batch_rollout_kernel(BatchArgs a) {
         }
         const BatchInst& d = a.inst[td.x];
         const int k = td.y + (int)threadIdx.x / G;
-        rollout_sample<G, BF16, false>(s_pc, s_L, smem, reinterpret_cast<const NT*>(a.z) + d.z_off,
+        rollout_sample<G, false, BF16, false>(s_pc, s_L, smem, reinterpret_cast<const NT*>(a.z) + d.z_off,
                                        a.table + d.table_off, s_x0, s_moving != 0, s_jb0, k, a.S + d.s_off, nullptr);
         __syncthreads();
     }

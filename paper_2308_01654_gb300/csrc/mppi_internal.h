@@ -6,6 +6,10 @@
 
 namespace mppi {
 
+// Largest block of the single-plan rollout kernel: it is compiled for two such blocks per
+// SM (at most 72 registers a thread), so one wave holds 896 lanes per SM.
+constexpr int MAX_ROLLOUT_THREADS = 448;
+
 // Per-context device record: iteration counter, status and the reduction results.
 struct __align__(16) DevState {
     unsigned long long iter;     // next iteration index (low 32 bits enter the Philox counter)
@@ -37,6 +41,7 @@ struct SceneLayout {
     int off_l2;      // float4 [n_l2]    level-2 group boxes
     int off_circ;    // float4 [n_circ]  (x, y, r, (d_safe_0 + r + r_ego)^2 when d_safe is constant)
     int off_vel;     // float2 [n_circ]  velocities
+    int off_disp;    // float  [n_circ]  bound on the distance a centre moves in one step
     int bytes;       // total, a multiple of 16
 };
 

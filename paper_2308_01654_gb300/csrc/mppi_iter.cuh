@@ -32,16 +32,6 @@ __device__ __forceinline__ float seg_heading(const double* ref, int i) {
     return (float)atan2(hy, hx);
 }
 
-__device__ __forceinline__ float4 vertex_box(const double* ref, int v0, int v1, double ox, double oy) {
-    float4 bb = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
-    for (int j = v0; j <= v1; ++j) {
-        const float2 p = local_vertex(ref, j, ox, oy);
-        bb.x = fminf(bb.x, p.x); bb.y = fminf(bb.y, p.y);
-        bb.z = fmaxf(bb.z, p.x); bb.w = fmaxf(bb.w, p.y);
-    }
-    return bb;
-}
-
 __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayout& L, const PlanInputs& in,
                                            const PlanBuffers& b, int tid, int nth) {
     const double ox = in.x0[0], oy = in.x0[1];
@@ -55,6 +45,7 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
     float4* l2 = reinterpret_cast<float4*>(sc + L.off_l2);
     float4* circ = reinterpret_cast<float4*>(sc + L.off_circ);
     float2* vel = reinterpret_cast<float2*>(sc + L.off_vel);
+    float* disp = reinterpret_cast<float*>(sc + L.off_disp);
     bool bad = false;
 
     if (tid == 0) {
@@ -80,13 +71,38 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
         const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)i;
         atomicMin(&b.state->jkey, key);
     }
+    // level-1 boxes: one thread per chunk (its REF_L1 + 1 vertex loads are independent)
     for (int c = tid; c < L.n_l1; c += nth) {
         const int v0 = c * REF_L1, v1 = min(v0 + REF_L1, L.n_seg);
-        l1[c] = vertex_box(in.ref, v0, v1, ox, oy);
+        float4 bb = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
+#pragma unroll
+        for (int j = 0; j <= REF_L1; ++j) {
+            if (v0 + j <= v1) {
+                const float2 p = local_vertex(in.ref, v0 + j, ox, oy);
+                bb.x = fminf(bb.x, p.x); bb.y = fminf(bb.y, p.y);
+                bb.z = fmaxf(bb.z, p.x); bb.w = fmaxf(bb.w, p.y);
+            }
+        }
+        l1[c] = bb;
     }
-    for (int g = tid; g < L.n_l2; g += nth) {
+    // level-2 boxes: one warp per group, the lanes stride over its vertices
+    const int lane = tid & 31, wid = tid >> 5, nwarps = nth >> 5;
+    for (int g = wid; g < L.n_l2; g += nwarps) {
         const int v0 = g * REF_L1 * REF_L2, v1 = min(v0 + REF_L1 * REF_L2, L.n_seg);
-        l2[g] = vertex_box(in.ref, v0, v1, ox, oy);
+        float4 bb = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
+        for (int j = v0 + lane; j <= v1; j += 32) {
+            const float2 p = local_vertex(in.ref, j, ox, oy);
+            bb.x = fminf(bb.x, p.x); bb.y = fminf(bb.y, p.y);
+            bb.z = fmaxf(bb.z, p.x); bb.w = fmaxf(bb.w, p.y);
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            bb.x = fminf(bb.x, __shfl_xor_sync(0xffffffffu, bb.x, o));
+            bb.y = fminf(bb.y, __shfl_xor_sync(0xffffffffu, bb.y, o));
+            bb.z = fmaxf(bb.z, __shfl_xor_sync(0xffffffffu, bb.z, o));
+            bb.w = fmaxf(bb.w, __shfl_xor_sync(0xffffffffu, bb.w, o));
+        }
+        if (lane == 0) l2[g] = bb;
     }
     for (int k = tid; k < L.n_circ; k += nth) {
         const double* c = in.circ + 5 * k;
@@ -98,12 +114,28 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
         circ[k] = make_float4((float)(c[0] - ox), (float)(c[1] - oy), r, lim > 0.0f ? lim * lim : -1.0f);
         vel[k] = make_float2((float)c[3], (float)c[4]);
         if (c[3] != 0.0 || c[4] != 0.0) atomicOr(&b.state->moving, 1);
+        if (!in.centres) disp[k] = (float)(sqrt(c[3] * c[3] + c[4] * c[4]) * pc.dt_d * 1.001) + 1e-5f;
     }
     if (in.centres) {
         for (int i = tid; i < L.T * L.n_circ; i += nth) {
             const double cx = in.centres[2 * i], cy = in.centres[2 * i + 1];
             bad |= !isfinite(cx) || !isfinite(cy);
             b.table[i] = make_float2((float)(cx - ox), (float)(cy - oy));
+        }
+        // the largest step of each tabulated centre (from the rounded entries the rollouts
+        // read): one warp per circle, the lanes stride over the steps
+        for (int k = wid; k < L.n_circ; k += nwarps) {
+            double m = 0.0;
+            for (int t = 1 + lane; t < L.T; t += 32) {
+                const double* a = in.centres + 2 * ((size_t)(t - 1) * L.n_circ + k);
+                const double* q = in.centres + 2 * ((size_t)t * L.n_circ + k);
+                const double dx = (double)(float)(q[0] - ox) - (double)(float)(a[0] - ox);
+                const double dy = (double)(float)(q[1] - oy) - (double)(float)(a[1] - oy);
+                m = fmax(m, fabs(dx) + fabs(dy));    // >= the Euclidean step
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) disp[k] = isfinite(m) ? (float)(m * 1.001) + 1e-5f : INFINITY;
         }
     }
     if (bad) atomicOr(&b.state->flags, FLAG_NONFINITE_INPUT);
@@ -397,37 +429,36 @@ __device__ __forceinline__ float warp_max_f(float v) { return ord_f32(__reduce_m
 // circles against the bounding box of every ego circle of the warp, and only the
 // circles that pass (ballot) get the exact per-pair test.  A circle is skipped only
 // when no ego circle of the warp can come within the band of it, so the result equals
-// the brute-force minimum over all in-band pairs.
+// the brute-force minimum over all in-band pairs.  The lanes of a warp may be at
+// different steps t (all within tb0..tb1, the same for the whole warp): the broad phase
+// then tests each circle's centre at tb0 with the band widened by the farthest it can
+// move in tb1 - tb0 steps.
 template <int G, bool STATS>
 __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4* circ, const float2* vel,
-                                              const float2* table, int n_circ, int t, bool has_table, bool moving,
-                                              bool dconst, float nx, float ny, float cnth, float snth, float mband,
-                                              int lane, int lane_g, unsigned mask, Counters& cnt) {
-    float ex[8], ey[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        if (e >= pc.n_ego) break;
-        ex[e] = fmaf(pc.ego_off[e], cnth, nx);
-        ey[e] = fmaf(pc.ego_off[e], snth, ny);
-    }
+                                              const float* disp, const float2* table, int n_circ, int t, int tb0,
+                                              int tb1,
+                                              bool has_table, bool moving, bool dconst, float nx, float ny,
+                                              float cnth, float snth, float mband, int lane, int lane_g,
+                                              unsigned mask, Counters& cnt) {
     // box of the ego circle centres of the whole warp
     const float xa = fmaf(pc.ego_omin, cnth, nx), xb = fmaf(pc.ego_omax, cnth, nx);
     const float ya = fmaf(pc.ego_omin, snth, ny), yb = fmaf(pc.ego_omax, snth, ny);
     const float bx0 = warp_min_f(fminf(xa, xb)), bx1 = warp_max_f(fmaxf(xa, xb));
     const float by0 = warp_min_f(fminf(ya, yb)), by1 = warp_max_f(fmaxf(ya, yb));
     const float mmax = dconst ? mband : warp_max_f(mband);
-    const float st = (float)(t + 1) * pc.dt;
+    const float st = (float)(t + 1) * pc.dt, st0 = (float)(tb0 + 1) * pc.dt;
     float dobj = INFINITY;
     for (int base = 0; base < n_circ; base += 32) {
         const int kc = base + lane;
         bool hit = false;
         if (kc < n_circ) {
             if (STATS) cnt.circ++;
-            const float2 cc = circle_centre(circ, vel, table, n_circ, t, kc, st, has_table, moving);
+            const float2 cc = circle_centre(circ, vel, table, n_circ, tb0, kc, st0, has_table, moving);
             const float lim = (mmax + circ[kc].z + pc.ego_rmax) * 1.0001f + 1e-4f;
+            const float ext = tb1 != tb0 && (has_table || moving) ? disp[kc] * (float)(tb1 - tb0) : 0.0f;
             const float dx = fmaxf(fmaxf(bx0 - cc.x, cc.x - bx1), 0.0f);
             const float dy = fmaxf(fmaxf(by0 - cc.y, cc.y - by1), 0.0f);
-            hit = lim > 0.0f && fmaf(dx, dx, dy * dy) <= lim * lim;
+            hit = lim > 0.0f && fmaf(dx, dx, dy * dy) <= (lim + ext) * (lim + ext);
         }
         unsigned m = __ballot_sync(0xffffffffu, hit);
         for (int j = 0; m; ++j) {
@@ -442,7 +473,7 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4*
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     if (e >= pc.n_ego) break;
-                    const float dx = ex[e] - cc.x, dy = ey[e] - cc.y;
+                    const float dx = fmaf(pc.ego_off[e], cnth, nx) - cc.x, dy = fmaf(pc.ego_off[e], snth, ny) - cc.y;
                     const float d2 = fmaf(dx, dx, dy * dy);
                     if (d2 <= c.w) {
                         if (STATS) cnt.pair++;
@@ -455,7 +486,7 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4*
                     if (e >= pc.n_ego) break;
                     const float R = c.z + pc.ego_rad[e];
                     const float lim = mband + R;
-                    const float dx = ex[e] - cc.x, dy = ey[e] - cc.y;
+                    const float dx = fmaf(pc.ego_off[e], cnth, nx) - cc.x, dy = fmaf(pc.ego_off[e], snth, ny) - cc.y;
                     const float d2 = fmaf(dx, dx, dy * dy);
                     if (lim > 0.0f && d2 <= lim * lim) {
                         if (STATS) cnt.pair++;
@@ -468,115 +499,207 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4*
     return group_min<G>(dobj, mask);
 }
 
+// The scene blob as staged in shared memory.
+struct Scene {
+    const float4* ctl;
+    const float* c0;
+    const float2* vert;
+    const float4* seg;
+    const float* head;
+    const float4* l1;
+    const float4* l2;
+    const float4* circ;
+    const float2* vel;
+    const float* disp;
+};
+
+__device__ __forceinline__ Scene scene_of(const SceneLayout& L, const unsigned char* smem) {
+    Scene s;
+    s.ctl = reinterpret_cast<const float4*>(smem + L.off_ctl);
+    s.c0 = reinterpret_cast<const float*>(smem + L.off_c0);
+    s.vert = reinterpret_cast<const float2*>(smem + L.off_vert);
+    s.seg = reinterpret_cast<const float4*>(smem + L.off_seg);
+    s.head = reinterpret_cast<const float*>(smem + L.off_head);
+    s.l1 = reinterpret_cast<const float4*>(smem + L.off_l1);
+    s.l2 = reinterpret_cast<const float4*>(smem + L.off_l2);
+    s.circ = reinterpret_cast<const float4*>(smem + L.off_circ);
+    s.vel = reinterpret_cast<const float2*>(smem + L.off_vel);
+    s.disp = reinterpret_cast<const float*>(smem + L.off_disp);
+    return s;
+}
+
+// x_t of one rollout with compensated (Kahan) accumulation (the value of each
+// coordinate is hi - lo), the direction of its yaw and |P_t - T_P|^2.
+struct Roll {
+    float px, py, th, v, px_c, py_c, th_c, v_c, sth, cth, tdp;
+};
+
+// What the state cost of one step needs beyond the search: x_{t+1} (binary32 head and
+// compensation), its yaw direction, and the cheap terms c_target (Eq. 13), the speed
+// error, d_safe (Eq. 17) and the control cost of Eq. (8).
+struct StepIn {
+    float nx, ny, px_c, py_c, th, th_c, snth, cnth, c_target, dv, ds, qu;
+};
+
+// Eq. (5): explicit Euler from x_t to x_{t+1} under the perturbed controls of step t.
+template <bool BF16>
+__device__ __forceinline__ StepIn dyn_step(const PlanConst& pc, const float4 ct, float c0t, float2 zz, float2 tp,
+                                           Roll& r) {
+    const Perturbed pe = perturb(ct.x, ct.y, zz, pc.sig_a, pc.sig_d, pc.amin, pc.amax, pc.dmin, pc.dmax);
+    const float vt = r.v - r.v_c;
+    float acc = pe.va;
+    if (pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt) / pc.dt), pc.amin);
+    const float tn = tanf(pe.vd);
+    kahan_add(r.px, r.px_c, vt * r.cth * pc.dt);
+    kahan_add(r.py, r.py_c, vt * r.sth * pc.dt);
+    kahan_add(r.th, r.th_c, vt * tn * pc.dt_over_L);
+    kahan_add(r.v, r.v_c, acc * pc.dt);
+    StepIn s;
+    s.nx = r.px;
+    s.ny = r.py;
+    s.px_c = r.px_c;
+    s.py_c = r.py_c;
+    s.th = r.th;
+    s.th_c = r.th_c;
+    sincosf(r.th, &s.snth, &s.cnth);
+    // Eq. (13): progress towards the target point
+    const float tx = (s.nx - tp.x) - r.px_c, ty = (s.ny - tp.y) - r.py_c;
+    const float tdn = fmaf(tx, tx, ty * ty);
+    s.c_target = tdn > r.tdp ? 1.0f : 0.0f;
+    r.tdp = tdn;
+    s.dv = (r.v - pc.v_ref) - r.v_c;
+    s.ds = fmaf(pc.d_safe_c, r.v - r.v_c, pc.d_safe_0);
+    s.qu = fmaf(ct.z, pe.ea, fmaf(ct.w, pe.ed, c0t));
+    r.sth = s.snth;
+    r.cth = s.cnth;
+    return s;
+}
+
+// Weighted state cost of Eq. (18) at x_{t+1}: the closest waypoint (Eq. 12, 14, search on
+// the binary32 position from the warm start jb) and the obstacle term (Eq. 16-17).
+template <int G, bool STATS>
+__device__ __forceinline__ float state_cost(const PlanConst& pc, const SceneLayout& L, const Scene& sc,
+                                            const float2* table, const StepIn& s, int t, int tb0, int tb1,
+                                            bool has_table, bool moving, bool dconst, int lane, int lane_g,
+                                            unsigned mask, int& jb, Counters& cnt) {
+    float d2r;
+    if (pc.ref_mode == 0)
+        nearest_segment<G, STATS>(s.nx, s.ny, sc.vert, sc.seg, sc.head, sc.l1, sc.l2, L.n_seg, L.n_l1, L.n_l2, lane_g,
+                                  mask, jb, d2r, cnt);
+    else
+        nearest_vertex<G>(s.nx, s.ny, sc.vert, sc.l1, sc.l2, L.n_ref, L.n_l1, L.n_l2, lane_g, mask, jb, d2r);
+    const float thr = sc.head[min(jb, L.n_seg - 1)];
+    {
+        // c_dist on the compensated position: closest point of the winning segment or vertex
+        const float2 a = sc.vert[jb];
+        float qx = a.x, qy = a.y;
+        if (pc.ref_mode == 0) {
+            const float4 sg = sc.seg[jb];
+            const float tau = fmaf(s.nx - a.x, sg.z, (s.ny - a.y) * sg.w);
+            if (tau >= 1.0f) {
+                qx = sc.vert[jb + 1].x;
+                qy = sc.vert[jb + 1].y;
+            } else if (tau > 0.0f) {
+                qx = fmaf(tau, sg.x, a.x);
+                qy = fmaf(tau, sg.y, a.y);
+            }
+        }
+        const float dx = (s.nx - qx) - s.px_c, dy = (s.ny - qy) - s.py_c;
+        d2r = fmaf(dx, dx, dy * dy);
+    }
+    const float dyaw = wrap_pi((s.th - thr) - s.th_c);
+
+    // Eq. (16)-(17): ego circles against obstacle circles
+    const float mband = pc.collision_only ? fmaxf(s.ds, 0.0f) : s.ds;
+    float dobj = INFINITY;
+    if (L.n_circ > 0)
+        dobj = obstacle_min<G, STATS>(pc, sc.circ, sc.vel, sc.disp, table, L.n_circ, t, tb0, tb1, has_table, moving, dconst,
+                                      s.nx, s.ny, s.cnth, s.snth, mband, lane, lane_g, mask, cnt);
+    const float gap = s.ds - dobj;
+    float c_safe = gap > 0.0f ? gap * gap : 0.0f;
+    if (pc.collision_only && !(dobj <= 0.0f)) c_safe = 0.0f;
+
+    // Eq. (18) weighted state cost
+    return fmaf(pc.w_dist, d2r,
+                fmaf(pc.w_target, s.c_target,
+                     fmaf(pc.w_yaw, dyaw * dyaw, fmaf(pc.w_speed, s.dv * s.dv, pc.w_safe * c_safe))));
+}
+
 // One sample's rollout and cost (Algorithm 1 inner loop), by the G lanes of its group.
 // smem holds the staged scene blob; z the noise [T][K]; x0 = (0, 0, yaw0, v0) in the local
 // frame; jb0 the segment closest to x0; S[k] receives the cost.  Every lane of the warp
 // must call it (the broad phase and the group reductions are warp / group collective).
-template <int G, bool BF16, bool STATS>
+//
+// TIME = false: the G lanes run the dynamics redundantly (identical bits) and split the
+// reference search and the obstacle pairs of every step, combining with shuffles.
+// TIME = true: the G lanes split the steps.  Every lane integrates the dynamics of all
+// steps (identical bits); lane p evaluates the state cost of the steps t0 + p of each
+// block of G steps (the reference search warm-started from its own previous step) and
+// the step costs are added in step order, so S is bit for bit that of G = 1.
+template <int G, bool TIME, bool BF16, bool STATS>
 __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneLayout& L, const unsigned char* smem,
                                                const typename NoiseT<BF16>::type* __restrict__ z,
                                                const float2* table, float4 x0, bool moving, int jb0, int k,
                                                double* S_out, unsigned long long* stats) {
-    const float4* ctl = reinterpret_cast<const float4*>(smem + L.off_ctl);
-    const float* c0 = reinterpret_cast<const float*>(smem + L.off_c0);
-    const float2* vert = reinterpret_cast<const float2*>(smem + L.off_vert);
-    const float4* seg = reinterpret_cast<const float4*>(smem + L.off_seg);
-    const float* head = reinterpret_cast<const float*>(smem + L.off_head);
-    const float4* l1 = reinterpret_cast<const float4*>(smem + L.off_l1);
-    const float4* l2 = reinterpret_cast<const float4*>(smem + L.off_l2);
-    const float4* circ = reinterpret_cast<const float4*>(smem + L.off_circ);
-    const float2* vel = reinterpret_cast<const float2*>(smem + L.off_vel);
-
+    const Scene sc = scene_of(L, smem);
     const int lane = threadIdx.x & 31;
     const int lane_g = threadIdx.x & (G - 1);
     const unsigned mask = group_mask<G>();
     const int K = pc.K, T = pc.T;
     const int kk = min(k, K - 1);               // whole groups past K run along (shuffle safety)
     const bool has_table = pc.has_table != 0;
-    const float2 tp = vert[L.n_ref - 1];        // target point T_P: last vertex
+    const float2 tp = sc.vert[L.n_ref - 1];     // target point T_P: last vertex
     const bool dconst = pc.d_safe_c == 0.0f && pc.ego_same_radius;
 
-    // x_t with compensated (Kahan) accumulation; the value of each coordinate is hi - lo
-    float px = x0.x, py = x0.y, th = x0.z, v = x0.w;
-    float px_c = 0.0f, py_c = 0.0f, th_c = 0.0f, v_c = 0.0f;
-    float sth, cth;
-    sincosf(th, &sth, &cth);
-    float tdp = fmaf(tp.x, tp.x, tp.y * tp.y);   // |P_0 - T_P|^2 with P_0 = (0, 0)
+    Roll r;
+    r.px = x0.x;
+    r.py = x0.y;
+    r.th = x0.z;
+    r.v = x0.w;
+    r.px_c = r.py_c = r.th_c = r.v_c = 0.0f;
+    sincosf(r.th, &r.sth, &r.cth);
+    r.tdp = fmaf(tp.x, tp.x, tp.y * tp.y);      // |P_0 - T_P|^2 with P_0 = (0, 0)
     int jb = jb0;
     float s_hi = 0.0f, s_c = 0.0f, q_last = 0.0f;
     Counters cnt{0, 0, 0, 0, 0, 0, 0};
 
-    for (int t = 0; t < T; ++t) {
-        const float4 ct = ctl[t];
-        const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
-        const Perturbed pe = perturb(ct.x, ct.y, zz, pc.sig_a, pc.sig_d, pc.amin, pc.amax, pc.dmin, pc.dmax);
-        const float vt = v - v_c;
-        float acc = pe.va;
-        if (pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt) / pc.dt), pc.amin);
-        // Eq. (5), explicit Euler from x_t
-        const float tn = tanf(pe.vd);
-        kahan_add(px, px_c, vt * cth * pc.dt);
-        kahan_add(py, py_c, vt * sth * pc.dt);
-        kahan_add(th, th_c, vt * tn * pc.dt_over_L);
-        kahan_add(v, v_c, acc * pc.dt);
-        const float nx = px, ny = py;
-        float snth, cnth;
-        sincosf(th, &snth, &cnth);
-
-        // Eq. (12), (14): closest waypoint (search on the binary32 position) and reference yaw
-        float d2r;
-        if (pc.ref_mode == 0)
-            nearest_segment<G, STATS>(nx, ny, vert, seg, head, l1, l2, L.n_seg, L.n_l1, L.n_l2, lane_g, mask, jb,
-                                      d2r, cnt);
-        else
-            nearest_vertex<G>(nx, ny, vert, l1, l2, L.n_ref, L.n_l1, L.n_l2, lane_g, mask, jb, d2r);
-        const float thr = head[min(jb, L.n_seg - 1)];
-        {
-            // c_dist on the compensated position: closest point of the winning segment or vertex
-            const float2 a = vert[jb];
-            float qx = a.x, qy = a.y;
-            if (pc.ref_mode == 0) {
-                const float4 sg = seg[jb];
-                const float tau = fmaf(nx - a.x, sg.z, (ny - a.y) * sg.w);
-                if (tau >= 1.0f) {
-                    qx = vert[jb + 1].x;
-                    qy = vert[jb + 1].y;
-                } else if (tau > 0.0f) {
-                    qx = fmaf(tau, sg.x, a.x);
-                    qy = fmaf(tau, sg.y, a.y);
+    if constexpr (!TIME) {
+        for (int t = 0; t < T; ++t) {
+            const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
+            const StepIn s = dyn_step<BF16>(pc, sc.ctl[t], sc.c0[t], zz, tp, r);
+            const float qx = state_cost<G, STATS>(pc, L, sc, table, s, t, t, t, has_table, moving, dconst, lane,
+                                                  lane_g, mask, jb, cnt);
+            kahan_add(s_hi, s_c, qx + s.qu);    // Eq. (6)
+            q_last = qx;
+        }
+    } else {
+        for (int t0 = 0; t0 < T; t0 += G) {
+            // past the last step a lane re-evaluates step T - 1 (the warp stays converged)
+            const int my = min(lane_g, T - 1 - t0);
+            StepIn e;
+#pragma unroll 1
+            for (int j = 0; j < G; ++j) {
+                if (t0 + j < T) {
+                    const int t = t0 + j;
+                    const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
+                    const StepIn s = dyn_step<BF16>(pc, sc.ctl[t], sc.c0[t], zz, tp, r);
+                    if (j == my) e = s;
                 }
             }
-            const float dx = (nx - qx) - px_c, dy = (ny - qy) - py_c;
-            d2r = fmaf(dx, dx, dy * dy);
+            const int tb1 = min(t0 + G - 1, T - 1);
+            const float qx = state_cost<1, STATS>(pc, L, sc, table, e, t0 + my, t0, tb1, has_table, moving, dconst,
+                                                  lane, 0, mask, jb, cnt);
+            const float c = qx + e.qu;
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                const float cj = __shfl_sync(mask, c, j, G);
+                const float qj = __shfl_sync(mask, qx, j, G);
+                if (t0 + j < T) {
+                    kahan_add(s_hi, s_c, cj);   // Eq. (6), in step order
+                    q_last = qj;
+                }
+            }
         }
-        // Eq. (13): progress towards the target point
-        const float tx = (nx - tp.x) - px_c, ty = (ny - tp.y) - py_c;
-        const float tdn = fmaf(tx, tx, ty * ty);
-        const float c_target = tdn > tdp ? 1.0f : 0.0f;
-        tdp = tdn;
-        const float dyaw = wrap_pi((th - thr) - th_c);
-        const float dv = (v - pc.v_ref) - v_c;
-
-        // Eq. (16)-(17): ego circles against obstacle circles
-        const float ds = fmaf(pc.d_safe_c, v - v_c, pc.d_safe_0);
-        const float mband = pc.collision_only ? fmaxf(ds, 0.0f) : ds;
-        float dobj = INFINITY;
-        if (L.n_circ > 0)
-            dobj = obstacle_min<G, STATS>(pc, circ, vel, table, L.n_circ, t, has_table, moving, dconst, nx, ny,
-                                          cnth, snth, mband, lane, lane_g, mask, cnt);
-        const float gap = ds - dobj;
-        float c_safe = gap > 0.0f ? gap * gap : 0.0f;
-        if (pc.collision_only && !(dobj <= 0.0f)) c_safe = 0.0f;
-
-        // Eq. (18) weighted state cost, Eq. (8) control cost
-        const float qx = fmaf(pc.w_dist, d2r,
-                              fmaf(pc.w_target, c_target,
-                                   fmaf(pc.w_yaw, dyaw * dyaw, fmaf(pc.w_speed, dv * dv, pc.w_safe * c_safe))));
-        const float qu = fmaf(ct.z, pe.ea, fmaf(ct.w, pe.ed, c0[t]));
-        kahan_add(s_hi, s_c, qx + qu);          // Eq. (6)
-        q_last = qx;
-        sth = snth;
-        cth = cnth;
     }
     if (lane_g == 0 && k < K) {
         double S = (double)s_hi - (double)s_c;

@@ -35,6 +35,7 @@ SceneLayout make_layout(int T, int n_ref, int n_circ) {
     L.off_l2 = o;   o = align16(o + 16 * L.n_l2);
     L.off_circ = o; o = align16(o + 16 * n_circ);
     L.off_vel = o;  o = align16(o + 8 * n_circ);
+    L.off_disp = o; o = align16(o + 4 * n_circ);
     L.bytes = o;
     return L;
 }
@@ -71,15 +72,15 @@ __global__ void philox_kernel(uint2 key, const uint4* ctr, uint4* out, int n) {
     if (i < n) out[i] = philox4x32_10(ctr[i], key);
 }
 
-template <int G, bool BF16, bool STATS>
-__global__ void __launch_bounds__(512, 1) rollout_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
+template <int G, bool TIME, bool BF16, bool STATS>
+__global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 2) rollout_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
                                                         const typename NoiseT<BF16>::type* __restrict__ z) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long bar;
     if (!stage_to_smem(smem, b.scene, L.bytes, &bar, &b.state->flags)) return;
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) / G;
-    rollout_sample<G, BF16, STATS>(pc, L, smem, z, b.table, b.state->x0f, b.state->moving != 0,
-                                   (int)(b.state->jkey & 0xffffffffu), k, b.S, b.stats);
+    rollout_sample<G, TIME, BF16, STATS>(pc, L, smem, z, b.table, b.state->x0f, b.state->moving != 0,
+                                         (int)(b.state->jkey & 0xffffffffu), k, b.S, b.stats);
 }
 
 // -----------------------------------------------------------------------------
@@ -163,20 +164,21 @@ __global__ void __launch_bounds__(1024) finalize_kernel(PlanConst pc, PlanBuffer
 // -----------------------------------------------------------------------------
 // host-side launchers
 // -----------------------------------------------------------------------------
-template <int G, bool BF16, bool STATS = false>
+template <int G, bool TIME, bool BF16, bool STATS = false>
 static cudaError_t launch_rollout_t(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int threads,
                                     cudaStream_t st) {
     const size_t smem = rollout_smem_bytes(L);
     static int configured_smem = -1;
     if (configured_smem < (int)smem) {
-        cudaError_t e = cudaFuncSetAttribute(rollout_kernel<G, BF16, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(rollout_kernel<G, TIME, BF16, STATS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(smem < 48 * 1024 ? 48 * 1024 : smem));
         if (e != cudaSuccess) return e;
         configured_smem = (int)(smem < 48 * 1024 ? 48 * 1024 : smem);
     }
     const long long total = (long long)pc.K * G;
     const int blocks = (int)((total + threads - 1) / threads);
-    rollout_kernel<G, BF16, STATS><<<blocks, threads, smem, st>>>(
+    rollout_kernel<G, TIME, BF16, STATS><<<blocks, threads, smem, st>>>(
         pc, L, b, reinterpret_cast<const typename NoiseT<BF16>::type*>(b.z));
     return cudaGetLastError();
 }
@@ -185,54 +187,58 @@ template <bool BF16>
 static cudaError_t launch_rollout_b(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int group,
                                     int threads, cudaStream_t st) {
     switch (group) {
-        case 1: return launch_rollout_t<1, BF16>(pc, L, b, threads, st);
-        case 2: return launch_rollout_t<2, BF16>(pc, L, b, threads, st);
-        case 4: return launch_rollout_t<4, BF16>(pc, L, b, threads, st);
-        case 8: return launch_rollout_t<8, BF16>(pc, L, b, threads, st);
-        case 16: return launch_rollout_t<16, BF16>(pc, L, b, threads, st);
-        case 32: return launch_rollout_t<32, BF16>(pc, L, b, threads, st);
+        case 1: return launch_rollout_t<1, false, BF16>(pc, L, b, threads, st);
+        case 2: return launch_rollout_t<2, false, BF16>(pc, L, b, threads, st);
+        case 4: return launch_rollout_t<4, false, BF16>(pc, L, b, threads, st);
+        case 8: return launch_rollout_t<8, false, BF16>(pc, L, b, threads, st);
+        case 16: return launch_rollout_t<16, false, BF16>(pc, L, b, threads, st);
+        case 32: return launch_rollout_t<32, false, BF16>(pc, L, b, threads, st);
+        case -2: return launch_rollout_t<2, true, BF16>(pc, L, b, threads, st);
+        case -4: return launch_rollout_t<4, true, BF16>(pc, L, b, threads, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <int G, bool BF16>
+template <int G, bool TIME, bool BF16>
 static int max_blocks_t(int threads, size_t smem) {
     int n = 0;
-    if (cudaFuncSetAttribute(rollout_kernel<G, BF16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(rollout_kernel<G, TIME, BF16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(smem < 48 * 1024 ? 48 * 1024 : smem)) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_kernel<G, BF16, false>, threads, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_kernel<G, TIME, BF16, false>, threads, smem) !=
+        cudaSuccess)
         return 0;
     return n;
 }
 
-int rollout_max_blocks_per_sm(int group, int threads, int noise_bf16, size_t smem) {
-    switch (group * 2 + (noise_bf16 ? 1 : 0)) {
-        case 2: return max_blocks_t<1, false>(threads, smem);
-        case 3: return max_blocks_t<1, true>(threads, smem);
-        case 4: return max_blocks_t<2, false>(threads, smem);
-        case 5: return max_blocks_t<2, true>(threads, smem);
-        case 8: return max_blocks_t<4, false>(threads, smem);
-        case 9: return max_blocks_t<4, true>(threads, smem);
-        case 16: return max_blocks_t<8, false>(threads, smem);
-        case 17: return max_blocks_t<8, true>(threads, smem);
-        case 32: return max_blocks_t<16, false>(threads, smem);
-        case 33: return max_blocks_t<16, true>(threads, smem);
-        case 64: return max_blocks_t<32, false>(threads, smem);
-        case 65: return max_blocks_t<32, true>(threads, smem);
+template <bool BF16>
+static int max_blocks_b(int group, int threads, size_t smem) {
+    switch (group) {
+        case 1: return max_blocks_t<1, false, BF16>(threads, smem);
+        case 2: return max_blocks_t<2, false, BF16>(threads, smem);
+        case 4: return max_blocks_t<4, false, BF16>(threads, smem);
+        case 8: return max_blocks_t<8, false, BF16>(threads, smem);
+        case 16: return max_blocks_t<16, false, BF16>(threads, smem);
+        case 32: return max_blocks_t<32, false, BF16>(threads, smem);
+        case -2: return max_blocks_t<2, true, BF16>(threads, smem);
+        case -4: return max_blocks_t<4, true, BF16>(threads, smem);
         default: return 0;
     }
 }
 
+int rollout_max_blocks_per_sm(int group, int threads, int noise_bf16, size_t smem) {
+    return noise_bf16 ? max_blocks_b<true>(group, threads, smem) : max_blocks_b<false>(group, threads, smem);
+}
+
 cudaError_t launch_rollout_stats(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int noise_bf16,
                                  cudaStream_t st) {
-    return noise_bf16 ? launch_rollout_t<1, true, true>(pc, L, b, 128, st)
-                      : launch_rollout_t<1, false, true>(pc, L, b, 128, st);
+    return noise_bf16 ? launch_rollout_t<1, false, true, true>(pc, L, b, 128, st)
+                      : launch_rollout_t<1, false, false, true>(pc, L, b, 128, st);
 }
 
 cudaError_t launch_rollout(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int group,
                            int threads, int noise_bf16, cudaStream_t st) {
-    if (threads < 32 || threads > 512 || threads % 32 != 0) return cudaErrorInvalidValue;
+    if (threads < 32 || threads > MAX_ROLLOUT_THREADS || threads % 32 != 0) return cudaErrorInvalidValue;
     return noise_bf16 ? launch_rollout_b<true>(pc, L, b, group, threads, st)
                       : launch_rollout_b<false>(pc, L, b, group, threads, st);
 }

@@ -79,7 +79,8 @@ def test_bf16_noise_is_the_rounded_normal():
 
 # ----------------------------------------------------------------------------- one iteration
 
-@pytest.mark.parametrize("K,T,group", [(1024, 50, 0), (1000, 37, 1), (777, 33, 4), (257, 13, 32), (1, 5, 0)])
+@pytest.mark.parametrize("K,T,group", [(1024, 50, 0), (1000, 37, 1), (777, 33, 4), (257, 13, 32), (1, 5, 0),
+                                       (1000, 37, -2), (777, 33, -4), (3, 2, -4)])
 def test_single_plan_parity(K, T, group):
     prob = sc.single_plan()
     prob.params.update(K=K, T=T, group=group)
@@ -149,16 +150,31 @@ def test_closed_loop_full_K():
     print("closed_loop", rep)
 
 
-def test_groups_give_identical_costs():
-    prob = sc.closed_loop()
-    prob.params.update(K=512, T=40)
+@pytest.mark.parametrize("scene,obstacles", [("lane", "table"), ("lane", "velocity"), ("lane", "static"),
+                                             ("close", "velocity"), ("close", "table")])
+def test_groups_give_identical_costs(scene, obstacles):
+    """Every lane split (of the work of a step, or of the steps) gives the costs of one
+    lane per sample bit for bit; T = 39 leaves a ragged last block of steps.  "close"
+    puts moving obstacles inside the safety band of most rollouts."""
+    if scene == "lane":
+        prob = sc.closed_loop()
+        prob.params.update(K=512, T=39)
+    else:
+        prob = sc.tiny(K=1500, T=39, n_ref=60, n_obs=3, moving=True)
+        prob.params["d_safe_0"] = 2.0
+    if obstacles == "table":
+        prob.centres = sc.predicted_centres(prob.circles, prob.T, prob.params["dt"])
+    else:
+        prob.centres = None
+    if obstacles == "static":
+        prob.circles[:, 3:] = 0.0
     S = {}
-    for g in (1, 2, 4, 8, 16, 32):
+    for g in (1, 2, 4, 8, 16, 32, -2, -4):
         p = dict(prob.params, group=g)
         outs, _, _, _ = run_gpu(prob, params=p)
         S[g] = outs[0][3]
-    for g in (2, 4, 8, 16, 32):
-        np.testing.assert_array_equal(S[g], S[1])
+    for g in (2, 4, 8, 16, 32, -2, -4):
+        np.testing.assert_array_equal(S[g], S[1], err_msg=f"group {g}")
 
 
 @pytest.mark.parametrize("variant", ["vertex", "collision_only", "vcap", "gamma", "terminal", "dsafe_v",
