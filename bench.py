@@ -55,10 +55,11 @@ def brute_force_ops_per_step(prob) -> float:
 # compensated sums, sincos and tan, cost terms, control cost, ego circles and the warp
 # box of the broad phase) and, per unit counted by mppi_rollout_stats, a box bound, a
 # segment distance with its key minimum, a broad-phase circle test, a candidate circle
-# (three pair distances and band tests) and an in-band pair (sqrt, subtract, min).
+# (three pair distances, their minimum and the band test) and an in-band circle (sqrt,
+# subtract, min).
 OPS_CORE = 150.0
-OPS_PER = {"l2_boxes": 12.0, "l1_boxes": 12.0, "segments": 13.0, "refinements": 40.0,
-           "circles_tested": 15.0, "candidates": 17.0, "pairs_in_band": 4.0}
+OPS_PER = {"group_boxes": 12.0, "chunk_boxes": 12.0, "segments": 13.0, "refinements": 40.0,
+           "circles_tested": 15.0, "candidates": 17.0, "in_band": 4.0}
 
 
 def executed_ops_per_step(stats) -> float:

@@ -250,8 +250,8 @@ class Planner:
         _check(rc, self._h)
         return g.value, b.value
 
-    STAT_NAMES = ("l2_boxes", "l1_boxes", "segments", "refinements", "circles_tested", "candidates",
-                  "pairs_in_band")
+    STAT_NAMES = ("group_boxes", "chunk_boxes", "segments", "refinements", "circles_tested", "candidates",
+                  "in_band")
 
     def rollout_stats(self, x0, ref, circles=None, centres=None) -> Dict[str, float]:
         """Work counters of the pruned searches, per rollout-step."""

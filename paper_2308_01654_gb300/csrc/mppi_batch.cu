@@ -182,8 +182,9 @@ __global__ void __launch_bounds__(512, 1) batch_rollout_kernel(BatchArgs a) {
                 bulk_issue(smem, a.scene + d.scene_off, d.L.bytes, &bar);
             }
             __syncthreads();
-            if (!bulk_wait(&bar, phase, &a.hdr->flags)) return;
+            if (!__syncthreads_and(bulk_wait(&bar, phase, &a.hdr->flags))) return;
             phase ^= 1u;
+            build_l2(smem, s_L);
         }
         const BatchInst& d = a.inst[td.x];
         const int k = td.y + (int)threadIdx.x / G;
@@ -362,7 +363,7 @@ struct mppi_batch {
     int device = 0;
     int max_slots = 0, max_batch = 0, max_T = 0, max_ref = 0, max_circ = 0, noise_bf16 = 0;
     long long max_samples = 0, max_steps = 0, max_tiles = 0;
-    size_t max_scene = 0, max_in = 0, max_out = 0, stage_bytes = 0, out_bytes = 0;
+    size_t max_scene = 0, rollout_smem = 0, max_in = 0, max_out = 0, stage_bytes = 0, out_bytes = 0;
     // offsets inside the staging buffer
     size_t off_inst = 0, off_npre = 0, off_wpre = 0, off_tiles = 0, off_in = 0;
     DevState* slots = nullptr;
@@ -437,6 +438,7 @@ int mppi_batch_create(int32_t max_slots, int32_t max_batch, int64_t max_samples,
     B->max_tiles = max_samples / 16 + max_batch;
     const SceneLayout Lmax = make_layout(max_T, max_ref, max_circ);
     B->max_scene = up((size_t)Lmax.bytes);
+    B->rollout_smem = up(rollout_smem_bytes(Lmax));   // blob and level-2 boxes
     B->max_in = 4 + 2 * (size_t)max_ref + 5 * (size_t)max_circ + 2 * (size_t)max_T * max_circ;
     B->max_out = out_elems(max_T);
     auto bail = [&](int st) {
@@ -447,6 +449,10 @@ int mppi_batch_create(int32_t max_slots, int32_t max_batch, int64_t max_samples,
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return bail(bfail(nullptr, MPPI_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e)));
     cudaDeviceGetAttribute(&B->n_sm, cudaDevAttrMultiProcessorCount, device);
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (B->rollout_smem + 1024 > (size_t)max_smem)
+        return bail(bfail(nullptr, MPPI_ERR_CAPACITY, "scene of max_T, max_ref, max_circ exceeds shared memory"));
     // staging layout
     size_t o = up(sizeof(BatchHeader));
     B->off_inst = o;  o += up(sizeof(BatchInst) * (size_t)max_batch);
@@ -632,7 +638,7 @@ static cudaError_t enqueue_kernels(mppi_batch* B, Pipeline& p, int per_sm) {
     else batch_noise_kernel<false><<<grid, 256, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(&a.hdr->tile_counter, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
-    const size_t smem = B->max_scene;
+    const size_t smem = B->rollout_smem;
     if (B->noise_bf16) e = launch_batch_rollout_b<true>(a, B->G, B->threads, B->n_sm * per_sm, smem, st);
     else e = launch_batch_rollout_b<false>(a, B->G, B->threads, B->n_sm * per_sm, smem, st);
     if (e != cudaSuccess) return e;
@@ -655,7 +661,7 @@ static cudaError_t ensure_graph(mppi_batch* B, Pipeline& p) {
         p.graph = nullptr;
     }
     // configure function attributes outside the capture
-    const int per_sm = batch_max_blocks(B->G, B->noise_bf16, B->threads, B->max_scene);
+    const int per_sm = batch_max_blocks(B->G, B->noise_bf16, B->threads, B->rollout_smem);
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(p.stream, cudaStreamCaptureModeThreadLocal);
@@ -780,7 +786,7 @@ int mppi_batch_autotune(mppi_batch* B, mppi_request* req, int32_t n, int32_t* gr
         for (int si = 0; si < 4 && e == cudaSuccess; ++si) {
             const int G = groups[gi], th = sizes[si];
             if (th / G < 16) continue;   // at least 16 samples per tile
-            const int per_sm = batch_max_blocks(G, B->noise_bf16, th, B->max_scene);
+            const int per_sm = batch_max_blocks(G, B->noise_bf16, th, B->rollout_smem);
             if (per_sm < 1) continue;
             B->G = G;
             B->threads = th;
@@ -792,8 +798,8 @@ int mppi_batch_autotune(mppi_batch* B, mppi_request* req, int32_t n, int32_t* gr
                 if (e == cudaSuccess) e = cudaMemsetAsync(&p.args.hdr->tile_counter, 0, sizeof(unsigned), p.stream);
                 if (e == cudaSuccess) e = cudaEventRecord(e0, p.stream);
                 if (e == cudaSuccess)
-                    e = B->noise_bf16 ? launch_batch_rollout_b<true>(p.args, G, th, B->n_sm * per_sm, B->max_scene, p.stream)
-                                      : launch_batch_rollout_b<false>(p.args, G, th, B->n_sm * per_sm, B->max_scene, p.stream);
+                    e = B->noise_bf16 ? launch_batch_rollout_b<true>(p.args, G, th, B->n_sm * per_sm, B->rollout_smem, p.stream)
+                                      : launch_batch_rollout_b<false>(p.args, G, th, B->n_sm * per_sm, B->rollout_smem, p.stream);
                 if (e == cudaSuccess) e = cudaEventRecord(e1, p.stream);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);

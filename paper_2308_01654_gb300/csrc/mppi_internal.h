@@ -31,14 +31,13 @@ struct __align__(16) DevState {
 // Byte offsets of the arrays in the scene blob that the rollout kernel stages into
 // shared memory with one bulk copy.  Every offset is a multiple of 16.
 struct SceneLayout {
-    int T, n_ref, n_seg, n_l1, n_l2, n_circ;
+    int T, n_ref, n_seg, n_l1, n_l2, n_circ;   // chunks of REF_L1 segments, groups of REF_L2 chunks
     int off_ctl;     // float4 [T]       (u_a, u_d, g_a, g_d): nominal controls and control-cost slopes
     int off_c0;      // float  [T]       1/2 u^T R u
     int off_vert;    // float2 [n_ref]   vertices, local frame
     int off_seg;     // float4 [n_seg]   (ex, ey, ex/|e|^2, ey/|e|^2)
     int off_head;    // float  [n_seg]   heading of each segment
     int off_l1;      // float4 [n_l1]    level-1 chunk boxes
-    int off_l2;      // float4 [n_l2]    level-2 group boxes
     int off_circ;    // float4 [n_circ]  (x, y, r, (d_safe_0 + r + r_ego)^2 when d_safe is constant)
     int off_vel;     // float2 [n_circ]  velocities
     int off_disp;    // float  [n_circ]  bound on the distance a centre moves in one step

@@ -42,7 +42,6 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
     float4* seg = reinterpret_cast<float4*>(sc + L.off_seg);
     float* head = reinterpret_cast<float*>(sc + L.off_head);
     float4* l1 = reinterpret_cast<float4*>(sc + L.off_l1);
-    float4* l2 = reinterpret_cast<float4*>(sc + L.off_l2);
     float4* circ = reinterpret_cast<float4*>(sc + L.off_circ);
     float2* vel = reinterpret_cast<float2*>(sc + L.off_vel);
     float* disp = reinterpret_cast<float*>(sc + L.off_disp);
@@ -85,25 +84,7 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
         }
         l1[c] = bb;
     }
-    // level-2 boxes: one warp per group, the lanes stride over its vertices
     const int lane = tid & 31, wid = tid >> 5, nwarps = nth >> 5;
-    for (int g = wid; g < L.n_l2; g += nwarps) {
-        const int v0 = g * REF_L1 * REF_L2, v1 = min(v0 + REF_L1 * REF_L2, L.n_seg);
-        float4 bb = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
-        for (int j = v0 + lane; j <= v1; j += 32) {
-            const float2 p = local_vertex(in.ref, j, ox, oy);
-            bb.x = fminf(bb.x, p.x); bb.y = fminf(bb.y, p.y);
-            bb.z = fmaxf(bb.z, p.x); bb.w = fmaxf(bb.w, p.y);
-        }
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            bb.x = fminf(bb.x, __shfl_xor_sync(0xffffffffu, bb.x, o));
-            bb.y = fminf(bb.y, __shfl_xor_sync(0xffffffffu, bb.y, o));
-            bb.z = fmaxf(bb.z, __shfl_xor_sync(0xffffffffu, bb.z, o));
-            bb.w = fmaxf(bb.w, __shfl_xor_sync(0xffffffffu, bb.w, o));
-        }
-        if (lane == 0) l2[g] = bb;
-    }
     for (int k = tid; k < L.n_circ; k += nth) {
         const double* c = in.circ + 5 * k;
         for (int j = 0; j < 5; ++j) bad |= !isfinite(c[j]);
@@ -283,6 +264,28 @@ __device__ __forceinline__ void scan_chunk(float px, float py, const float2* ver
             best = k < best ? k : best;
         }
     }
+}
+
+// Level-2 boxes (each the union of REF_L2 chunk boxes), built by each rollout block in
+// shared memory right after the staged blob.
+__device__ __forceinline__ const float4* l2_boxes(const unsigned char* smem, const SceneLayout& L) {
+    return reinterpret_cast<const float4*>(smem + L.bytes);
+}
+
+__device__ __forceinline__ void build_l2(unsigned char* smem, const SceneLayout& L) {
+    const float4* l1 = reinterpret_cast<const float4*>(smem + L.off_l1);
+    float4* l2 = reinterpret_cast<float4*>(smem + L.bytes);
+    for (int g = threadIdx.x; g < L.n_l2; g += blockDim.x) {
+        float4 a = l1[g * REF_L2];
+        const int c1 = min((g + 1) * REF_L2, L.n_l1);
+        for (int c = g * REF_L2 + 1; c < c1; ++c) {
+            const float4 q = l1[c];
+            a.x = fminf(a.x, q.x); a.y = fminf(a.y, q.y);
+            a.z = fmaxf(a.z, q.z); a.w = fmaxf(a.w, q.w);
+        }
+        l2[g] = a;
+    }
+    __syncthreads();
 }
 
 // Closest point of the polyline (ties -> lowest segment).  The chunk of the previous
@@ -470,15 +473,18 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4*
             const float4 c = circ[kc2];
             const float2 cc = circle_centre(circ, vel, table, n_circ, t, kc2, st, has_table, moving);
             if (dconst) {
+                // equal ego radii: the closest ego circle gives the pair minimum (sqrt and the
+                // subtraction are monotone), one square root per circle
+                float d2m = INFINITY;
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     if (e >= pc.n_ego) break;
                     const float dx = fmaf(pc.ego_off[e], cnth, nx) - cc.x, dy = fmaf(pc.ego_off[e], snth, ny) - cc.y;
-                    const float d2 = fmaf(dx, dx, dy * dy);
-                    if (d2 <= c.w) {
-                        if (STATS) cnt.pair++;
-                        dobj = fminf(dobj, sqrtf(d2) - (c.z + pc.ego_rad[e]));
-                    }
+                    d2m = fminf(d2m, fmaf(dx, dx, dy * dy));
+                }
+                if (d2m <= c.w) {
+                    if (STATS) cnt.pair++;
+                    dobj = fminf(dobj, sqrtf(d2m) - (c.z + pc.ego_rad[0]));
                 }
             } else {
 #pragma unroll
@@ -499,15 +505,15 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4*
     return group_min<G>(dobj, mask);
 }
 
-// The scene blob as staged in shared memory.
+// The scene blob as staged in shared memory (base: its first byte; the level-2 boxes follow it).
 struct Scene {
+    const unsigned char* base;
     const float4* ctl;
     const float* c0;
     const float2* vert;
     const float4* seg;
     const float* head;
     const float4* l1;
-    const float4* l2;
     const float4* circ;
     const float2* vel;
     const float* disp;
@@ -515,13 +521,13 @@ struct Scene {
 
 __device__ __forceinline__ Scene scene_of(const SceneLayout& L, const unsigned char* smem) {
     Scene s;
+    s.base = smem;
     s.ctl = reinterpret_cast<const float4*>(smem + L.off_ctl);
     s.c0 = reinterpret_cast<const float*>(smem + L.off_c0);
     s.vert = reinterpret_cast<const float2*>(smem + L.off_vert);
     s.seg = reinterpret_cast<const float4*>(smem + L.off_seg);
     s.head = reinterpret_cast<const float*>(smem + L.off_head);
     s.l1 = reinterpret_cast<const float4*>(smem + L.off_l1);
-    s.l2 = reinterpret_cast<const float4*>(smem + L.off_l2);
     s.circ = reinterpret_cast<const float4*>(smem + L.off_circ);
     s.vel = reinterpret_cast<const float2*>(smem + L.off_vel);
     s.disp = reinterpret_cast<const float*>(smem + L.off_disp);
@@ -584,10 +590,11 @@ __device__ __forceinline__ float state_cost(const PlanConst& pc, const SceneLayo
                                             unsigned mask, int& jb, Counters& cnt) {
     float d2r;
     if (pc.ref_mode == 0)
-        nearest_segment<G, STATS>(s.nx, s.ny, sc.vert, sc.seg, sc.head, sc.l1, sc.l2, L.n_seg, L.n_l1, L.n_l2, lane_g,
-                                  mask, jb, d2r, cnt);
+        nearest_segment<G, STATS>(s.nx, s.ny, sc.vert, sc.seg, sc.head, sc.l1, l2_boxes(sc.base, L), L.n_seg, L.n_l1,
+                                  L.n_l2, lane_g, mask, jb, d2r, cnt);
     else
-        nearest_vertex<G>(s.nx, s.ny, sc.vert, sc.l1, sc.l2, L.n_ref, L.n_l1, L.n_l2, lane_g, mask, jb, d2r);
+        nearest_vertex<G>(s.nx, s.ny, sc.vert, sc.l1, l2_boxes(sc.base, L), L.n_ref, L.n_l1, L.n_l2, lane_g, mask, jb,
+                          d2r);
     const float thr = sc.head[min(jb, L.n_seg - 1)];
     {
         // c_dist on the compensated position: closest point of the winning segment or vertex

@@ -32,7 +32,6 @@ SceneLayout make_layout(int T, int n_ref, int n_circ) {
     L.off_seg = o;  o = align16(o + 16 * L.n_seg);
     L.off_head = o; o = align16(o + 4 * L.n_seg);
     L.off_l1 = o;   o = align16(o + 16 * L.n_l1);
-    L.off_l2 = o;   o = align16(o + 16 * L.n_l2);
     L.off_circ = o; o = align16(o + 16 * n_circ);
     L.off_vel = o;  o = align16(o + 8 * n_circ);
     L.off_disp = o; o = align16(o + 4 * n_circ);
@@ -40,7 +39,8 @@ SceneLayout make_layout(int T, int n_ref, int n_circ) {
     return L;
 }
 
-size_t rollout_smem_bytes(const SceneLayout& L) { return (size_t)L.bytes; }
+// the staged blob and the level-2 boxes built after it
+size_t rollout_smem_bytes(const SceneLayout& L) { return (size_t)L.bytes + (size_t)16 * L.n_l2; }
 
 // -----------------------------------------------------------------------------
 // prep: one pass over the inputs.  Positions are shifted into a frame centred on
@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 2) rollout_kernel(PlanCon
                                                         const typename NoiseT<BF16>::type* __restrict__ z) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long bar;
-    if (!stage_to_smem(smem, b.scene, L.bytes, &bar, &b.state->flags)) return;
+    if (!__syncthreads_and(stage_to_smem(smem, b.scene, L.bytes, &bar, &b.state->flags))) return;
+    build_l2(smem, L);
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     rollout_sample<G, TIME, BF16, STATS>(pc, L, smem, z, b.table, b.state->x0f, b.state->moving != 0,
                                          (int)(b.state->jkey & 0xffffffffu), k, b.S, b.stats);

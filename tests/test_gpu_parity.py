@@ -328,11 +328,11 @@ def test_rollout_stats_are_consistent_and_leave_state():
         np.testing.assert_array_equal(U, U0)
         assert it == 3
         n_l2 = math.ceil(math.ceil((prob.ref.shape[0] - 1) / 16) / 16)
-        assert st["l2_boxes"] == pytest.approx(n_l2)            # every level-2 box is tested every step
+        assert st["group_boxes"] == pytest.approx(n_l2)         # every level-2 box is tested every step
         assert 1 <= st["segments"] <= prob.ref.shape[0]
         # the broad phase tests one circle per lane per 32-circle chunk
         assert st["circles_tested"] == pytest.approx(math.ceil(prob.circles.shape[0] / 32), rel=1e-9)
-        assert st["pairs_in_band"] <= 3 * st["candidates"]
+        assert st["in_band"] <= st["candidates"]
         # the plan after the stats run still matches the oracle
         u, x, info = pl.plan(prob.x0, prob.ref, prob.circles)
         orc = oracle.plan(prob, U=U0, iter_=3)
