@@ -58,7 +58,7 @@ def brute_force_ops_per_step(prob) -> float:
 # (three pair distances, their minimum and the band test) and an in-band circle (sqrt,
 # subtract, min).
 OPS_CORE = 150.0
-OPS_PER = {"group_boxes": 12.0, "chunk_boxes": 12.0, "segments": 13.0, "refinements": 40.0,
+OPS_PER = {"range_boxes": 12.0, "chunk_boxes": 12.0, "segments": 13.0, "refinements": 40.0,
            "circles_tested": 15.0, "candidates": 17.0, "in_band": 4.0}
 
 

@@ -250,7 +250,7 @@ class Planner:
         _check(rc, self._h)
         return g.value, b.value
 
-    STAT_NAMES = ("group_boxes", "chunk_boxes", "segments", "refinements", "circles_tested", "candidates",
+    STAT_NAMES = ("range_boxes", "chunk_boxes", "segments", "refinements", "circles_tested", "candidates",
                   "in_band")
 
     def rollout_stats(self, x0, ref, circles=None, centres=None) -> Dict[str, float]:

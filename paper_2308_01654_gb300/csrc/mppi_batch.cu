@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(512, 1) batch_rollout_kernel(BatchArgs a) {
             __syncthreads();
             if (!__syncthreads_and(bulk_wait(&bar, phase, &a.hdr->flags))) return;
             phase ^= 1u;
-            build_l2(smem, s_L);
+            build_boxes(smem, s_L);
         }
         const BatchInst& d = a.inst[td.x];
         const int k = td.y + (int)threadIdx.x / G;
@@ -438,7 +438,7 @@ int mppi_batch_create(int32_t max_slots, int32_t max_batch, int64_t max_samples,
     B->max_tiles = max_samples / 16 + max_batch;
     const SceneLayout Lmax = make_layout(max_T, max_ref, max_circ);
     B->max_scene = up((size_t)Lmax.bytes);
-    B->rollout_smem = up(rollout_smem_bytes(Lmax));   // blob and level-2 boxes
+    B->rollout_smem = up(rollout_smem_bytes(Lmax));   // blob and the boxes built after it
     B->max_in = 4 + 2 * (size_t)max_ref + 5 * (size_t)max_circ + 2 * (size_t)max_T * max_circ;
     B->max_out = out_elems(max_T);
     auto bail = [&](int st) {

@@ -13,7 +13,7 @@ namespace mppi {
 
 // Chunking of the reference polyline for the exact bounded nearest-segment search:
 // level-1 chunks of L1 segments, level-2 groups of L2 level-1 chunks.
-constexpr int REF_L1 = 16;
+constexpr int REF_L1 = 8;
 constexpr int REF_L2 = 16;
 
 // Status bits raised on the device (DevState::flags).

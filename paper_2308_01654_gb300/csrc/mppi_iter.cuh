@@ -266,71 +266,141 @@ __device__ __forceinline__ void scan_chunk(float px, float py, const float2* ver
     }
 }
 
-// Level-2 boxes (each the union of REF_L2 chunk boxes), built by each rollout block in
-// shared memory right after the staged blob.
-__device__ __forceinline__ const float4* l2_boxes(const unsigned char* smem, const SceneLayout& L) {
-    return reinterpret_cast<const float4*>(smem + L.bytes);
+// Boxes built by each rollout block in shared memory right after the staged blob, from
+// the staged chunk boxes: the level-2 boxes (each the union of REF_L2 chunk boxes), and the
+// prefix and suffix boxes of the chunk sequence, pre[i] = box of the chunks 0 .. i-1 and
+// suf[i] = box of the chunks i .. n_l1-1 (i = 0 .. n_l1; the empty box never passes a test).
+struct RefBoxes {
+    const float4* l1;
+    const float4* l2;
+    const float4* pre;
+    const float4* suf;
+};
+
+__device__ __forceinline__ RefBoxes ref_boxes(const unsigned char* smem, const SceneLayout& L) {
+    RefBoxes r;
+    r.l1 = reinterpret_cast<const float4*>(smem + L.off_l1);
+    r.l2 = reinterpret_cast<const float4*>(smem + L.bytes);
+    r.pre = r.l2 + L.n_l2;
+    r.suf = r.pre + (L.n_l1 + 1);
+    return r;
 }
 
-__device__ __forceinline__ void build_l2(unsigned char* smem, const SceneLayout& L) {
-    const float4* l1 = reinterpret_cast<const float4*>(smem + L.off_l1);
-    float4* l2 = reinterpret_cast<float4*>(smem + L.bytes);
+__device__ __forceinline__ float4 box_union(float4 a, float4 b) {
+    return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
+}
+
+__device__ __forceinline__ void build_boxes(unsigned char* smem, const SceneLayout& L) {
+    const RefBoxes r = ref_boxes(smem, L);
+    float4* l2 = const_cast<float4*>(r.l2);
+    float4* pre = const_cast<float4*>(r.pre);
+    float4* suf = const_cast<float4*>(r.suf);
+    const float4 empty = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
     for (int g = threadIdx.x; g < L.n_l2; g += blockDim.x) {
-        float4 a = l1[g * REF_L2];
+        float4 a = r.l1[g * REF_L2];
         const int c1 = min((g + 1) * REF_L2, L.n_l1);
-        for (int c = g * REF_L2 + 1; c < c1; ++c) {
-            const float4 q = l1[c];
-            a.x = fminf(a.x, q.x); a.y = fminf(a.y, q.y);
-            a.z = fmaxf(a.z, q.z); a.w = fmaxf(a.w, q.w);
-        }
+        for (int c = g * REF_L2 + 1; c < c1; ++c) a = box_union(a, r.l1[c]);
         l2[g] = a;
+    }
+    // warp 0 scans the chunks forwards (prefix boxes), warp 1 backwards (suffix boxes)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    for (int side = w; side < 2; side += nw) {
+        float4 carry = empty;
+        for (int base = 0; base < L.n_l1; base += 32) {
+            const int j = base + lane;
+            const int c = side == 0 ? j : L.n_l1 - 1 - j;
+            float4 v = j < L.n_l1 ? r.l1[c] : empty;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                float4 u;
+                u.x = __shfl_up_sync(0xffffffffu, v.x, o);
+                u.y = __shfl_up_sync(0xffffffffu, v.y, o);
+                u.z = __shfl_up_sync(0xffffffffu, v.z, o);
+                u.w = __shfl_up_sync(0xffffffffu, v.w, o);
+                if (lane >= o) v = box_union(v, u);
+            }
+            v = box_union(v, carry);
+            if (j < L.n_l1) {
+                if (side == 0) pre[c + 1] = v;
+                else suf[c] = v;
+            }
+            carry.x = __shfl_sync(0xffffffffu, v.x, 31);
+            carry.y = __shfl_sync(0xffffffffu, v.y, 31);
+            carry.z = __shfl_sync(0xffffffffu, v.z, 31);
+            carry.w = __shfl_sync(0xffffffffu, v.w, 31);
+        }
+        if (lane == 0) {
+            if (side == 0) pre[0] = empty;
+            else suf[L.n_l1] = empty;
+        }
     }
     __syncthreads();
 }
 
-// Closest point of the polyline (ties -> lowest segment).  The chunk of the previous
-// step's segment is scanned first; the two-level boxes then skip every chunk whose lower
-// bound exceeds the best distance (with a relative slack far above binary32 rounding), so
-// no segment that can be the closest is missed.  Two segments that share a vertex can be
-// closer than binary32 resolves (next to the vertex on the outside of a bend their
-// distances differ by a second-order term): the winner's neighbours of another heading are
-// re-ordered against it in binary64 when their binary32 distances are within 4e-6.
+// The chunks lo .. hi-1 under the level-2 boxes (the search's rare fallback).
 template <int G, bool STATS>
-__device__ __forceinline__ void nearest_segment(float px, float py, const float2* vert, const float4* seg,
-                                                const float* head, const float4* l1, const float4* l2, int n_seg,
-                                                int n_l1, int n_l2, int lane_g, unsigned mask, int& jb,
-                                                float& best2, Counters& cnt) {
+__device__ __forceinline__ void search_range(float px, float py, const float2* vert, const float4* seg,
+                                             const RefBoxes& rb, int n_seg, int lo, int hi, int lane_g,
+                                             unsigned mask, unsigned long long& best, Counters& cnt) {
     constexpr float SLACK = 1.0f + 1.0f / 1024.0f;
-    const int cw = jb / REF_L1;
-    unsigned long long best = ~0ull;
-    scan_chunk<G, STATS>(px, py, vert, seg, cw, n_seg, lane_g, best, cnt);
-    best = group_min_key<G>(best, mask);
-    float b2 = __uint_as_float((unsigned)(best >> 32));
 #pragma unroll 1
-    for (int g0 = 0; g0 < n_l2; g0 += 8) {
-        unsigned m2 = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (g0 + q < n_l2 && box_dist2(px, py, l2[g0 + q]) <= b2 * SLACK) m2 |= 1u << q;
-        if (STATS) cnt.l2 += min(8, n_l2 - g0);
-        while (m2) {
-            const int c0 = (g0 + __ffs(m2) - 1) * REF_L2;
-            m2 &= m2 - 1;
-            unsigned m1 = 0;
-#pragma unroll
-            for (int j = 0; j < REF_L2; ++j)
-                if (c0 + j < n_l1 && c0 + j != cw && box_dist2(px, py, l1[c0 + j]) <= b2 * SLACK) m1 |= 1u << j;
-            if (STATS) cnt.l1 += min(REF_L2, n_l1 - c0);
-            while (m1) {
-                const int c = c0 + __ffs(m1) - 1;
-                m1 &= m1 - 1;
-                if (box_dist2(px, py, l1[c]) > b2 * SLACK) continue;   // the bound may have tightened
+    for (int g = lo / REF_L2; g <= (hi - 1) / REF_L2; ++g) {
+        if (STATS) cnt.l2++;
+        if (box_dist2(px, py, rb.l2[g]) > __uint_as_float((unsigned)(best >> 32)) * SLACK) continue;
+        const int c1 = min(hi, (g + 1) * REF_L2);
+#pragma unroll 1
+        for (int c = max(lo, g * REF_L2); c < c1; ++c) {
+            if (STATS) cnt.l1++;
+            if (box_dist2(px, py, rb.l1[c]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK) {
                 scan_chunk<G, STATS>(px, py, vert, seg, c, n_seg, lane_g, best, cnt);
                 best = group_min_key<G>(best, mask);
-                b2 = __uint_as_float((unsigned)(best >> 32));
             }
         }
     }
+}
+
+// Closest point of the polyline (ties -> lowest segment).  The chunk of the predicted
+// segment jh is scanned first, then each neighbouring chunk whose box lies within the best
+// distance; one prefix box and one suffix box bound everything farther, and a range whose
+// box passes is searched under its level-2 and chunk boxes.  A box is skipped only when its
+// lower bound exceeds the best distance (with a relative slack far above binary32
+// rounding), so no segment that can be the closest is missed and the result does not
+// depend on jh.  Two segments that share a vertex can be closer than binary32 resolves
+// (next to the vertex on the outside of a bend their distances differ by a second-order
+// term): the winner's neighbours of another heading are re-ordered against it in binary64
+// when their binary32 distances are within 4e-6.
+template <int G, bool STATS>
+__device__ __forceinline__ void nearest_segment(float px, float py, const float2* vert, const float4* seg,
+                                                const float* head, const RefBoxes& rb, int n_seg, int n_l1,
+                                                int lane_g, unsigned mask, int jh, int& jb, float& best2,
+                                                Counters& cnt) {
+    constexpr float SLACK = 1.0f + 1.0f / 1024.0f;
+    const int cw = jh / REF_L1;
+    unsigned long long best = ~0ull;
+    scan_chunk<G, STATS>(px, py, vert, seg, cw, n_seg, lane_g, best, cnt);
+    best = group_min_key<G>(best, mask);
+#pragma unroll
+    for (int d = -1; d <= 1; d += 2) {
+        const int c = cw + d;
+        if (c >= 0 && c < n_l1) {
+            if (STATS) cnt.l1++;
+            if (box_dist2(px, py, rb.l1[c]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK) {
+                scan_chunk<G, STATS>(px, py, vert, seg, c, n_seg, lane_g, best, cnt);
+                best = group_min_key<G>(best, mask);
+            }
+        }
+    }
+    if (cw >= 2) {
+        if (STATS) cnt.l2++;
+        if (box_dist2(px, py, rb.pre[cw - 1]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK)
+            search_range<G, STATS>(px, py, vert, seg, rb, n_seg, 0, cw - 1, lane_g, mask, best, cnt);
+    }
+    if (cw + 2 < n_l1) {
+        if (STATS) cnt.l2++;
+        if (box_dist2(px, py, rb.suf[cw + 2]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK)
+            search_range<G, STATS>(px, py, vert, seg, rb, n_seg, cw + 2, n_l1, lane_g, mask, best, cnt);
+    }
+    float b2 = __uint_as_float((unsigned)(best >> 32));
     int bi = (int)(best & 0xffffffffu);
     const int b0 = bi;
     const float hb = head[b0];
@@ -587,14 +657,18 @@ template <int G, bool STATS>
 __device__ __forceinline__ float state_cost(const PlanConst& pc, const SceneLayout& L, const Scene& sc,
                                             const float2* table, const StepIn& s, int t, int tb0, int tb1,
                                             bool has_table, bool moving, bool dconst, int lane, int lane_g,
-                                            unsigned mask, int& jb, Counters& cnt) {
+                                            unsigned mask, int& jb, int& jbp, Counters& cnt) {
     float d2r;
-    if (pc.ref_mode == 0)
-        nearest_segment<G, STATS>(s.nx, s.ny, sc.vert, sc.seg, sc.head, sc.l1, l2_boxes(sc.base, L), L.n_seg, L.n_l1,
-                                  L.n_l2, lane_g, mask, jb, d2r, cnt);
-    else
-        nearest_vertex<G>(s.nx, s.ny, sc.vert, sc.l1, l2_boxes(sc.base, L), L.n_ref, L.n_l1, L.n_l2, lane_g, mask, jb,
-                          d2r);
+    if (pc.ref_mode == 0) {
+        // search hint: the last closest segment moved on by its last change
+        const int jh = min(max(2 * jb - jbp, 0), L.n_seg - 1);
+        jbp = jb;
+        nearest_segment<G, STATS>(s.nx, s.ny, sc.vert, sc.seg, sc.head, ref_boxes(sc.base, L), L.n_seg, L.n_l1,
+                                  lane_g, mask, jh, jb, d2r, cnt);
+    } else {
+        nearest_vertex<G>(s.nx, s.ny, sc.vert, sc.l1, ref_boxes(sc.base, L).l2, L.n_ref, L.n_l1, L.n_l2, lane_g, mask,
+                          jb, d2r);
+    }
     const float thr = sc.head[min(jb, L.n_seg - 1)];
     {
         // c_dist on the compensated position: closest point of the winning segment or vertex
@@ -666,7 +740,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
     r.px_c = r.py_c = r.th_c = r.v_c = 0.0f;
     sincosf(r.th, &r.sth, &r.cth);
     r.tdp = fmaf(tp.x, tp.x, tp.y * tp.y);      // |P_0 - T_P|^2 with P_0 = (0, 0)
-    int jb = jb0;
+    int jb = jb0, jbp = jb0;   // closest segment of the last evaluated step and of the one before
     float s_hi = 0.0f, s_c = 0.0f, q_last = 0.0f;
     Counters cnt{0, 0, 0, 0, 0, 0, 0};
 
@@ -675,7 +749,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
             const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
             const StepIn s = dyn_step<BF16>(pc, sc.ctl[t], sc.c0[t], zz, tp, r);
             const float qx = state_cost<G, STATS>(pc, L, sc, table, s, t, t, t, has_table, moving, dconst, lane,
-                                                  lane_g, mask, jb, cnt);
+                                                  lane_g, mask, jb, jbp, cnt);
             kahan_add(s_hi, s_c, qx + s.qu);    // Eq. (6)
             q_last = qx;
         }
@@ -695,7 +769,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
             }
             const int tb1 = min(t0 + G - 1, T - 1);
             const float qx = state_cost<1, STATS>(pc, L, sc, table, e, t0 + my, t0, tb1, has_table, moving, dconst,
-                                                  lane, 0, mask, jb, cnt);
+                                                  lane, 0, mask, jb, jbp, cnt);
             const float c = qx + e.qu;
 #pragma unroll
             for (int j = 0; j < G; ++j) {

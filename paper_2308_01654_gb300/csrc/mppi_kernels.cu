@@ -39,8 +39,10 @@ SceneLayout make_layout(int T, int n_ref, int n_circ) {
     return L;
 }
 
-// the staged blob and the level-2 boxes built after it
-size_t rollout_smem_bytes(const SceneLayout& L) { return (size_t)L.bytes + (size_t)16 * L.n_l2; }
+// the staged blob and the level-2, prefix and suffix boxes built after it
+size_t rollout_smem_bytes(const SceneLayout& L) {
+    return (size_t)L.bytes + (size_t)16 * (L.n_l2 + 2 * (L.n_l1 + 1));
+}
 
 // -----------------------------------------------------------------------------
 // prep: one pass over the inputs.  Positions are shifted into a frame centred on
@@ -78,7 +80,7 @@ __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 2) rollout_kernel(PlanCon
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long bar;
     if (!__syncthreads_and(stage_to_smem(smem, b.scene, L.bytes, &bar, &b.state->flags))) return;
-    build_l2(smem, L);
+    build_boxes(smem, L);
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     rollout_sample<G, TIME, BF16, STATS>(pc, L, smem, z, b.table, b.state->x0f, b.state->moving != 0,
                                          (int)(b.state->jkey & 0xffffffffu), k, b.S, b.stats);
