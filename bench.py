@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "rollout-steps/s (K*T) of one MPPI iteration"
 UNIT = "rollout-steps/s"
-KERNEL_LAUNCHES_PER_STEP = 7   # prep, noise, rollout, argmin, weights, wsum, finalize
+KERNEL_LAUNCHES_PER_STEP = 7   # prep, noise, rollout, argmin, weights, wsum, finalize (+1 noise fix-up for bf16 noise)
 
 
 # ------------------------------------------------------------------------ helpers
@@ -342,7 +342,7 @@ def run_gpu(args, world, rank, local):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed between steps (256 MB write)",
                    "rollout_launch": launch_desc(group, block)},
-        "e2e": e2e, "roofline": roofline, "gpu_launches": KERNEL_LAUNCHES_PER_STEP * args.steps,
+        "e2e": e2e, "roofline": roofline, "gpu_launches": (KERNEL_LAUNCHES_PER_STEP + int(bool(prob.params.get("noise_bf16", 0)))) * args.steps,
         "kernel_ms": kmean, "clocks": clocks,
     }
     if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.quick):

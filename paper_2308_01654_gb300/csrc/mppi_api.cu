@@ -182,7 +182,7 @@ PlanConst make_const_shared(const mppi_params& p) { return make_const(p); }
 static void free_all(mppi_ctx* c) {
     PlanBuffers& b = c->b;
     void* dev[] = {b.state, b.scene, b.table, b.z, b.S, b.w, b.eta_part, b.min_part, b.min_idx_part,
-                   b.min_cnt_part, b.du_part, b.U, b.stats, c->d_in, c->d_out};
+                   b.min_cnt_part, b.du_part, b.U, b.stats, b.fix_count, b.fix_list, c->d_in, c->d_out};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_in) cudaFreeHost(c->h_in);
@@ -268,9 +268,9 @@ int mppi_create(const mppi_params* params, int device, void* cuda_stream, int32_
     PlanBuffers& b = c->b;
     b.n_mblk = (int)std::min<long long>((K + 255) / 256, 296);
     b.n_wblk = b.n_mblk;
-    b.kt_size = 256 * 8;
+    b.kt_size = 256 * WS_J;
     b.n_kt = (K + b.kt_size - 1) / b.kt_size;
-    b.n_tt = (T + 31) / 32;
+    b.n_tt = (T + WS_TT - 1) / WS_TT;
     const SceneLayout Lmax = make_layout(T, c->cap_ref, c->cap_circ);
     const size_t zbytes = (size_t)T * K * (params->noise_bf16 ? 4 : 8);
     c->in_elems = 4 + 2 * (size_t)c->cap_ref + 5 * (size_t)c->cap_circ + 2 * (size_t)T * c->cap_circ;
@@ -292,6 +292,8 @@ int mppi_create(const mppi_params* params, int device, void* cuda_stream, int32_
         {(void**)&b.du_part, sizeof(double) * 2 * (size_t)T * b.n_kt},
         {(void**)&b.U, sizeof(double) * 2 * (size_t)T},
         {(void**)&b.stats, sizeof(unsigned long long) * 8},
+        {(void**)&b.fix_count, sizeof(unsigned)},
+        {(void**)&b.fix_list, sizeof(uint2) * (c->p.noise_bf16 ? NOISE_FIX_CAP : 1u)},
         {(void**)&c->d_in, sizeof(double) * c->in_elems},
         {(void**)&c->d_out, sizeof(double) * c->out_elems},
     };

@@ -13,8 +13,13 @@ namespace mppi {
 
 // Chunking of the reference polyline for the exact bounded nearest-segment search:
 // level-1 chunks of L1 segments, level-2 groups of L2 level-1 chunks.
-constexpr int REF_L1 = 8;
+constexpr int REF_L1 = 4;
 constexpr int REF_L2 = 16;
+
+// Tiles of the weighted noise sum (Eq. 11): WS_J samples per thread (256 threads, so
+// 256 * WS_J samples per k-tile) and WS_TT steps per tile.
+constexpr int WS_J = 8;
+constexpr int WS_TT = 8;
 
 // Status bits raised on the device (DevState::flags).
 constexpr int FLAG_NONFINITE_INPUT = 1;

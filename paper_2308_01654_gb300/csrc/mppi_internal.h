@@ -84,8 +84,13 @@ struct PlanBuffers {
     double* du_part;         // [n_kt][T][2]
     double* U;               // [T][2] nominal controls (the warm start)
     unsigned long long* stats;  // [7] work counters (STATS launches only)
+    unsigned* fix_count;     // bfloat16 noise: pairs whose rounding is taken again in binary64
+    uint2* fix_list;         // [NOISE_FIX_CAP] their (step pair j, sample k); null: decided in place
     int n_mblk, n_wblk, n_kt, n_tt, kt_size;
 };
+
+// Capacity of the deferred bfloat16 rounding list (pairs beyond it are decided in place).
+constexpr unsigned NOISE_FIX_CAP = 1u << 16;
 
 struct PlanInputs {
     const double* x0;        // [4]

@@ -48,6 +48,7 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
     bool bad = false;
 
     if (tid == 0) {
+        if (b.fix_count) *b.fix_count = 0u;
         for (int i = 0; i < 4; ++i) bad |= !isfinite(in.x0[i]);
         b.state->x0f = make_float4(0.0f, 0.0f, (float)in.x0[2], (float)in.x0[3]);
     }
@@ -894,8 +895,6 @@ __device__ __forceinline__ double clampd(double x, double lo, double hi) { retur
 // as the rollout did, accumulates in binary32 over its samples and its warp (32 x WS_J
 // products); the per-warp partials are added in binary64 into du_part[kt][T][2].
 // -----------------------------------------------------------------------------
-constexpr int WS_J = 8;
-constexpr int WS_TT = 32;
 
 template <bool BF16>
 __device__ __forceinline__ void wsum_tile(const PlanConst& pc, const float4* ctl,
@@ -949,6 +948,9 @@ __device__ __forceinline__ void wsum_tile(const PlanConst& pc, const float4* ctl
 // finalize: u <- clamp(u + du), u* = clamp(SG(u)), x* = F-rollout of u*, warm start.
 // One block, one thread per step (T <= 1024).  x* is a chain of prefix sums:
 // v_t from sum a dt, yaw from sum v tan(delta)/L dt, x and y from sum v (cos, sin) dt.
+// The sums run in binary64; tan, sin and cos are taken in binary32 (relative error a
+// few 1e-8 per term, far below the rollouts' own rounding), which keeps this one-block
+// kernel off the slow binary64 transcendental path.
 // -----------------------------------------------------------------------------
 __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBuffers& b, const PlanInputs& in) {
     __shared__ double s_un[2 * 1024];
@@ -966,9 +968,13 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
         else if (flags & FLAG_TIMEOUT) status = -5;
         else if (st->n_finite == 0) status = -4;
         s_status = status;
+    }
+    {
+        // eta: the per-block partial sums of the weights kernel, reduced by the whole block
         double e = 0.0;
-        for (int i = 0; i < b.n_wblk; ++i) e += b.eta_part[i];
-        s_eta = e;
+        for (int i = t; i < b.n_wblk; i += blockDim.x) e += b.eta_part[i];
+        e = block_sum_d(e);
+        if (t == 0) s_eta = e;
     }
     __syncthreads();
     if (s_status != 0) {
@@ -983,6 +989,7 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
     const double eta = s_eta;
     for (int i = t; i < 2 * T; i += blockDim.x) {
         double num = 0.0;
+#pragma unroll 8
         for (int kt = 0; kt < b.n_kt; ++kt) num += b.du_part[(size_t)kt * 2 * T + i];
         const bool ch = i & 1;
         s_un[i] = clampd(b.U[i] + num / eta, ch ? pc.dmin_d : pc.amin_d, ch ? pc.dmax_d : pc.amax_d);
@@ -1022,8 +1029,10 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
                 const double lim = (pc.v_max_d - v) / dt;
                 if (a > lim) a = lim;
                 if (a < pc.amin_d) a = pc.amin_d;
-                const double nx = x + v * cos(th) * dt, ny = y + v * sin(th) * dt;
-                const double nth = th + v * tan(s_us[2 * s + 1]) / pc.wheelbase_d * dt;
+                float sn, cs;
+                sincosf((float)th, &sn, &cs);
+                const double nx = x + v * (double)cs * dt, ny = y + v * (double)sn * dt;
+                const double nth = th + v * (double)tanf((float)s_us[2 * s + 1]) / pc.wheelbase_d * dt;
                 const double nv = v + a * dt;
                 x = nx; y = ny; th = nth; v = nv;
                 in.x_out[4 * (s + 1)] = x; in.x_out[4 * (s + 1) + 1] = y;
@@ -1035,10 +1044,12 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
         const double a = on ? s_us[2 * t] : 0.0, dl = on ? s_us[2 * t + 1] : 0.0;
         const double pv = block_scan_incl(on ? a * dt : 0.0, s_scan);          // v_{t+1} - v0
         const double vt = v0 + (pv - (on ? a * dt : 0.0));                      // v_t
-        const double dth = on ? vt * tan(dl) / pc.wheelbase_d * dt : 0.0;
+        const double dth = on ? vt * (double)tanf((float)dl) / pc.wheelbase_d * dt : 0.0;
         const double pth = block_scan_incl(dth, s_scan);                         // yaw_{t+1} - yaw0
         const double tht = th0 + (pth - dth);                                    // yaw_t
-        const double dx = on ? vt * cos(tht) * dt : 0.0, dy = on ? vt * sin(tht) * dt : 0.0;
+        float sn = 0.0f, cs = 0.0f;
+        if (on) sincosf((float)tht, &sn, &cs);
+        const double dx = on ? vt * (double)cs * dt : 0.0, dy = on ? vt * (double)sn * dt : 0.0;
         const double px = block_scan_incl(dx, s_scan);
         const double py = block_scan_incl(dy, s_scan);
         if (on) {

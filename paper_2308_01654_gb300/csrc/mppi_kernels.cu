@@ -54,19 +54,70 @@ __global__ void __launch_bounds__(256) prep_kernel(PlanConst pc, SceneLayout L, 
 }
 
 // -----------------------------------------------------------------------------
-// noise: one thread per (step pair j, sample k); coalesced stores along k.
+// noise: one thread per (step pair j, sample k); coalesced stores along k.  The
+// bfloat16 form stores the binary32 normals rounded and lists the pairs that lie within
+// the binary32 error bound of a rounding midpoint; noise_fix_kernel takes their rounding
+// again on the exact (binary64) normals, so the stored codes are those of the exact values.
 // -----------------------------------------------------------------------------
 template <bool BF16>
 __global__ void __launch_bounds__(256) noise_kernel(PlanConst pc, const DevState* st,
-                                                    typename NoiseT<BF16>::type* z) {
+                                                    typename NoiseT<BF16>::type* z, unsigned* fix_count,
+                                                    uint2* fix_list) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (k >= pc.K) return;
     const uint32_t it = (uint32_t)st->iter;
     const uint4 w = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)k, it, pc.session), make_uint2(pc.key0, pc.key1));
     const size_t K = (size_t)pc.K;
-    z[(size_t)(2 * j) * K + k] = make_noise<BF16>(uniform24(w.x), uniform24(w.y));
-    if (2 * j + 1 < pc.T) z[(size_t)(2 * j + 1) * K + k] = make_noise<BF16>(uniform24(w.z), uniform24(w.w));
+    const bool two = 2 * j + 1 < pc.T;
+    if constexpr (BF16) {
+        const float2 za = box_muller(uniform24(w.x), uniform24(w.y));
+        const float2 zb = box_muller(uniform24(w.z), uniform24(w.w));
+        z[(size_t)(2 * j) * K + k] = NoiseT<true>::pack(za);
+        if (two) z[(size_t)(2 * j + 1) * K + k] = NoiseT<true>::pack(zb);
+        const bool fix = near_bf16_midpoint(za.x) || near_bf16_midpoint(za.y) ||
+                         (two && (near_bf16_midpoint(zb.x) || near_bf16_midpoint(zb.y)));
+        if (fix) {
+            const unsigned i = atomicAdd(fix_count, 1u);
+            if (i < NOISE_FIX_CAP) {
+                fix_list[i] = make_uint2((unsigned)j, (unsigned)k);
+            } else {
+                z[(size_t)(2 * j) * K + k] = make_noise<true>(uniform24(w.x), uniform24(w.y));
+                if (two) z[(size_t)(2 * j + 1) * K + k] = make_noise<true>(uniform24(w.z), uniform24(w.w));
+            }
+        }
+    } else {
+        z[(size_t)(2 * j) * K + k] = make_noise<false>(uniform24(w.x), uniform24(w.y));
+        if (two) z[(size_t)(2 * j + 1) * K + k] = make_noise<false>(uniform24(w.z), uniform24(w.w));
+    }
+}
+
+// One warp per block and four blocks per SM, so the few binary64 Box-Muller pairs spread
+// over every SM's binary64 pipe.
+__global__ void __launch_bounds__(32) noise_fix_kernel(PlanConst pc, const DevState* st, __nv_bfloat162* z,
+                                                       const unsigned* fix_count, const uint2* fix_list) {
+    const unsigned n = min(*fix_count, NOISE_FIX_CAP);
+    const uint32_t it = (uint32_t)st->iter;
+    const size_t K = (size_t)pc.K;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint2 jk = fix_list[i];
+        const uint4 w = philox4x32_10(make_uint4(jk.x, jk.y, it, pc.session), make_uint2(pc.key0, pc.key1));
+        z[(size_t)(2 * jk.x) * K + jk.y] = make_noise<true>(uniform24(w.x), uniform24(w.y));
+        if (2 * (int)jk.x + 1 < pc.T)
+            z[(size_t)(2 * jk.x + 1) * K + jk.y] = make_noise<true>(uniform24(w.z), uniform24(w.w));
+    }
+}
+
+static cudaError_t launch_noise(const PlanConst& pc, const PlanBuffers& b, int noise_bf16, cudaStream_t st) {
+    dim3 grid((pc.K + 255) / 256, (pc.T + 1) / 2);
+    if (noise_bf16) {
+        __nv_bfloat162* z = reinterpret_cast<__nv_bfloat162*>(b.z);
+        noise_kernel<true><<<grid, 256, 0, st>>>(pc, b.state, z, b.fix_count, b.fix_list);
+        noise_fix_kernel<<<4 * 152, 32, 0, st>>>(pc, b.state, z, b.fix_count, b.fix_list);
+    } else {
+        noise_kernel<false><<<grid, 256, 0, st>>>(pc, b.state, reinterpret_cast<float2*>(b.z), nullptr, nullptr);
+    }
+    return cudaGetLastError();
 }
 
 __global__ void philox_kernel(uint2 key, const uint4* ctr, uint4* out, int n) {
@@ -256,12 +307,7 @@ cudaError_t launch_prep_noise(const PlanConst& pc, const SceneLayout& L, const P
     prep_kernel<<<blocks, 256, 0, st>>>(pc, L, in, b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    dim3 grid((pc.K + 255) / 256, (pc.T + 1) / 2);
-    if (noise_bf16)
-        noise_kernel<true><<<grid, 256, 0, st>>>(pc, b.state, reinterpret_cast<__nv_bfloat162*>(b.z));
-    else
-        noise_kernel<false><<<grid, 256, 0, st>>>(pc, b.state, reinterpret_cast<float2*>(b.z));
-    return cudaGetLastError();
+    return launch_noise(pc, b, noise_bf16, st);
 }
 
 // resets the per-iteration fields that prep accumulates into (after a prep without finalize)
@@ -297,14 +343,8 @@ cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const Pl
         prep_kernel<<<blocks, 256, 0, st>>>(pc, L, in, b);
         if ((e = mark()) != cudaSuccess) return e;
     }
-    {
-        dim3 grid((pc.K + 255) / 256, (pc.T + 1) / 2);
-        if (noise_bf16)
-            noise_kernel<true><<<grid, 256, 0, st>>>(pc, b.state, reinterpret_cast<__nv_bfloat162*>(b.z));
-        else
-            noise_kernel<false><<<grid, 256, 0, st>>>(pc, b.state, reinterpret_cast<float2*>(b.z));
-        if ((e = mark()) != cudaSuccess) return e;
-    }
+    if ((e = launch_noise(pc, b, noise_bf16, st)) != cudaSuccess) return e;
+    if ((e = mark()) != cudaSuccess) return e;
     if ((e = launch_rollout(pc, L, b, group, threads, noise_bf16, st)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
     argmin_kernel<<<b.n_mblk, 256, 0, st>>>(pc.K, b);
