@@ -87,18 +87,25 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes per rollout launch from the committed ncu summary, if taken on the current kernel source."""
+def profiled_value(workload: str, key: str):
+    """A figure ("key = value" line) of the committed ncu summary of the rollout kernel for this
+    workload, if that summary was taken on the current kernel source."""
     import re
     path = TRAFFIC_PROFILE.get(workload)
     if not path or not os.path.exists(os.path.join(ROOT, path)):
         return None
     txt = open(os.path.join(ROOT, path)).read()
     m_h = re.search(r"sha256\[:16\]\): `([0-9a-f]+)`", txt)
-    m_b = re.search(r"dram_bytes_per_launch = (\d+)", txt)
+    m_b = re.search(re.escape(key) + r" = ([0-9.]+)", txt)
     if not m_h or not m_b or m_h.group(1) != kernel_source_hash():
         return None
-    return int(m_b.group(1))
+    return float(m_b.group(1))
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per rollout launch from the committed ncu summary (same source only)."""
+    v = profiled_value(workload, "dram_bytes_per_launch")
+    return None if v is None else int(v)
 
 
 def measured_peaks():
@@ -189,6 +196,49 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(values, world: int, device):
+    """Element-wise maximum of per-rank figures (the slowest rank's times) over all ranks."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def sum_over_ranks(values, world: int, device):
+    """Element-wise sum of per-rank figures over all ranks."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+    return [float(v) for v in t.cpu()]
+
+
+def dist_init(world: int, local: int):
+    """One process group per job (NCCL, this rank's GPU); nothing for one rank."""
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+
+def dist_done(world: int):
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+def weak_value(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of a weak-scaling run: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
+def rank_session(rank: int, session: int = 0) -> int:
+    """Philox session word of a rank's problem: ranks plan independent problems."""
+    return rank * 100000 + session
+
+
 # ------------------------------------------------------------------------ CPU baseline (the oracle)
 
 def oracle_sample(prob, seconds: float):
@@ -231,7 +281,7 @@ def run_gpu(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     prob = scenarios.by_name(args.workload)
-    prob.params["session"] = rank                      # an independent planning problem per rank
+    prob.params["session"] = rank_session(rank)        # an independent planning problem per rank
     K, T = prob.K, prob.T
     stream = torch.cuda.Stream(device=dev)             # the planner and the timing events share it
     torch.cuda.set_stream(stream)
@@ -285,11 +335,8 @@ def run_gpu(args, world, rank, local):
 
     ms_step = statistics.mean(step_ms)
     ms_roll = statistics.mean(roll_ms)
-    if world > 1:
-        t = torch.tensor([ms_step, ms_roll], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step, ms_roll = float(t[0]), float(t[1])
-    value = world * K * T / (ms_step * 1e-3)
+    ms_step, ms_roll = max_over_ranks([ms_step, ms_roll], world, dev)
+    value = weak_value(K * T, world, ms_step * 1e-3)
 
     # end to end through the host-buffer C ABI: H2D of inputs and D2H of outputs every step
     h2d = 8 * (4 + prob.ref.size + prob.circles.size + (0 if prob.centres is None else prob.centres.size))
@@ -305,11 +352,8 @@ def run_gpu(args, world, rank, local):
             for _ in range(args.steps):
                 pe.plan(prob.x0, prob.ref, prob.circles, prob.centres)
             e2e_s = (time.perf_counter() - t0) / args.steps
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t[0])
-        e2e = {"value": world * K * T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        (e2e_s,) = max_over_ranks([e2e_s], world, dev)
+        e2e = {"value": weak_value(K * T, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3}
 
     # roofline of the rollout kernel: FP32-pipe bound (no dense contraction, noise bytes << compute)
@@ -325,6 +369,9 @@ def run_gpu(args, world, rank, local):
                 "frac": achieved / peak_tops,
                 "traffic": args.traffic if args.traffic is not None else profiled_traffic(args.workload),
                 "kernel": "rollout_kernel", "ops_per_rollout_step": ops_step,
+                # issue slots used by the same launch (ncu smsp__issue_active, committed summary)
+                "issue_active_frac": (lambda v: None if v is None else v / 100.0)(
+                    profiled_value(args.workload, "issue_active_pct")),
                 "work_per_rollout_step": {k: round(v, 4) for k, v in work.items()},
                 "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {f_max:.0f} MHz (max SM clock)",
                 "kernel_ms": ms_roll,
@@ -379,7 +426,7 @@ def run_batched(args, world, rank, local):
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     probs = scenarios.batched(seed=0, n=args.batch_size)
     for p in probs:
-        p.params["session"] = rank * 100000 + int(p.params["session"])
+        p.params["session"] = rank_session(rank, int(p.params["session"]))
     n = len(probs)
     sum_k = sum(p.K for p in probs)
     sum_kt = sum(p.K * p.T for p in probs)
@@ -424,11 +471,8 @@ def run_batched(args, world, rank, local):
     t_plain = (time.perf_counter() - t0) / reps
     for pl in ctxs:
         pl.close()
-    if world > 1:
-        t = torch.tensor([t_batch, t_plain], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_batch, t_plain = float(t[0]), float(t[1])
-    out = {"metric": f"plans/s ({n} uneven plans per submission, batched)", "value": world * n / t_batch,
+    t_batch, t_plain = max_over_ranks([t_batch, t_plain], world, "cuda")
+    out = {"metric": f"plans/s ({n} uneven plans per submission, batched)", "value": weak_value(n, world, t_batch),
            "unit": "plans/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64-reduce", "data": "synthetic (uneven plans: K in 2^10..2^14, T 30..150, 0..32 obstacles)",
@@ -456,14 +500,16 @@ def run_closed_loop(args, world, rank, local):
     from paper_2308_01654_gb300 import closed_loop, scenarios
 
     torch.cuda.set_device(local)
+    dist_init(world, local)
     prob = scenarios.closed_loop()
-    prob.params["session"] = rank
+    prob.params["session"] = rank_session(rank)
     res = closed_loop.run(prob, cycles=args.cycles, device=local)
     t = res.plan_ms[3:] if len(res.plan_ms) > 6 else res.plan_ms
     K, T = prob.K, prob.T
+    (p50,) = max_over_ranks([float(np.median(t))], world, "cuda")
     out = {"metric": "rollout-steps/s (K*T) of one MPPI iteration per control cycle, closed loop",
-           "value": world * K * T / (float(np.median(t)) * 1e-3), "unit": "rollout-steps/s", "n_gpus": world,
-           "steps": args.cycles, "warmup": 3, "ms_per_step": float(np.median(t)), "higher_is_better": True,
+           "value": weak_value(K * T, world, p50 * 1e-3), "unit": "rollout-steps/s", "n_gpus": world,
+           "steps": args.cycles, "warmup": 3, "ms_per_step": p50, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64-reduce", "data": "synthetic",
            "config": {"workload": f"closed_loop: K={K} T={T}, {args.cycles} cycles, sinusoidal lane, 8 obstacles "
                                   f"(4 moving, per-step centre table)",
@@ -475,6 +521,7 @@ def run_closed_loop(args, world, rank, local):
                    "max_speed": float(res.states[:, 3].max())}}
     if rank == 0:
         print(json.dumps(out), flush=True)
+    dist_done(world)
 
 
 # ------------------------------------------------------------------------ serving
@@ -513,9 +560,11 @@ def run_serving(args, world, rank, local):
     from paper_2308_01654_gb300 import scenarios
 
     torch.cuda.set_device(local)
+    dist_init(world, local)
     sessions = scenarios.serving_sessions(seed=0, n=args.sessions)
     for p in sessions:
         p.params["shift"] = 1
+        p.params["session"] = rank_session(rank, int(p.params["session"]))
     cparams = [mp.make_params(p.params) for p in sessions]
     warm, meas = args.serve_warmup_s, args.serve_seconds
     trace = serving_trace(sessions, args.rate, warm + meas)
@@ -605,16 +654,20 @@ def run_serving(args, world, rank, local):
         c.close()
     plain = summarise(plat, parr, pdone, "plain FIFO mppi_plan loop")
     mean_kt = float(np.mean([sessions[s].K * sessions[s].T for _, s, _ in trace]))
+    # every rank serves its own sessions: plans/s add up, latency is the worst rank's
+    (total,) = sum_over_ranks([served["plans_per_s"]], world, "cuda")
+    p50_all, p99_all = max_over_ranks([served["p50_ms"], served["p99_ms"]], world, "cuda")
     out = {"metric": f"served plans/s ({len(sessions)} sessions, Poisson {args.rate:.0f} plans/s offered)",
-           "value": served["plans_per_s"], "unit": "plans/s", "n_gpus": world, "steps": len(trace), "warmup": 0,
-           "ms_per_step": served["p50_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "value": total, "unit": "plans/s", "n_gpus": world, "steps": len(trace), "warmup": 0,
+           "ms_per_step": p50_all, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64-reduce", "data": "synthetic sessions (K 2^10..2^14, T 30..150, 0..32 obstacles)",
            "config": {"workload": f"serving: {warm:.0f} s warm-up + {meas:.0f} s measured, mean K*T {mean_kt:.0f}",
                       "pipelines": args.pipelines, "max_wait_us": args.max_wait_us},
-           "latency_ms": {"p50": served["p50_ms"], "p99": served["p99_ms"], "max": served["max_ms"]},
+           "latency_ms": {"p50": p50_all, "p99": p99_all, "max": served["max_ms"]},
            "server": served, "plain_per_plan_loop": plain}
     if rank == 0:
         print(json.dumps(out), flush=True)
+    dist_done(world)
 
 
 # ------------------------------------------------------------------------ the reference arm (the oracle)
@@ -624,7 +677,12 @@ def run_reference(args, world, rank, local):
         return
     import oracle
     from paper_2308_01654_gb300 import scenarios
-    prob = scenarios.by_name(args.workload)
+    if args.workload in ("batched", "serving"):
+        prob = scenarios.batched(seed=0, n=1)[0]        # one instance of the uneven mix
+    elif args.workload == "closed_loop_run":
+        prob = scenarios.closed_loop()                 # one cycle's iteration
+    else:
+        prob = scenarios.by_name(args.workload)
     T = prob.T
     budget = max(2.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
     k_s = oracle_sample(prob, budget)
