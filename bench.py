@@ -584,8 +584,11 @@ def run_serving(args, world, rank, local):
     srv = mp.Server(max_sessions=len(sessions), max_batch=256, max_samples=2_000_000, max_rollout_steps=200_000_000,
                     max_T=max_t, max_ref=max_ref, max_circ=max_circ, pipelines=args.pipelines,
                     hbm_budget_bytes=args.hbm_budget_gb << 30, max_wait_us=args.max_wait_us, device=local)
-    big = max(sessions, key=lambda p: p.K * p.T)
-    group, block = srv.autotune(cparams[sessions.index(big)], big.x0, big.ref, big.circles, 64)
+    # tune for the micro-batches the trace produces: a few plans of median size
+    by_size = sorted(range(len(sessions)), key=lambda i: sessions[i].K * sessions[i].T)
+    mid = by_size[len(by_size) // 2]
+    tune_n = max(1, min(8, int(round(args.rate * 1e-3))))        # ~ plans arriving per millisecond
+    group, block = srv.autotune(cparams[mid], sessions[mid].x0, sessions[mid].ref, sessions[mid].circles, tune_n)
     ids, lat, arr_t, done_t = {}, {}, {}, {}
     t0 = [0.0]
     stop = threading.Event()

@@ -92,8 +92,8 @@ typedef struct {
     uint64_t seed;              /* Philox key */
     uint32_t session;           /* Philox counter word 3: independent streams per session */
     int32_t group;              /* lanes per sample in the rollout kernel: 0 = choose; 1,2,4,8,16,32 = the
-                                   lanes split the search and obstacle work of each step; -2,-4 = 2 or 4
-                                   lanes split the steps (each evaluates every 2nd / 4th step's cost) */
+                                   lanes split the search and obstacle work of each step; -2,-4,-8,-16 = that
+                                   many lanes split the steps (lane p evaluates the cost of steps p, p+|g|, ...) */
     int32_t block;              /* threads per block of the rollout kernel: 0 = choose, else a multiple of 32 up to 448 */
 } mppi_params;
 
@@ -149,7 +149,7 @@ int mppi_plan_device(mppi_ctx* ctx, const double* d_x0, const double* d_ref_xy, 
                      const double* d_circ, int32_t n_circ, const double* d_centres,
                      double* d_u_out, double* d_x_out, mppi_info* info);
 
-/* Autotuner: times the rollout kernel for every lanes-per-sample group (1..32, -2, -4) and
+/* Autotuner: times the rollout kernel for every lanes-per-sample group (1..32, -2..-16) and
    block size (64, 128, 256, and sizes that spread the lanes evenly over the SMs with
    1 to 4 resident blocks each) on the given inputs (host arrays, as for mppi_plan) and
    keeps the fastest for this context; *group and *block receive the choice (either
@@ -243,9 +243,17 @@ int mppi_batch_submit(mppi_batch* batch, mppi_request* req, int32_t n, int32_t* 
 int mppi_batch_wait(mppi_batch* batch, int32_t ticket);
 int mppi_batch_plan(mppi_batch* batch, mppi_request* req, int32_t n);
 
-/* Times the persistent rollout kernel for every lanes-per-sample group and block size on
-   this submission's plans (without changing any slot) and keeps the fastest. */
+/* Times the persistent rollout kernel for every lanes-per-sample group (1..32 splitting the
+   work of each step, -2, -4, -8 splitting the steps) and block size (64, 128, 256, 448) on
+   this submission's plans (without changing any slot) and keeps the fastest; *group and
+   *block receive the choice (either may be NULL). */
 int mppi_batch_autotune(mppi_batch* batch, mppi_request* req, int32_t n, int32_t* group, int32_t* block);
+
+/* Sets the persistent rollout kernel's launch shape directly (e.g. a shape tuned earlier):
+   group as for mppi_batch_autotune, block a multiple of 32 up to 448 holding at least 16
+   samples.  MPPI_ERR_ARG for other values, MPPI_ERR_CAPACITY while a submission is in flight
+   or when the shape does not fit the shared memory of a block.  No counterpart in the paper. */
+int mppi_batch_set_launch(mppi_batch* batch, int32_t group, int32_t block);
 
 /* Warm start of one slot: U[T][2] and its iteration index (the Philox counter word 2). */
 int mppi_batch_set_controls(mppi_batch* batch, int32_t slot, const double* U, int32_t T, uint64_t iter);

@@ -95,6 +95,7 @@ SIGNATURES = {
     "mppi_batch_wait": (C.c_int, [_VP, C.c_int32]),
     "mppi_batch_plan": (C.c_int, [_VP, _VP, C.c_int32]),
     "mppi_batch_autotune": (C.c_int, [_VP, _VP, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "mppi_batch_set_launch": (C.c_int, [_VP, C.c_int32, C.c_int32]),
     "mppi_batch_set_controls": (C.c_int, [_VP, C.c_int32, _DP, C.c_int32, C.c_uint64]),
     "mppi_batch_get_controls": (C.c_int, [_VP, C.c_int32, _DP, C.c_int32, C.POINTER(C.c_uint64)]),
     "mppi_batch_last_error": (C.c_char_p, [_VP]),
@@ -427,6 +428,10 @@ class BatchPlanner:
         g, b = C.c_int32(), C.c_int32()
         self._check(lib().mppi_batch_autotune(self._h, C.cast(reqs, _VP), len(reqs), C.byref(g), C.byref(b)), self._h)
         return g.value, b.value
+
+    def set_launch(self, group: int, block: int):
+        """Fix the rollout launch shape (group < 0: lanes split the steps)."""
+        self._check(lib().mppi_batch_set_launch(self._h, int(group), int(block)), self._h)
 
     def set_controls(self, slot: int, U, iter_: int = 0):
         U = _f64(U).reshape(-1, 2)

@@ -63,7 +63,8 @@ static bool finite_all(const double* v, size_t n) {
 }
 
 static bool valid_group(int g) {
-    return g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32 || g == -2 || g == -4;
+    return g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32 || g == -2 || g == -4 || g == -8 ||
+           g == -16;
 }
 
 static bool valid_block(int b) { return b >= 32 && b <= MAX_ROLLOUT_THREADS && b % 32 == 0; }
@@ -93,7 +94,7 @@ static int check_params(const mppi_params* p, std::string& why) {
         if (!isfinite(p->ego_offset[e]) || !isfinite(p->ego_radius[e])) { why = "ego circles must be finite"; return MPPI_ERR_ARG; }
     if (p->ref_mode != 0 && p->ref_mode != 1) { why = "ref_mode must be 0 or 1"; return MPPI_ERR_ARG; }
     if (!valid_group(p->group)) {
-        why = "group must be 0, 1, 2, 4, 8, 16, 32, -2 or -4";
+        why = "group must be 0, 1, 2, 4, 8, 16, 32, -2, -4, -8 or -16";
         return MPPI_ERR_ARG;
     }
     if (!(p->block == 0 || valid_block(p->block))) {
@@ -585,9 +586,9 @@ int mppi_autotune(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n
         CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
         const size_t smem = rollout_smem_bytes(L);
         // lanes per sample: > 0 split the work of each step, < 0 split the steps
-        const int groups[] = {1, 2, 4, 8, 16, 32, -2, -4};
+        const int groups[] = {1, 2, 4, 8, 16, 32, -2, -4, -8, -16};
         cudaError_t err = cudaSuccess;
-        for (int gi = 0; gi < 8 && err == cudaSuccess; ++gi) {
+        for (int gi = 0; gi < 10 && err == cudaSuccess; ++gi) {
             const int G = groups[gi];
             const long long lanes = (long long)c->p.K * (G < 0 ? -G : G);
             if (G != 1 && lanes > 4LL * n_sm * 2048) continue;  // far more lanes than the GPU holds

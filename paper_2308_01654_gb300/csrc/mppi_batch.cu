@@ -146,8 +146,9 @@ __global__ void __launch_bounds__(256) batch_noise_kernel(BatchArgs a) {
     }
 }
 
-template <int G, bool BF16>
-__global__ void __launch_bounds__(512, 1) batch_rollout_kernel(BatchArgs a) {
+// G lanes per sample; TIME: they split the steps, else the work of each step (rollout_sample).
+template <int G, bool TIME, bool BF16>
+__global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 2) batch_rollout_kernel(BatchArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long bar;
     __shared__ PlanConst s_pc;
@@ -187,8 +188,8 @@ __global__ void __launch_bounds__(512, 1) batch_rollout_kernel(BatchArgs a) {
             build_boxes(smem, s_L);
         }
         const BatchInst& d = a.inst[td.x];
-        const int k = td.y + (int)threadIdx.x / G;
-        rollout_sample<G, false, BF16, false>(s_pc, s_L, smem, reinterpret_cast<const NT*>(a.z) + d.z_off,
+        const int k = td.y + (int)threadIdx.x / G;   // G lanes per sample
+        rollout_sample<G, TIME, BF16, false>(s_pc, s_L, smem, reinterpret_cast<const NT*>(a.z) + d.z_off,
                                        a.table + d.table_off, s_x0, s_moving != 0, s_jb0, k, a.S + d.s_off, nullptr);
         __syncthreads();
     }
@@ -281,20 +282,25 @@ __global__ void __launch_bounds__(1024) batch_finalize_kernel(BatchArgs a) {
     }
 }
 
-template <int G, bool BF16>
+template <int G, bool TIME, bool BF16>
 static cudaError_t set_rollout_smem(size_t smem) {
-    return cudaFuncSetAttribute(batch_rollout_kernel<G, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(batch_rollout_kernel<G, TIME, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(smem < 48 * 1024 ? 48 * 1024 : smem));
 }
 
-template <int G, bool BF16>
+template <int G, bool TIME, bool BF16>
 static int batch_blocks_per_sm(int threads, size_t smem) {
     int n = 0;
-    if (set_rollout_smem<G, BF16>(smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_rollout_kernel<G, BF16>, threads, smem) != cudaSuccess)
+    if (set_rollout_smem<G, TIME, BF16>(smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_rollout_kernel<G, TIME, BF16>, threads, smem) !=
+        cudaSuccess)
         return 0;
     return n;
 }
+
+// Lanes per sample as the group value: g > 0 split the work of each step, g < 0 split the steps.
+#define MPPI_BATCH_GROUPS(X) X(1, 1, false) X(2, 2, false) X(4, 4, false) X(8, 8, false) X(16, 16, false) \
+    X(32, 32, false) X(-2, 2, true) X(-4, 4, true) X(-8, 8, true)
 
 // The shared-memory attribute must already be set (batch_max_blocks does it), so this
 // only launches and may be captured into a graph.
@@ -302,27 +308,28 @@ template <bool BF16>
 static cudaError_t launch_batch_rollout_b(const BatchArgs& a, int G, int threads, int blocks, size_t smem,
                                           cudaStream_t st) {
     switch (G) {
-#define CASE(g)                                                                      \
-    case g: {                                                                        \
-        batch_rollout_kernel<g, BF16><<<blocks, threads, smem, st>>>(a);             \
+#define CASE(gv, g, time)                                                            \
+    case gv: {                                                                       \
+        batch_rollout_kernel<g, time, BF16><<<blocks, threads, smem, st>>>(a);       \
         return cudaGetLastError();                                                   \
     }
-        CASE(1) CASE(2) CASE(4) CASE(8) CASE(16) CASE(32)
+        MPPI_BATCH_GROUPS(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;
     }
 }
 
 static int batch_max_blocks(int G, int bf16, int threads, size_t smem) {
-    switch (G * 2 + bf16) {
-#define CASE(g)                                                           \
-    case 2 * g: return batch_blocks_per_sm<g, false>(threads, smem);      \
-    case 2 * g + 1: return batch_blocks_per_sm<g, true>(threads, smem);
-        CASE(1) CASE(2) CASE(4) CASE(8) CASE(16) CASE(32)
+    switch (G) {
+#define CASE(gv, g, time)                                                                                    \
+    case gv: return bf16 ? batch_blocks_per_sm<g, time, true>(threads, smem) : batch_blocks_per_sm<g, time, false>(threads, smem);
+        MPPI_BATCH_GROUPS(CASE)
 #undef CASE
         default: return 0;
     }
 }
+
+static int lanes_of(int G) { return G < 0 ? -G : G; }
 
 }  // namespace mppi
 
@@ -548,7 +555,7 @@ static int build_submission(mppi_batch* B, Pipeline& p, mppi_request* req, int n
     double* inp = reinterpret_cast<double*>(p.h_stage + B->off_in);
     long long z_off = 0, s_off = 0, in_off = 0, table_off = 0, out_off = 0, du_off = 0, scene_off = 0;
     long long noise = 0, wsum = 0, n_tiles = 0;
-    const int spt = B->threads / B->G;   // samples per rollout tile
+    const int spt = B->threads / lanes_of(B->G);   // samples per rollout tile
     p.out_offsets.assign((size_t)n, 0);
     std::vector<std::pair<double, int>> cost((size_t)n);
     for (int i = 0; i < n; ++i) {
@@ -764,8 +771,8 @@ int mppi_batch_autotune(mppi_batch* B, mppi_request* req, int32_t n, int32_t* gr
     const int saveG = B->G, saveT = B->threads;
     float best = INFINITY;
     int bg = saveG, bt = saveT;
-    const int groups[] = {1, 2, 4, 8, 16, 32};
-    const int sizes[] = {64, 128, 256, 512};
+    const int groups[] = {1, 2, 4, 8, 16, 32, -2, -4, -8};
+    const int sizes[] = {64, 128, 256, MAX_ROLLOUT_THREADS};
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0), "cudaEventCreate");
     BCK(cudaEventCreate(&e1), "cudaEventCreate");
@@ -782,10 +789,10 @@ int mppi_batch_autotune(mppi_batch* B, mppi_request* req, int32_t n, int32_t* gr
         else batch_noise_kernel<false><<<B->n_sm * 8, 256, 0, p.stream>>>(p.args);
         e = cudaGetLastError();
     }
-    for (int gi = 0; gi < 6 && rc == MPPI_OK && e == cudaSuccess; ++gi) {
+    for (int gi = 0; gi < 9 && rc == MPPI_OK && e == cudaSuccess; ++gi) {
         for (int si = 0; si < 4 && e == cudaSuccess; ++si) {
             const int G = groups[gi], th = sizes[si];
-            if (th / G < 16) continue;   // at least 16 samples per tile
+            if (th / lanes_of(G) < 16) continue;   // at least 16 samples per tile
             const int per_sm = batch_max_blocks(G, B->noise_bf16, th, B->rollout_smem);
             if (per_sm < 1) continue;
             B->G = G;
@@ -822,6 +829,25 @@ int mppi_batch_autotune(mppi_batch* B, mppi_request* req, int32_t n, int32_t* gr
     if (e != cudaSuccess) return bfail(B, MPPI_ERR_CUDA, std::string("batch autotune: ") + cudaGetErrorString(e));
     if (group) *group = B->G;
     if (block) *block = B->threads;
+    return MPPI_OK;
+}
+
+int mppi_batch_set_launch(mppi_batch* B, int32_t group, int32_t block) {
+    if (!B) return bfail(B, MPPI_ERR_ARG, "NULL argument");
+    bool known = false;
+#define CASE(gv, g, time) known |= group == gv;
+    MPPI_BATCH_GROUPS(CASE)
+#undef CASE
+    if (!known || block < 32 || block > MAX_ROLLOUT_THREADS || block % 32 != 0 || block / lanes_of(group) < 16)
+        return bfail(B, MPPI_ERR_ARG, "group must be 1..32 or -2, -4, -8; block a multiple of 32 up to 448 with "
+                                      "at least 16 samples per block");
+    for (auto& p : B->pipes)
+        if (p.busy) return bfail(B, MPPI_ERR_CAPACITY, "a submission is in flight");
+    BCK(cudaSetDevice(B->device), "cudaSetDevice");
+    if (batch_max_blocks(group, B->noise_bf16, block, B->rollout_smem) < 1)
+        return bfail(B, MPPI_ERR_CAPACITY, "launch shape does not fit the shared memory of a block");
+    B->G = group;
+    B->threads = block;
     return MPPI_OK;
 }
 

@@ -27,9 +27,13 @@ __device__ __forceinline__ float4 seg_record(const double* ref, int i, double ox
     return make_float4(ex, ey, ex * inv, ey * inv);
 }
 
+// Heading of segment i: the direction is formed in binary64 and its angle taken in binary32
+// (each component rounded to 2^-24 relative, atan2f within a few ulp: a few 1e-7 rad, the
+// same order as storing the angle as a binary32), which keeps scene preparation off the slow
+// binary64 transcendental path.
 __device__ __forceinline__ float seg_heading(const double* ref, int i) {
     const double hx = ref[2 * i + 2] - ref[2 * i], hy = ref[2 * i + 3] - ref[2 * i + 1];
-    return (float)atan2(hy, hx);
+    return atan2f((float)hy, (float)hx);
 }
 
 __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayout& L, const PlanInputs& in,

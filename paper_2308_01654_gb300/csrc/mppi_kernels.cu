@@ -249,6 +249,8 @@ static cudaError_t launch_rollout_b(const PlanConst& pc, const SceneLayout& L, c
         case 32: return launch_rollout_t<32, false, BF16>(pc, L, b, threads, st);
         case -2: return launch_rollout_t<2, true, BF16>(pc, L, b, threads, st);
         case -4: return launch_rollout_t<4, true, BF16>(pc, L, b, threads, st);
+        case -8: return launch_rollout_t<8, true, BF16>(pc, L, b, threads, st);
+        case -16: return launch_rollout_t<16, true, BF16>(pc, L, b, threads, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -276,6 +278,8 @@ static int max_blocks_b(int group, int threads, size_t smem) {
         case 32: return max_blocks_t<32, false, BF16>(threads, smem);
         case -2: return max_blocks_t<2, true, BF16>(threads, smem);
         case -4: return max_blocks_t<4, true, BF16>(threads, smem);
+        case -8: return max_blocks_t<8, true, BF16>(threads, smem);
+        case -16: return max_blocks_t<16, true, BF16>(threads, smem);
         default: return 0;
     }
 }

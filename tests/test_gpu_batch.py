@@ -57,6 +57,31 @@ def test_alone_and_in_the_mix_are_bit_identical():
             assert alone[0].info.eta == mix[i].info.eta
 
 
+@pytest.mark.parametrize("group,block", [(1, 128), (4, 256), (-2, 128), (-4, 448), (-8, 256)])
+def test_every_launch_shape_gives_the_same_plans(group, block):
+    """Lane splits of the work of a step and of the steps give bit-identical costs."""
+    probs = mixed_problems(n=6)
+    out = {}
+    for gb in ((1, 64), (group, block)):
+        with batch_for(probs) as bp:
+            bp.set_launch(*gb)
+            plans = plans_of(probs)
+            bp.plan(plans)
+            out[gb] = plans
+    for a, b in zip(out[(1, 64)], out[(group, block)]):
+        assert a.info.s_min == b.info.s_min and a.info.argmin == b.info.argmin
+        np.testing.assert_array_equal(a.u, b.u)
+
+
+def test_launch_shape_validation():
+    probs = mixed_problems(n=3)
+    with batch_for(probs) as bp:
+        for g, b in ((3, 128), (-16, 448), (1, 480), (32, 256), (2, 100)):
+            with pytest.raises(mp.MppiError) as e:
+                bp.set_launch(g, b)
+            assert e.value.status == -1
+
+
 def test_batch_agrees_with_the_single_plan_path():
     probs = mixed_problems()
     with batch_for(probs) as bp:
@@ -128,7 +153,7 @@ def test_autotune_leaves_the_slots_and_is_used():
         U0 = np.full((probs[0].T, 2), 0.01)
         bp.set_controls(0, U0, 4)
         g, b = bp.autotune(plans_of(probs))
-        assert g in (1, 2, 4, 8, 16, 32) and b in (64, 128, 256, 512)
+        assert g in (1, 2, 4, 8, 16, 32, -2, -4, -8) and b in (64, 128, 256, 448)
         U, it = bp.get_controls(0, probs[0].T)
         np.testing.assert_array_equal(U, U0)
         assert it == 4

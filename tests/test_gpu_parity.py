@@ -80,7 +80,7 @@ def test_bf16_noise_is_the_rounded_normal():
 # ----------------------------------------------------------------------------- one iteration
 
 @pytest.mark.parametrize("K,T,group", [(1024, 50, 0), (1000, 37, 1), (777, 33, 4), (257, 13, 32), (1, 5, 0),
-                                       (1000, 37, -2), (777, 33, -4), (3, 2, -4)])
+                                       (1000, 37, -2), (777, 33, -4), (3, 2, -4), (900, 45, -8), (257, 21, -16)])
 def test_single_plan_parity(K, T, group):
     prob = sc.single_plan()
     prob.params.update(K=K, T=T, group=group)
@@ -169,11 +169,11 @@ def test_groups_give_identical_costs(scene, obstacles):
     if obstacles == "static":
         prob.circles[:, 3:] = 0.0
     S = {}
-    for g in (1, 2, 4, 8, 16, 32, -2, -4):
+    for g in (1, 2, 4, 8, 16, 32, -2, -4, -8, -16):
         p = dict(prob.params, group=g)
         outs, _, _, _ = run_gpu(prob, params=p)
         S[g] = outs[0][3]
-    for g in (2, 4, 8, 16, 32, -2, -4):
+    for g in (2, 4, 8, 16, 32, -2, -4, -8, -16):
         np.testing.assert_array_equal(S[g], S[1], err_msg=f"group {g}")
 
 
