@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 2) batch_rollout_kernel(B
             __syncthreads();
             if (!__syncthreads_and(bulk_wait(&bar, phase, &a.hdr->flags))) return;
             phase ^= 1u;
-            build_boxes(smem, s_L);
+            build_boxes(smem, s_L, a.table + a.inst[s_plan].table_off, s_pc.has_table != 0);
         }
         const BatchInst& d = a.inst[td.x];
         const int k = td.y + (int)threadIdx.x / G;   // G lanes per sample

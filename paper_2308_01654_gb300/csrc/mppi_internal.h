@@ -41,6 +41,9 @@ struct SceneLayout {
     int off_circ;    // float4 [n_circ]  (x, y, r, (d_safe_0 + r + r_ego)^2 when d_safe is constant)
     int off_vel;     // float2 [n_circ]  velocities
     int off_disp;    // float  [n_circ]  bound on the distance a centre moves in one step
+    int off_proj;    // float4           (dx, dy, 0, 0): unit direction of the lane (first to last vertex)
+    int off_order;   // int    [n_circ]  circles sorted by their key s = p . d (p: centre at step 0),
+    int off_skey;    // float  [n_circ]  and the sorted keys: space only, filled in each block's copy
     int bytes;       // total, a multiple of 16
 };
 
@@ -88,6 +91,16 @@ struct PlanBuffers {
     uint2* fix_list;         // [NOISE_FIX_CAP] their (step pair j, sample k); null: decided in place
     int n_mblk, n_wblk, n_kt, n_tt, kt_size;
 };
+
+// Shared memory each rollout block builds after the staged blob: the level-2 boxes, the
+// prefix and suffix boxes of the chunk sequence, and the circle index (a float4 of scalars
+// and CIRC_BUCKETS + 1 bucket starts into the sorted circles, then the unsorted keys).
+constexpr int CIRC_BUCKETS = 64;
+
+inline size_t block_extra_bytes(const SceneLayout& L) {
+    return (size_t)16 * (L.n_l2 + 2 * (L.n_l1 + 1)) + 16 + (size_t)4 * ((CIRC_BUCKETS + 1 + 3) & ~3) +
+           (size_t)4 * ((L.n_circ + 3) & ~3);   // unsorted keys while the block sorts
+}
 
 // Capacity of the deferred bfloat16 rounding list (pairs beyond it are decided in place).
 constexpr unsigned NOISE_FIX_CAP = 1u << 16;

@@ -102,6 +102,14 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
         if (c[3] != 0.0 || c[4] != 0.0) atomicOr(&b.state->moving, 1);
         if (!in.centres) disp[k] = (float)(sqrt(c[3] * c[3] + c[4] * c[4]) * pc.dt_d * 1.001) + 1e-5f;
     }
+    // unit lane direction (first to last vertex): the axis the rollout blocks sort the circles on
+    if (tid == 0) {
+        const double ex = in.ref[2 * (L.n_ref - 1)] - in.ref[0], ey = in.ref[2 * (L.n_ref - 1) + 1] - in.ref[1];
+        const double el = sqrt(ex * ex + ey * ey);
+        const bool ok = el > 0.0 && isfinite(el);
+        *reinterpret_cast<float4*>(sc + L.off_proj) =
+            make_float4(ok ? (float)(ex / el) : 1.0f, ok ? (float)(ey / el) : 0.0f, 0.0f, 0.0f);
+    }
     if (in.centres) {
         for (int i = tid; i < L.T * L.n_circ; i += nth) {
             const double cx = in.centres[2 * i], cy = in.centres[2 * i + 1];
@@ -291,11 +299,54 @@ __device__ __forceinline__ RefBoxes ref_boxes(const unsigned char* smem, const S
     return r;
 }
 
+// The circle index built after the boxes: circles sorted by their key along the lane
+// direction, CIRC_BUCKETS buckets of equal key width over the finite keys, and the
+// scalars the broad phase needs to bound where a circle can be at step t.
+struct CircleIndex {
+    const int* order;       // [n_circ] circle of each sorted position
+    const int* start;       // [CIRC_BUCKETS + 1] first sorted position of each bucket
+    float smin, inv_w;      // bucket b holds the keys from smin + b / inv_w (inv_w = 0: one range)
+    float dmax, rmax;       // largest step bound and radius over the circles
+    float dx, dy;           // lane direction
+};
+
+__device__ __forceinline__ const unsigned char* circle_index_base(const unsigned char* smem, const SceneLayout& L) {
+    return smem + L.bytes + 16 * (L.n_l2 + 2 * (L.n_l1 + 1));
+}
+
+__device__ __forceinline__ CircleIndex circle_index(const unsigned char* smem, const SceneLayout& L) {
+    const unsigned char* e = circle_index_base(smem, L);
+    const float4 sc = *reinterpret_cast<const float4*>(e);
+    const float4 pj = *reinterpret_cast<const float4*>(smem + L.off_proj);
+    CircleIndex c;
+    c.order = reinterpret_cast<const int*>(smem + L.off_order);
+    c.start = reinterpret_cast<const int*>(e + 16);
+    c.smin = sc.x;
+    c.inv_w = sc.y;
+    c.dmax = sc.z;
+    c.rmax = sc.w;
+    c.dx = pj.x;
+    c.dy = pj.y;
+    return c;
+}
+
+// First position in skey[0, n) whose key is >= v (n if none).
+__device__ __forceinline__ int lower_bound_f(const float* skey, int n, float v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (skey[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ float4 box_union(float4 a, float4 b) {
     return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
 }
 
-__device__ __forceinline__ void build_boxes(unsigned char* smem, const SceneLayout& L) {
+__device__ __forceinline__ void build_boxes(unsigned char* smem, const SceneLayout& L, const float2* table,
+                                            bool has_table) {
     const RefBoxes r = ref_boxes(smem, L);
     float4* l2 = const_cast<float4*>(r.l2);
     float4* pre = const_cast<float4*>(r.pre);
@@ -339,6 +390,55 @@ __device__ __forceinline__ void build_boxes(unsigned char* smem, const SceneLayo
             else suf[L.n_l1] = empty;
         }
     }
+    // circle index.  Keys: the step-0 centre (first table row, or the given centre) projected
+    // on the lane direction, non-finite keys last; the rank of each circle (key, then index)
+    // places it, so the sorted order is one permutation.
+    __shared__ unsigned s_dmax, s_rmax;
+    __shared__ int s_nfin;
+    if (threadIdx.x == 0) {
+        s_dmax = 0u;
+        s_rmax = 0u;
+    }
+    const float4* circ = reinterpret_cast<const float4*>(smem + L.off_circ);
+    const float* disp = reinterpret_cast<const float*>(smem + L.off_disp);
+    const float4 pj = *reinterpret_cast<const float4*>(smem + L.off_proj);
+    float* keyt = reinterpret_cast<float*>(const_cast<unsigned char*>(circle_index_base(smem, L)) + 16 +
+                                           4 * ((CIRC_BUCKETS + 1 + 3) & ~3));
+    for (int k = threadIdx.x; k < L.n_circ; k += blockDim.x) {
+        const float2 p = has_table ? table[k] : make_float2(circ[k].x, circ[k].y);
+        const float key = fmaf(p.x, pj.x, p.y * pj.y);
+        keyt[k] = isfinite(key) ? key : INFINITY;
+    }
+    __syncthreads();
+    int* order = reinterpret_cast<int*>(smem + L.off_order);
+    float* skey = reinterpret_cast<float*>(smem + L.off_skey);
+    for (int k = threadIdx.x; k < L.n_circ; k += blockDim.x) {
+        const float sk = keyt[k];
+        int rank = 0;
+        for (int j = 0; j < L.n_circ; ++j) {
+            const float sj = keyt[j];
+            rank += (sj < sk || (sj == sk && j < k)) ? 1 : 0;
+        }
+        order[rank] = k;
+        skey[rank] = sk;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < L.n_circ; k += blockDim.x) {
+        atomicMax(&s_dmax, __float_as_uint(fmaxf(disp[k], 0.0f)));     // non-negative: bits order as values
+        atomicMax(&s_rmax, __float_as_uint(fmaxf(circ[k].z, 0.0f)));
+    }
+    if (threadIdx.x == 0) s_nfin = lower_bound_f(skey, L.n_circ, INFINITY);
+    __syncthreads();
+    unsigned char* e = const_cast<unsigned char*>(circle_index_base(smem, L));
+    int* start = reinterpret_cast<int*>(e + 16);
+    const int nfin = s_nfin;
+    const float smin = nfin > 0 ? skey[0] : 0.0f;
+    const float bw = nfin > 0 ? (skey[nfin - 1] - smin) / (float)CIRC_BUCKETS : 0.0f;
+    const float inv_w = (bw > 0.0f && isfinite(bw)) ? 1.0f / bw : 0.0f;
+    for (int b = threadIdx.x; b <= CIRC_BUCKETS; b += blockDim.x)
+        start[b] = b == 0 ? 0 : (b == CIRC_BUCKETS ? L.n_circ : lower_bound_f(skey, nfin, fmaf((float)b, bw, smin)));
+    if (threadIdx.x == 0)
+        *reinterpret_cast<float4*>(e) = make_float4(smin, inv_w, __uint_as_float(s_dmax), __uint_as_float(s_rmax));
     __syncthreads();
 }
 
@@ -512,7 +612,8 @@ __device__ __forceinline__ float warp_max_f(float v) { return ord_f32(__reduce_m
 // then tests each circle's centre at tb0 with the band widened by the farthest it can
 // move in tb1 - tb0 steps.
 template <int G, bool STATS>
-__device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4* circ, const float2* vel,
+__device__ __forceinline__ float obstacle_min(const PlanConst& pc, const unsigned char* smem, const SceneLayout& L,
+                                              const float4* circ, const float2* vel,
                                               const float* disp, const float2* table, int n_circ, int t, int tb0,
                                               int tb1,
                                               bool has_table, bool moving, bool dconst, float nx, float ny,
@@ -525,11 +626,30 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4*
     const float by0 = warp_min_f(fminf(ya, yb)), by1 = warp_max_f(fmaxf(ya, yb));
     const float mmax = dconst ? mband : warp_max_f(mband);
     const float st = (float)(t + 1) * pc.dt, st0 = (float)(tb0 + 1) * pc.dt;
+    // the sorted positions whose circles can reach the warp box: a circle's key moves by at
+    // most dmax per step from its step-0 value, and projecting on the lane direction does not
+    // increase distances, so every circle the box test below can pass lies in [lo, hi)
+    const CircleIndex ci = circle_index(smem, L);
+    int lo = 0, hi = n_circ;
+    {
+        const float qx0 = bx0 * ci.dx, qx1 = bx1 * ci.dx, qy0 = by0 * ci.dy, qy1 = by1 * ci.dy;
+        const float slo = fminf(qx0, qx1) + fminf(qy0, qy1), shi = fmaxf(qx0, qx1) + fmaxf(qy0, qy1);
+        const float reach = (mmax + ci.rmax + pc.ego_rmax) * 1.0001f + 1e-4f + ci.dmax * (float)(2 * tb1 + 2) +
+                            1e-3f + 1e-5f * (fabsf(slo) + fabsf(shi));
+        const float f0 = (slo - reach - ci.smin) * ci.inv_w, f1 = (shi + reach - ci.smin) * ci.inv_w;
+        if (ci.inv_w > 0.0f && isfinite(f0) && isfinite(f1)) {
+            const int b0 = f0 < 1.0f ? 0 : (int)fminf(floorf(f0) - 1.0f, (float)CIRC_BUCKETS);
+            const int b1 = f1 < -1.0f ? -1 : (int)fminf(floorf(f1) + 1.0f, (float)(CIRC_BUCKETS - 1));
+            lo = ci.start[b0];
+            hi = ci.start[b1 + 1];
+        }
+    }
     float dobj = INFINITY;
-    for (int base = 0; base < n_circ; base += 32) {
-        const int kc = base + lane;
+    for (int base = lo; base < hi; base += 32) {
+        const int pos = base + lane;
         bool hit = false;
-        if (kc < n_circ) {
+        if (pos < hi) {
+            const int kc = ci.order[pos];
             if (STATS) cnt.circ++;
             const float2 cc = circle_centre(circ, vel, table, n_circ, tb0, kc, st0, has_table, moving);
             const float lim = (mmax + circ[kc].z + pc.ego_rmax) * 1.0001f + 1e-4f;
@@ -544,7 +664,7 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const float4*
             m &= m - 1;
             if ((j & (G - 1)) != lane_g) continue;
             if (STATS) cnt.cand++;
-            const int kc2 = base + bit;
+            const int kc2 = ci.order[base + bit];
             const float4 c = circ[kc2];
             const float2 cc = circle_centre(circ, vel, table, n_circ, t, kc2, st, has_table, moving);
             if (dconst) {
@@ -699,7 +819,7 @@ __device__ __forceinline__ float state_cost(const PlanConst& pc, const SceneLayo
     const float mband = pc.collision_only ? fmaxf(s.ds, 0.0f) : s.ds;
     float dobj = INFINITY;
     if (L.n_circ > 0)
-        dobj = obstacle_min<G, STATS>(pc, sc.circ, sc.vel, sc.disp, table, L.n_circ, t, tb0, tb1, has_table, moving, dconst,
+        dobj = obstacle_min<G, STATS>(pc, sc.base, L, sc.circ, sc.vel, sc.disp, table, L.n_circ, t, tb0, tb1, has_table, moving, dconst,
                                       s.nx, s.ny, s.cnth, s.snth, mband, lane, lane_g, mask, cnt);
     const float gap = s.ds - dobj;
     float c_safe = gap > 0.0f ? gap * gap : 0.0f;

@@ -35,14 +35,15 @@ SceneLayout make_layout(int T, int n_ref, int n_circ) {
     L.off_circ = o; o = align16(o + 16 * n_circ);
     L.off_vel = o;  o = align16(o + 8 * n_circ);
     L.off_disp = o; o = align16(o + 4 * n_circ);
+    L.off_proj = o; o = align16(o + 16);
+    L.off_order = o; o = align16(o + 4 * n_circ);
+    L.off_skey = o; o = align16(o + 4 * n_circ);
     L.bytes = o;
     return L;
 }
 
-// the staged blob and the level-2, prefix and suffix boxes built after it
-size_t rollout_smem_bytes(const SceneLayout& L) {
-    return (size_t)L.bytes + (size_t)16 * (L.n_l2 + 2 * (L.n_l1 + 1));
-}
+// the staged blob and what each block builds after it (block_extra_bytes)
+size_t rollout_smem_bytes(const SceneLayout& L) { return (size_t)L.bytes + block_extra_bytes(L); }
 
 // -----------------------------------------------------------------------------
 // prep: one pass over the inputs.  Positions are shifted into a frame centred on
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 2) rollout_kernel(PlanCon
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long bar;
     if (!__syncthreads_and(stage_to_smem(smem, b.scene, L.bytes, &bar, &b.state->flags))) return;
-    build_boxes(smem, L);
+    build_boxes(smem, L, b.table, pc.has_table != 0);
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     rollout_sample<G, TIME, BF16, STATS>(pc, L, smem, z, b.table, b.state->x0f, b.state->moving != 0,
                                          (int)(b.state->jkey & 0xffffffffu), k, b.S, b.stats);

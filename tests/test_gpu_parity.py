@@ -331,8 +331,9 @@ def test_rollout_stats_are_consistent_and_leave_state():
         # (fewer at the ends of the lane); the fallback ranges never open
         assert 1.0 <= st["range_boxes"] <= 2.0 and 1.0 <= st["chunk_boxes"] <= 2.0
         assert 1 <= st["segments"] <= prob.ref.shape[0]
-        # the broad phase tests one circle per lane per 32-circle chunk
-        assert st["circles_tested"] == pytest.approx(math.ceil(prob.circles.shape[0] / 32), rel=1e-9)
+        # the broad phase tests one circle per lane per 32 circles of the indexed range, at most
+        # every circle; on this lane of 200 m the range around a warp is a few circles
+        assert 0.0 < st["circles_tested"] <= math.ceil(prob.circles.shape[0] / 32)
         assert st["in_band"] <= st["candidates"]
         # the plan after the stats run still matches the oracle
         u, x, info = pl.plan(prob.x0, prob.ref, prob.circles)
