@@ -751,10 +751,12 @@ __device__ __forceinline__ StepIn dyn_step(const PlanConst& pc, const float4 ct,
     float acc = pe.va;
     if (pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt) / pc.dt), pc.amin);
     const float tn = tanf(pe.vd);
-    kahan_add(r.px, r.px_c, vt * r.cth * pc.dt);
-    kahan_add(r.py, r.py_c, vt * r.sth * pc.dt);
-    kahan_add(r.th, r.th_c, vt * tn * pc.dt_over_L);
-    kahan_add(r.v, r.v_c, acc * pc.dt);
+    // the increments are rounded products (no fused multiply-add), the same expressions as
+    // the time-split form below, so both give the same bits
+    kahan_add(r.px, r.px_c, __fmul_rn(__fmul_rn(vt, r.cth), pc.dt));
+    kahan_add(r.py, r.py_c, __fmul_rn(__fmul_rn(vt, r.sth), pc.dt));
+    kahan_add(r.th, r.th_c, __fmul_rn(__fmul_rn(vt, tn), pc.dt_over_L));
+    kahan_add(r.v, r.v_c, __fmul_rn(acc, pc.dt));
     StepIn s;
     s.nx = r.px;
     s.ny = r.py;
@@ -838,10 +840,14 @@ __device__ __forceinline__ float state_cost(const PlanConst& pc, const SceneLayo
 //
 // TIME = false: the G lanes run the dynamics redundantly (identical bits) and split the
 // reference search and the obstacle pairs of every step, combining with shuffles.
-// TIME = true: the G lanes split the steps.  Every lane integrates the dynamics of all
-// steps (identical bits); lane p evaluates the state cost of the steps t0 + p of each
-// block of G steps (the reference search warm-started from its own previous step) and
-// the step costs are added in step order, so S is bit for bit that of G = 1.
+// TIME = true: the G lanes split the steps.  In each block of G steps lane p perturbs the
+// controls of step t0 + p and takes its steering tangent; yaw and speed, which do not
+// depend on the position, are then advanced through the block by every lane from the
+// shuffled controls, lane p takes the sine and cosine of its step's yaw, and the positions
+// follow from the shuffled directions (same operations as one lane per sample, identical
+// bits).  Lane p evaluates the state cost of its step (the reference search warm-started
+// from its own previous step) and the step costs are added in step order, so S is bit for
+// bit that of G = 1.
 template <int G, bool TIME, bool BF16, bool STATS>
 __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneLayout& L, const unsigned char* smem,
                                                const typename NoiseT<BF16>::type* __restrict__ z,
@@ -880,20 +886,79 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
         }
     } else {
         for (int t0 = 0; t0 < T; t0 += G) {
-            // past the last step a lane re-evaluates step T - 1 (the warp stays converged)
-            const int my = min(lane_g, T - 1 - t0);
+            // nv real steps in this block; past the last step a lane re-evaluates step T - 1
+            // (the warp stays converged)
+            const int nv = min(G, T - t0);
+            const int my = min(lane_g, nv - 1);
+            const int tm = t0 + my;
             StepIn e;
+            if constexpr (G <= 2) {
+                // two lanes: integrating both steps in each lane is cheaper than the shuffles
 #pragma unroll 1
-            for (int j = 0; j < G; ++j) {
-                if (t0 + j < T) {
+                for (int j = 0; j < nv; ++j) {
                     const int t = t0 + j;
                     const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
-                    const StepIn s = dyn_step<BF16>(pc, sc.ctl[t], sc.c0[t], zz, tp, r);
-                    if (j == my) e = s;
+                    const StepIn q = dyn_step<BF16>(pc, sc.ctl[t], sc.c0[t], zz, tp, r);
+                    if (j == my) e = q;
+                }
+            } else {
+            // own step: perturbed controls and the steering tangent (independent of the state)
+            const float4 ct = sc.ctl[tm];
+            const Perturbed pe = perturb(ct.x, ct.y, NoiseT<BF16>::load(z + (size_t)tm * K + kk), pc.sig_a, pc.sig_d,
+                                         pc.amin, pc.amax, pc.dmin, pc.dmax);
+            const float tn_own = tanf(pe.vd);
+            // yaw and speed through the block: every lane, the lanes' controls by shuffle
+            float vt_own = 0.0f, th_own = 0.0f, thc_own = 0.0f, v_own = 0.0f, vc_own = 0.0f;
+#pragma unroll 1
+            for (int j = 0; j < nv; ++j) {
+                const float va = __shfl_sync(mask, pe.va, j, G);
+                const float tn = __shfl_sync(mask, tn_own, j, G);
+                const float vt = r.v - r.v_c;
+                float acc = va;
+                if (pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt) / pc.dt), pc.amin);
+                kahan_add(r.th, r.th_c, __fmul_rn(__fmul_rn(vt, tn), pc.dt_over_L));
+                kahan_add(r.v, r.v_c, __fmul_rn(acc, pc.dt));
+                if (j == my) {
+                    vt_own = vt;
+                    th_own = r.th;
+                    thc_own = r.th_c;
+                    v_own = r.v;
+                    vc_own = r.v_c;
                 }
             }
+            sincosf(th_own, &e.snth, &e.cnth);
+            // positions through the block: the yaw direction before step j is lane j-1's
+            // (the carried one for j = 0)
+#pragma unroll 1
+            for (int j = 0; j < nv; ++j) {
+                const float vt = __shfl_sync(mask, vt_own, j, G);
+                const float cn = __shfl_sync(mask, e.cnth, j > 0 ? j - 1 : 0, G);
+                const float sn = __shfl_sync(mask, e.snth, j > 0 ? j - 1 : 0, G);
+                const float cj = j > 0 ? cn : r.cth, sj = j > 0 ? sn : r.sth;
+                kahan_add(r.px, r.px_c, __fmul_rn(__fmul_rn(vt, cj), pc.dt));
+                kahan_add(r.py, r.py_c, __fmul_rn(__fmul_rn(vt, sj), pc.dt));
+                // Eq. (13): progress towards the target point
+                const float tx = (r.px - tp.x) - r.px_c, ty = (r.py - tp.y) - r.py_c;
+                const float tdn = fmaf(tx, tx, ty * ty);
+                if (j == my) {
+                    e.nx = r.px;
+                    e.ny = r.py;
+                    e.px_c = r.px_c;
+                    e.py_c = r.py_c;
+                    e.c_target = tdn > r.tdp ? 1.0f : 0.0f;
+                }
+                r.tdp = tdn;
+            }
+            r.cth = __shfl_sync(mask, e.cnth, nv - 1, G);
+            r.sth = __shfl_sync(mask, e.snth, nv - 1, G);
+            e.th = th_own;
+            e.th_c = thc_own;
+            e.dv = (v_own - pc.v_ref) - vc_own;
+            e.ds = fmaf(pc.d_safe_c, v_own - vc_own, pc.d_safe_0);
+            e.qu = fmaf(ct.z, pe.ea, fmaf(ct.w, pe.ed, sc.c0[tm]));
+            }
             const int tb1 = min(t0 + G - 1, T - 1);
-            const float qx = state_cost<1, STATS>(pc, L, sc, table, e, t0 + my, t0, tb1, has_table, moving, dconst,
+            const float qx = state_cost<1, STATS>(pc, L, sc, table, e, tm, t0, tb1, has_table, moving, dconst,
                                                   lane, 0, mask, jb, jbp, cnt);
             const float c = qx + e.qu;
 #pragma unroll
