@@ -65,6 +65,19 @@ typedef struct {
     double x, y, r, vx, vy;
 } mppi_circle;
 
+/* Covers an oriented rectangular object with circles (Sec. III-C, Fig. 3; Algorithm 1,
+   ApproximateObstacles: the paper shows an object as three circles along its length and
+   gives no construction, so this is one).  The rectangle has centre (x, y), heading yaw
+   [rad], length along the heading and width across it [m]; it is cut into n equal slices
+   along its length and each slice gets the circle through its four corners, centred on the
+   centre line (radius sqrt((length/2n)^2 + (width/2)^2)), so the circles cover the
+   rectangle.  n = 0 picks n = ceil(length / width).  Every circle gets the object's
+   velocity (vx, vy).  out: caller-owned array of max_out circles.  Returns the number of
+   circles written, MPPI_ERR_ARG for non-finite values, length or width <= 0 or n < 0, or
+   MPPI_ERR_CAPACITY when n exceeds max_out.  Host code; needs no GPU. */
+int32_t mppi_box_to_circles(double x, double y, double yaw, double length, double width, double vx, double vy,
+                            int32_t n, mppi_circle* out, int32_t max_out);
+
 /* Hyper-parameters (Algorithm 1 "Given": M = K, T, lambda, gamma, Sigma, R, D, Z). */
 typedef struct {
     int32_t K;                  /* samples (rollouts), >= 1 */

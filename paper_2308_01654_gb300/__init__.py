@@ -95,6 +95,7 @@ SIGNATURES = {
     "mppi_batch_wait": (C.c_int, [_VP, C.c_int32]),
     "mppi_batch_plan": (C.c_int, [_VP, _VP, C.c_int32]),
     "mppi_batch_autotune": (C.c_int, [_VP, _VP, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "mppi_box_to_circles": (C.c_int32, [C.c_double] * 7 + [C.c_int32, _VP, C.c_int32]),
     "mppi_batch_set_launch": (C.c_int, [_VP, C.c_int32, C.c_int32]),
     "mppi_batch_set_controls": (C.c_int, [_VP, C.c_int32, _DP, C.c_int32, C.c_uint64]),
     "mppi_batch_get_controls": (C.c_int, [_VP, C.c_int32, _DP, C.c_int32, C.POINTER(C.c_uint64)]),
@@ -310,6 +311,19 @@ def _set_profiling(self, on: bool = True):
 
 Planner.kernel_times = _kernel_times
 Planner.set_profiling = _set_profiling
+
+
+def box_to_circles(x: float, y: float, yaw: float, length: float, width: float, vx: float = 0.0,
+                   vy: float = 0.0, n: int = 0) -> np.ndarray:
+    """Circles (rows x, y, r, vx, vy) covering an oriented rectangular object (mppi_box_to_circles)."""
+    ok = width > 0 and length > 0 and np.isfinite(length / width)
+    cap = n if n > 0 else (max(1, int(np.ceil(length / width))) if ok else 1)
+    out = np.zeros((cap, 5), dtype=np.float64)
+    rc = lib().mppi_box_to_circles(float(x), float(y), float(yaw), float(length), float(width), float(vx),
+                                   float(vy), int(n), out.ctypes.data_as(_VP), cap)
+    if rc < 0:
+        raise MppiError(rc, "mppi_box_to_circles")
+    return out[:rc]
 
 
 def philox(seed: int, ctr) -> np.ndarray:
