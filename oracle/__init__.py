@@ -45,6 +45,7 @@ class OrcParams(C.Structure):
         ("sg_enable", C.c_int32), ("shift", C.c_int32), ("noise_bf16", C.c_int32),
         ("seed", C.c_uint64),
         ("session", C.c_uint32),
+        ("model", C.c_int32),
     ]
 
 
@@ -87,6 +88,7 @@ def lib():
         L.orc_round_bf16.restype = C.c_double
         L.orc_noise.argtypes = [C.POINTER(OrcParams), C.c_uint32, dp]
         L.orc_bicycle_step.argtypes = [dp, C.c_double, C.c_double, C.c_double, C.c_double, dp]
+        L.orc_bicycle5_step.argtypes = [dp, C.c_double, C.c_double, C.c_double, C.c_double, dp]
         L.orc_nearest_ref.argtypes = [dp, C.c_int32, C.c_int32, C.c_double, C.c_double,
                                       C.POINTER(C.c_int32), dp, dp]
         L.orc_nearest_ref.restype = C.c_double
@@ -147,6 +149,7 @@ def make_params(p: Dict[str, object]) -> OrcParams:
     s.sg_enable, s.shift, s.noise_bf16 = int(p["sg_enable"]), int(p["shift"]), int(p["noise_bf16"])
     s.seed = int(p["seed"]) & 0xFFFFFFFFFFFFFFFF
     s.session = int(p["session"]) & 0xFFFFFFFF
+    s.model = int(p.get("model", 0))
     return s
 
 
@@ -189,6 +192,19 @@ def bicycle_step(x, a: float, delta: float, dt: float, wheelbase: float) -> np.n
     out = np.empty(4)
     lib().orc_bicycle_step(_dp(xi), a, delta, dt, wheelbase, _dp(out))
     return out
+
+
+def bicycle5_step(x, a: float, omega: float, dt: float, wheelbase: float) -> np.ndarray:
+    """The steering-rate form: state (x, y, yaw, v, delta), control (a, omega)."""
+    xi = _f64(x)
+    out = np.empty(5)
+    lib().orc_bicycle5_step(_dp(xi), a, omega, dt, wheelbase, _dp(out))
+    return out
+
+
+def nx_of(p) -> int:
+    """State entries of the parameter set's model: 4, or 5 for the steering-rate form."""
+    return 5 if int(p.get("model", 0)) == 1 else 4
 
 
 def nearest_ref(ref, px: float, py: float, mode: int = 0):
@@ -244,7 +260,7 @@ def savgol5(u) -> np.ndarray:
 
 def rollout_states(p, x0, u) -> np.ndarray:
     s = make_params(p)
-    xs = np.empty((s.T + 1, 4))
+    xs = np.empty((s.T + 1, nx_of(p)))
     lib().orc_rollout_states(C.byref(s), _dp(_f64(x0)), _dp(_f64(u)), _dp(xs))
     return xs
 
@@ -262,7 +278,7 @@ def plan(prob, U=None, iter_: int = 0, want_eps: bool = False, params=None) -> P
     K, T = s.K, s.T
     Uw = np.zeros((T, 2)) if U is None else _f64(U).copy()
     u_star = np.zeros((T, 2))
-    x_star = np.zeros((T + 1, 4))
+    x_star = np.zeros((T + 1, nx_of(p)))
     S = np.empty(K)
     margin = np.empty(K)
     eps = np.empty((T, K, 2)) if want_eps else None

@@ -141,6 +141,15 @@ void orc_bicycle_step(const double x[4], double a, double delta, double dt, doub
     out[3] = v + dv * dt;
 }
 
+/* Eq. (5) with the steering angle as the fifth state and the steering rate omega as the
+   second control: every right-hand side at x_t, delta advanced by omega * dt. */
+void orc_bicycle5_step(const double x[5], double a, double omega, double dt, double wheelbase,
+                       double out[5])
+{
+    orc_bicycle_step(x, a, x[4], dt, wheelbase, out);
+    out[4] = x[4] + omega * dt;
+}
+
 static double clampd(double v, double lo, double hi)
 {
     return v < lo ? lo : (v > hi ? hi : v);
@@ -365,7 +374,7 @@ double orc_rollout_cost(const orc_params* p, const double x0[4], const double* U
                         const double* ref, int32_t n_ref, const orc_circle* circ, int32_t n_circ,
                         const double* centres, double* eps_out, double* margin)
 {
-    double x[4] = {x0[0], x0[1], x0[2], x0[3]};
+    double x[5] = {x0[0], x0[1], x0[2], x0[3], p->model == 1 ? x0[4] : 0.0};
     double prev_x = x0[0], prev_y = x0[1];
     double* cxy = n_circ > 0 ? (double*)malloc(sizeof(double) * 2 * (size_t)n_circ) : NULL;
     double S = 0.0, last_qx = 0.0;
@@ -383,8 +392,11 @@ double orc_rollout_cost(const orc_params* p, const double x0[4], const double* U
             eps_out[2 * t + 1] = ep[1];
         }
         double a = capped_accel(p, v[0], x[3]);
-        double xn[4];
-        orc_bicycle_step(x, a, v[1], p->dt, p->wheelbase, xn);
+        double xn[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        if (p->model == 1)
+            orc_bicycle5_step(x, a, v[1], p->dt, p->wheelbase, xn);
+        else
+            orc_bicycle_step(x, a, v[1], p->dt, p->wheelbase, xn);
         centres_at(p, circ, n_circ, centres, t, cxy);
         double qx = state_cost(p, xn, prev_x, prev_y, ref, n_ref, circ, n_circ, cxy, margin);
         double qu = control_cost(p, u, ep);
@@ -459,13 +471,17 @@ void orc_savgol5(int32_t T, const double* u_in, int32_t stride, double* u_out)
     }
 }
 
-/* Algorithm 1: x*_{t+1} = F(x*_t, u*_t), noise free. xs is [T+1][4]. */
+/* Algorithm 1: x*_{t+1} = F(x*_t, u*_t), noise free. xs is [T+1][NX]. */
 void orc_rollout_states(const orc_params* p, const double x0[4], const double* u, double* xs)
 {
-    memcpy(xs, x0, 4 * sizeof(double));
+    const int nx = ORC_NX(p);
+    memcpy(xs, x0, (size_t)nx * sizeof(double));
     for (int32_t t = 0; t < p->T; ++t) {
-        double a = capped_accel(p, u[2 * t], xs[4 * t + 3]);
-        orc_bicycle_step(xs + 4 * t, a, u[2 * t + 1], p->dt, p->wheelbase, xs + 4 * (t + 1));
+        double a = capped_accel(p, u[2 * t], xs[nx * t + 3]);
+        if (nx == 5)
+            orc_bicycle5_step(xs + 5 * t, a, u[2 * t + 1], p->dt, p->wheelbase, xs + 5 * (t + 1));
+        else
+            orc_bicycle_step(xs + 4 * t, a, u[2 * t + 1], p->dt, p->wheelbase, xs + 4 * (t + 1));
     }
 }
 
@@ -482,9 +498,10 @@ static int validate(const orc_params* p, const double x0[4], const double* ref, 
     if (!p || p->K < 1 || p->T < 1 || n_ref < 2 || n_circ < 0) return -1;
     if (!(p->dt > 0.0) || !(p->lam > 0.0) || !(p->wheelbase > 0.0) || !(p->gamma > 0.0)) return -1;
     if (p->n_ego < 0 || p->n_ego > ORC_MAX_EGO) return -1;
+    if (p->model != 0 && p->model != 1) return -1;
     for (int c = 0; c < 2; ++c)
         if (!(p->sigma[c] >= 0.0) || !(p->u_min[c] <= p->u_max[c])) return -1;
-    if (!all_finite(x0, 4) || !all_finite(ref, 2 * (size_t)n_ref) || !all_finite(U, 2 * (size_t)p->T))
+    if (!all_finite(x0, (size_t)ORC_NX(p)) || !all_finite(ref, 2 * (size_t)n_ref) || !all_finite(U, 2 * (size_t)p->T))
         return -1;
     if (n_circ > 0 && !all_finite((const double*)circ, 5 * (size_t)n_circ)) return -1;
     if (centres && !all_finite(centres, (size_t)p->T * n_circ * 2)) return -1;

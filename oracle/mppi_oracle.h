@@ -48,7 +48,12 @@ typedef struct {
     int32_t sg_enable, shift, noise_bf16;
     uint64_t seed;
     uint32_t session;
+    int32_t model;                         /* 0: state (x, y, yaw, v), control (a, delta);
+                                              1: state (x, y, yaw, v, delta), control (a, omega) */
 } orc_params;
+
+/* state entries of a model: 4 or 5 */
+#define ORC_NX(p) ((p)->model == 1 ? 5 : 4)
 
 typedef struct { double x, y, r, vx, vy; } orc_circle;
 
@@ -70,6 +75,9 @@ void orc_noise(const orc_params* p, uint32_t iter, double* z);
 /* ---- dynamics (Eq. (5), explicit Euler) ---- */
 void orc_bicycle_step(const double x[4], double a, double delta, double dt, double wheelbase,
                       double out[4]);
+/* the steering-rate form: the steering angle is the fifth state, driven by omega */
+void orc_bicycle5_step(const double x[5], double a, double omega, double dt, double wheelbase,
+                       double out[5]);
 
 /* ---- cost pieces (Sec. IV-C, Eq. (12)-(18)) ---- */
 /* Closest reference point to (px,py); returns squared distance, the winning segment
@@ -98,7 +106,8 @@ void orc_savgol5(int32_t T, const double* u_in, int32_t stride, double* u_out);
 void orc_rollout_states(const orc_params* p, const double x0[4], const double* u, double* xs);
 
 /* ---- one full MPPI iteration (Algorithm 1, one pass of the while loop) ----
-   U: in/out nominal controls [T][2] (the warm start).  u_star [T][2], x_star [T+1][4].
+   U: in/out nominal controls [T][2] (the warm start).  u_star [T][2], x_star [T+1][NX]
+   (NX = 4, or 5 for model 1; x0 has NX entries).
    S_out [K], margin_out [K], eps_out [T][K][2] optional (NULL to skip).
    Returns 0 on success, -1 on invalid arguments, -4 when no sample cost is finite
    (U is left unchanged then). */

@@ -35,7 +35,7 @@ import numpy as np
 PAPER_WEIGHTS = dict(w_dist=15.0, w_target=7.0, w_yaw=120.0, w_speed=5.0, w_safe=25.0)
 V_G = 30.0 / 3.6  # target speed v_G = 30 km/h (Table I)
 
-CONFIG_IDS = {"single_plan": 1, "closed_loop": 2, "roofline": 3, "batched": 4, "serving": 5}
+CONFIG_IDS = {"single_plan": 1, "closed_loop": 2, "roofline": 3, "batched": 4, "serving": 5, "paper_preset": 6}
 
 
 @dataclasses.dataclass
@@ -81,7 +81,7 @@ def default_params(K: int, T: int, dt: float, lam: float = 1.0,
         d_safe_c=0.0, d_safe_0=0.5, collision_only=0,
         n_ego=3, ego_offset=[0.0, 1.35, 2.7], ego_radius=[1.1, 1.1, 1.1],
         ref_mode=0, sg_enable=1, shift=0, noise_bf16=0,
-        seed=0, session=0,
+        seed=0, session=0, model=0,
         **PAPER_WEIGHTS,
     )
 
@@ -216,6 +216,20 @@ def tiny(seed: int = 0, K: int = 8, T: int = 4, n_ref: int = 12, n_obs: int = 1,
     return Problem(p, np.array([0.0, 0.2, 0.1, 4.0]), ref, circles, None, "tiny")
 
 
+def paper_preset(seed: int = 0) -> Problem:
+    """The paper's own setting (Table I) on the 5-state steering-rate model: M = 2560 samples,
+    T = 16 steps of 0.25 s, lambda = 150, sigma = (0.85 m/s^2, 0.05 rad/s), |omega| <= 0.11,
+    a in [-2.5, 1.1], d_safe = 1.36 v + 11, target speed 30 km/h as the speed cap.  A curved
+    lane with two static objects of three circles each; state (x, y, yaw, v, delta)."""
+    rng = _rng(seed, CONFIG_IDS["paper_preset"])
+    p = default_params(2560, 16, 0.25, lam=150.0, sigma=(0.85, 0.05), u_min=(-2.5, -0.11), u_max=(1.1, 0.11))
+    p.update(model=1, seed=seed, d_safe_c=1.36, d_safe_0=11.0, v_max=V_G)
+    ref = sinusoid_lane(600, 0.5, 3.0, 80.0)
+    circles = obstacle_circles(rng, ref, 2, (45.0, 90.0), (-3.0, 3.0))
+    yaw0 = math.atan2(ref[1, 1] - ref[0, 1], ref[1, 0] - ref[0, 0])
+    return Problem(p, np.array([0.0, 0.0, yaw0, 7.0, 0.0]), ref, circles, None, "paper_preset")
+
+
 def by_name(name: str, seed: int = 0) -> Problem:
     if name == "single_plan":
         return single_plan(seed)
@@ -225,4 +239,6 @@ def by_name(name: str, seed: int = 0) -> Problem:
         return roofline(seed)
     if name == "roofline_bf16":
         return roofline(seed, bf16=True)
+    if name == "paper_preset":
+        return paper_preset(seed)
     raise KeyError(name)
