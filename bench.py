@@ -294,7 +294,8 @@ def run_gpu(args, world, rank, local):
     circ = torch.tensor(prob.circles, dtype=torch.float64, device=dev)
     cen = None if prob.centres is None else torch.tensor(prob.centres, dtype=torch.float64, device=dev)
     u_out = torch.empty((T, 2), dtype=torch.float64, device=dev)
-    x_out = torch.empty((T + 1, 4), dtype=torch.float64, device=dev)
+    nx = prob.x0.shape[0]                              # 4, or 5 for the steering-rate model
+    x_out = torch.empty((T + 1, nx), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
     def step():
@@ -339,8 +340,8 @@ def run_gpu(args, world, rank, local):
     value = weak_value(K * T, world, ms_step * 1e-3)
 
     # end to end through the host-buffer C ABI: H2D of inputs and D2H of outputs every step
-    h2d = 8 * (4 + prob.ref.size + prob.circles.size + (0 if prob.centres is None else prob.centres.size))
-    d2h = 8 * (2 * T + 4 * (T + 1))
+    h2d = 8 * (prob.x0.size + prob.ref.size + prob.circles.size + (0 if prob.centres is None else prob.centres.size))
+    d2h = 8 * (2 * T + nx * (T + 1))
     e2e = None
     if not args.quick:
         p_e = dict(prob.params, group=group, block=block)
@@ -712,7 +713,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="roofline",
                     choices=["roofline", "roofline_bf16", "closed_loop", "single_plan", "batched", "serving",
-                             "closed_loop_run"])
+                             "closed_loop_run", "paper_preset"])
     ap.add_argument("--cycles", type=int, default=200)
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--sessions", type=int, default=512)

@@ -108,6 +108,11 @@ typedef struct {
                                    lanes split the search and obstacle work of each step; -2,-4,-8,-16 = that
                                    many lanes split the steps (lane p evaluates the cost of steps p, p+|g|, ...) */
     int32_t block;              /* threads per block of the rollout kernel: 0 = choose, else a multiple of 32 up to 448 */
+    int32_t model;              /* 0: state (x, y, yaw, v), control (a, delta) with delta the steering angle;
+                                   1: the steering-rate form of Eq. (5): state (x, y, yaw, v, delta),
+                                   control (a, omega), delta advanced by omega * dt.  Model 1 makes x0
+                                   5 entries and each row of x_out 5 entries (single-plan entry points
+                                   only: the batch engine and the server run model 0). */
 } mppi_params;
 
 /* Results of one iteration. */

@@ -54,6 +54,7 @@ class MppiParams(C.Structure):
         ("ego_offset", C.c_double * MAX_EGO), ("ego_radius", C.c_double * MAX_EGO),
         ("ref_mode", C.c_int32), ("sg_enable", C.c_int32), ("shift", C.c_int32), ("noise_bf16", C.c_int32),
         ("seed", C.c_uint64), ("session", C.c_uint32), ("group", C.c_int32), ("block", C.c_int32),
+        ("model", C.c_int32),
     ]
 
 
@@ -163,6 +164,7 @@ def make_params(p: Dict[str, object]) -> MppiParams:
     s.session = int(p["session"]) & 0xFFFFFFFF
     s.group = int(p.get("group", 0))
     s.block = int(p.get("block", 0))
+    s.model = int(p.get("model", 0))
     return s
 
 
@@ -181,6 +183,7 @@ class Planner:
                  max_ref: int = 0, max_circ: int = 0):
         self.params = dict(params)
         self.K, self.T = int(params["K"]), int(params["T"])
+        self.nx = 5 if int(params.get("model", 0)) == 1 else 4      # state entries
         self._p = make_params(params)
         h = _VP()
         rc = lib().mppi_create(C.byref(self._p), int(device), _VP(stream) if stream else None, int(max_ref),
@@ -215,13 +218,13 @@ class Planner:
 
     # the iteration -----------------------------------------------------------
     def plan(self, x0, ref, circles=None, centres=None) -> Tuple[np.ndarray, np.ndarray, Dict[str, object]]:
-        """One MPPI iteration from host arrays; returns (u*[T][2], x*[T+1][4], info)."""
+        """One MPPI iteration from host arrays; returns (u*[T][2], x*[T+1][nx], info)."""
         x0 = _f64(x0)
         ref = _f64(ref).reshape(-1, 2)
         circ = _f64(np.zeros((0, 5)) if circles is None else circles).reshape(-1, 5)
         cen = None if centres is None else _f64(centres)
         u = np.empty((self.T, 2))
-        x = np.empty((self.T + 1, 4))
+        x = np.empty((self.T + 1, self.nx))
         info = MppiInfo()
         rc = lib().mppi_plan(self._h, _dp(x0), _dp(ref), ref.shape[0], _dp(circ) if circ.shape[0] else None,
                              circ.shape[0], _dp(cen), _dp(u), _dp(x), C.byref(info))

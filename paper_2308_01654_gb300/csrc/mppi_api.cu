@@ -22,7 +22,8 @@ struct mppi_ctx {
     PlanConst pc{};
     PlanBuffers b{};
     double* d_in = nullptr;      // x0 | ref | circ | centres (binary64, device)
-    double* d_out = nullptr;     // u_out [T][2] | x_out [T+1][4]
+    double* d_out = nullptr;     // u_out [T][2] | x_out [T+1][nx]
+    int nx = 4;                  // state entries: 4, or 5 for the steering-rate model
     double* h_in = nullptr;      // pinned staging of the same layout
     double* h_out = nullptr;     // pinned staging of outputs
     DevState* h_state = nullptr; // pinned copy of the device record
@@ -93,6 +94,7 @@ static int check_params(const mppi_params* p, std::string& why) {
     for (int e = 0; e < p->n_ego; ++e)
         if (!isfinite(p->ego_offset[e]) || !isfinite(p->ego_radius[e])) { why = "ego circles must be finite"; return MPPI_ERR_ARG; }
     if (p->ref_mode != 0 && p->ref_mode != 1) { why = "ref_mode must be 0 or 1"; return MPPI_ERR_ARG; }
+    if (p->model != 0 && p->model != 1) { why = "model must be 0 or 1"; return MPPI_ERR_ARG; }
     if (!valid_group(p->group)) {
         why = "group must be 0, 1, 2, 4, 8, 16, 32, -2, -4, -8 or -16";
         return MPPI_ERR_ARG;
@@ -116,6 +118,7 @@ static PlanConst make_const(const mppi_params& p) {
     PlanConst c{};
     c.K = p.K;
     c.T = p.T;
+    c.model = p.model;
     c.dt = (float)p.dt;
     c.dt_over_L = (float)(p.dt / p.wheelbase);
     c.sig_a = (float)p.sigma[0];
@@ -274,8 +277,9 @@ int mppi_create(const mppi_params* params, int device, void* cuda_stream, int32_
     b.n_tt = (T + WS_TT - 1) / WS_TT;
     const SceneLayout Lmax = make_layout(T, c->cap_ref, c->cap_circ);
     const size_t zbytes = (size_t)T * K * (params->noise_bf16 ? 4 : 8);
-    c->in_elems = 4 + 2 * (size_t)c->cap_ref + 5 * (size_t)c->cap_circ + 2 * (size_t)T * c->cap_circ;
-    c->out_elems = 2 * (size_t)T + 4 * (size_t)(T + 1);
+    c->nx = params->model == 1 ? 5 : 4;
+    c->in_elems = 8 + 2 * (size_t)c->cap_ref + 5 * (size_t)c->cap_circ + 2 * (size_t)T * c->cap_circ;
+    c->out_elems = 2 * (size_t)T + (size_t)c->nx * (size_t)(T + 1);
     struct A {
         void** p;
         size_t n;
@@ -401,23 +405,24 @@ static int stage_host_inputs(mppi_ctx* c, const double* x0, const double* ref_xy
     if (rc != MPPI_OK) return rc;
     const int T = c->p.T;
     const size_t nr = 2 * (size_t)n_ref, nc = 5 * (size_t)n_circ, nt = centres ? 2 * (size_t)T * n_circ : 0;
-    if (!finite_all(x0, 4) || !finite_all(ref_xy, nr) || (nc && !finite_all((const double*)circ, nc)) ||
+    if (!finite_all(x0, (size_t)c->nx) || !finite_all(ref_xy, nr) || (nc && !finite_all((const double*)circ, nc)) ||
         (centres && !finite_all(centres, nt)))
         return fail(c, MPPI_ERR_ARG, "non-finite input");
     double* h = c->h_in;
-    memcpy(h, x0, 4 * sizeof(double));
-    memcpy(h + 4, ref_xy, nr * sizeof(double));
-    if (nc) memcpy(h + 4 + nr, circ, nc * sizeof(double));
-    if (nt) memcpy(h + 4 + nr + nc, centres, nt * sizeof(double));
-    const size_t n_in = 4 + nr + nc + nt;
+    // x0 in the first 8 entries (4 or 5 used): the reference stays 16-byte aligned
+    memcpy(h, x0, (size_t)c->nx * sizeof(double));
+    memcpy(h + 8, ref_xy, nr * sizeof(double));
+    if (nc) memcpy(h + 8 + nr, circ, nc * sizeof(double));
+    if (nt) memcpy(h + 8 + nr + nc, centres, nt * sizeof(double));
+    const size_t n_in = 8 + nr + nc + nt;
     if (n_in_out) *n_in_out = n_in;
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     if (copy)
         CK(cudaMemcpyAsync(c->d_in, h, n_in * sizeof(double), cudaMemcpyHostToDevice, c->stream), "input copy");
     in.x0 = c->d_in;
-    in.ref = c->d_in + 4;
-    in.circ = c->d_in + 4 + nr;
-    in.centres = nt ? c->d_in + 4 + nr + nc : nullptr;
+    in.ref = c->d_in + 8;
+    in.circ = c->d_in + 8 + nr;
+    in.centres = nt ? c->d_in + 8 + nr + nc : nullptr;
     in.n_ref = n_ref;
     in.n_circ = n_circ;
     in.u_out = c->d_out;
@@ -491,7 +496,7 @@ int mppi_plan(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n_ref
     }
     if (rc != MPPI_OK) return rc;
     memcpy(u_out, c->h_out, 2 * (size_t)T * sizeof(double));
-    memcpy(x_out, c->h_out + 2 * (size_t)T, 4 * (size_t)(T + 1) * sizeof(double));
+    memcpy(x_out, c->h_out + 2 * (size_t)T, (size_t)c->nx * (size_t)(T + 1) * sizeof(double));
     return MPPI_OK;
 }
 

@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 2) batch_rollout_kernel(B
         const BatchInst& d = a.inst[td.x];
         const int k = td.y + (int)threadIdx.x / G;   // G lanes per sample
         rollout_sample<G, TIME, BF16, false>(s_pc, s_L, smem, reinterpret_cast<const NT*>(a.z) + d.z_off,
-                                       a.table + d.table_off, s_x0, s_moving != 0, s_jb0, k, a.S + d.s_off, nullptr);
+                                       a.table + d.table_off, s_x0, 0.0f, s_moving != 0, s_jb0, k, a.S + d.s_off,
+                                       nullptr);
         __syncthreads();
     }
 }
@@ -564,6 +565,7 @@ static int build_submission(mppi_batch* B, Pipeline& p, mppi_request* req, int n
         if (!r.params || check_params_shared(r.params, why) != MPPI_OK)
             return bfail(B, MPPI_ERR_ARG, "plan " + std::to_string(i) + ": " + (r.params ? why : "params NULL"));
         const mppi_params& pr = *r.params;
+        if (pr.model != 0) return bfail(B, MPPI_ERR_ARG, "the batch engine runs model 0 (state x, y, yaw, v)");
         if (pr.noise_bf16 != B->noise_bf16) return bfail(B, MPPI_ERR_ARG, "noise precision differs from the batch's");
         if (r.slot < 0 || r.slot >= B->max_slots || used[(size_t)r.slot])
             return bfail(B, MPPI_ERR_ARG, "slot out of range or used twice in one submission");

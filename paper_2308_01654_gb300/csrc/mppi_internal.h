@@ -25,7 +25,8 @@ struct __align__(16) DevState {
     float4 x0f;                  // (0, 0, yaw0, v0): x0 in the local frame
     unsigned long long iter_used;  // iteration index of the last finished iteration
     int32_t moving;              // some obstacle circle has a nonzero velocity
-    int32_t pad_[3];
+    float delta0f;               // steering angle of x0 (model 1)
+    int32_t pad_[2];
 };
 
 // Byte offsets of the arrays in the scene blob that the rollout kernel stages into
@@ -50,6 +51,7 @@ struct SceneLayout {
 // Per-plan constants in the precision the kernels use.
 struct PlanConst {
     int K, T;
+    int model;               // 0: control (a, delta); 1: state carries delta, control (a, omega)
     float dt, dt_over_L;
     float sig_a, sig_d, amin, amax, dmin, dmax;
     float w_dist, w_target, w_yaw, w_speed, w_safe, w_terminal;
@@ -97,10 +99,15 @@ struct PlanBuffers {
 // and CIRC_BUCKETS + 1 bucket starts into the sorted circles, then the unsorted keys).
 constexpr int CIRC_BUCKETS = 64;
 
-inline size_t block_extra_bytes(const SceneLayout& L) {
+__host__ __device__ inline size_t block_extra_bytes(const SceneLayout& L) {
     return (size_t)16 * (L.n_l2 + 2 * (L.n_l1 + 1)) + 16 + (size_t)4 * ((CIRC_BUCKETS + 1 + 3) & ~3) +
            (size_t)4 * ((L.n_circ + 3) & ~3);   // unsorted keys while the block sorts
 }
+
+// Per-thread slots after the block's extras: the compensated steering angle of the
+// steering-rate model (float2 per thread, MAX_ROLLOUT_THREADS threads at most), kept out of
+// the registers of the other model.
+__host__ __device__ inline size_t steer_slots_bytes() { return (size_t)8 * MAX_ROLLOUT_THREADS; }
 
 // Capacity of the deferred bfloat16 rounding list (pairs beyond it are decided in place).
 constexpr unsigned NOISE_FIX_CAP = 1u << 16;

@@ -53,8 +53,9 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
 
     if (tid == 0) {
         if (b.fix_count) *b.fix_count = 0u;
-        for (int i = 0; i < 4; ++i) bad |= !isfinite(in.x0[i]);
+        for (int i = 0; i < (pc.model == 1 ? 5 : 4); ++i) bad |= !isfinite(in.x0[i]);
         b.state->x0f = make_float4(0.0f, 0.0f, (float)in.x0[2], (float)in.x0[3]);
+        b.state->delta0f = pc.model == 1 ? (float)in.x0[4] : 0.0f;
     }
     for (int t = tid; t < L.T; t += nth) {
         const double ua = b.U[2 * t], ud = b.U[2 * t + 1];
@@ -735,6 +736,13 @@ struct Roll {
     float px, py, th, v, px_c, py_c, th_c, v_c, sth, cth, tdp;
 };
 
+// The steering angle of the steering-rate model (value hi - lo, compensated like the other
+// states) lives in this thread's shared-memory slot.
+__device__ __forceinline__ float2* steer_slot(const unsigned char* smem, const SceneLayout& L) {
+    return reinterpret_cast<float2*>(const_cast<unsigned char*>(smem) + L.bytes + block_extra_bytes(L)) +
+           threadIdx.x;
+}
+
 // What the state cost of one step needs beyond the search: x_{t+1} (binary32 head and
 // compensation), its yaw direction, and the cheap terms c_target (Eq. 13), the speed
 // error, d_safe (Eq. 17) and the control cost of Eq. (8).
@@ -745,12 +753,22 @@ struct StepIn {
 // Eq. (5): explicit Euler from x_t to x_{t+1} under the perturbed controls of step t.
 template <bool BF16>
 __device__ __forceinline__ StepIn dyn_step(const PlanConst& pc, const float4 ct, float c0t, float2 zz, float2 tp,
-                                           Roll& r) {
+                                           Roll& r, float2* ds) {
     const Perturbed pe = perturb(ct.x, ct.y, zz, pc.sig_a, pc.sig_d, pc.amin, pc.amax, pc.dmin, pc.dmax);
     const float vt = r.v - r.v_c;
     float acc = pe.va;
     if (pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt) / pc.dt), pc.amin);
-    const float tn = tanf(pe.vd);
+    // model 0: the steering angle is the control; model 1: it is the state, advanced by the
+    // steering rate (the second control) after its tangent is taken (right-hand side at x_t)
+    float tn;
+    if (pc.model == 1) {
+        float2 d = *ds;
+        tn = tanf(d.x);
+        kahan_add(d.x, d.y, __fmul_rn(pe.vd, pc.dt));
+        *ds = d;
+    } else {
+        tn = tanf(pe.vd);
+    }
     // the increments are rounded products (no fused multiply-add), the same expressions as
     // the time-split form below, so both give the same bits
     kahan_add(r.px, r.px_c, __fmul_rn(__fmul_rn(vt, r.cth), pc.dt));
@@ -851,8 +869,8 @@ __device__ __forceinline__ float state_cost(const PlanConst& pc, const SceneLayo
 template <int G, bool TIME, bool BF16, bool STATS>
 __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneLayout& L, const unsigned char* smem,
                                                const typename NoiseT<BF16>::type* __restrict__ z,
-                                               const float2* table, float4 x0, bool moving, int jb0, int k,
-                                               double* S_out, unsigned long long* stats) {
+                                               const float2* table, float4 x0, float d0, bool moving, int jb0,
+                                               int k, double* S_out, unsigned long long* stats) {
     const Scene sc = scene_of(L, smem);
     const int lane = threadIdx.x & 31;
     const int lane_g = threadIdx.x & (G - 1);
@@ -869,6 +887,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
     r.th = x0.z;
     r.v = x0.w;
     r.px_c = r.py_c = r.th_c = r.v_c = 0.0f;
+    if (pc.model == 1) *steer_slot(smem, L) = make_float2(d0, 0.0f);
     sincosf(r.th, &r.sth, &r.cth);
     r.tdp = fmaf(tp.x, tp.x, tp.y * tp.y);      // |P_0 - T_P|^2 with P_0 = (0, 0)
     int jb = jb0, jbp = jb0;   // closest segment of the last evaluated step and of the one before
@@ -878,7 +897,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
     if constexpr (!TIME) {
         for (int t = 0; t < T; ++t) {
             const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
-            const StepIn s = dyn_step<BF16>(pc, sc.ctl[t], sc.c0[t], zz, tp, r);
+            const StepIn s = dyn_step<BF16>(pc, sc.ctl[t], sc.c0[t], zz, tp, r, steer_slot(smem, L));
             const float qx = state_cost<G, STATS>(pc, L, sc, table, s, t, t, t, has_table, moving, dconst, lane,
                                                   lane_g, mask, jb, jbp, cnt);
             kahan_add(s_hi, s_c, qx + s.qu);    // Eq. (6)
@@ -898,7 +917,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
                 for (int j = 0; j < nv; ++j) {
                     const int t = t0 + j;
                     const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
-                    const StepIn q = dyn_step<BF16>(pc, sc.ctl[t], sc.c0[t], zz, tp, r);
+                    const StepIn q = dyn_step<BF16>(pc, sc.ctl[t], sc.c0[t], zz, tp, r, steer_slot(smem, L));
                     if (j == my) e = q;
                 }
             } else {
@@ -906,7 +925,23 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
             const float4 ct = sc.ctl[tm];
             const Perturbed pe = perturb(ct.x, ct.y, NoiseT<BF16>::load(z + (size_t)tm * K + kk), pc.sig_a, pc.sig_d,
                                          pc.amin, pc.amax, pc.dmin, pc.dmax);
-            const float tn_own = tanf(pe.vd);
+            float tn_own;
+            if (pc.model == 1) {
+                // steering angle through the block (every lane); the tangent of the angle at
+                // the start of the own step
+                float2 d = *steer_slot(smem, L);
+                float d_own = d.x;
+#pragma unroll 1
+                for (int j = 0; j < nv; ++j) {
+                    const float w = __shfl_sync(mask, pe.vd, j, G);
+                    if (j == my) d_own = d.x;
+                    kahan_add(d.x, d.y, __fmul_rn(w, pc.dt));
+                }
+                *steer_slot(smem, L) = d;
+                tn_own = tanf(d_own);
+            } else {
+                tn_own = tanf(pe.vd);
+            }
             // yaw and speed through the block: every lane, the lanes' controls by shuffle
             float vt_own = 0.0f, th_own = 0.0f, thc_own = 0.0f, v_own = 0.0f, vc_own = 0.0f;
 #pragma unroll 1
@@ -1204,15 +1239,19 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
     }
     __syncthreads();
 
-    // x*: prefix sums in binary64 (sequential when the speed cap makes v nonlinear)
-    const double x0 = in.x0[0], y0 = in.x0[1], th0 = in.x0[2], v0 = in.x0[3];
+    // x*: prefix sums in binary64 (sequential when the speed cap makes v nonlinear).  Model 1
+    // carries the steering angle as a fifth state: delta_t = delta_0 + sum of omega dt.
+    const bool m1 = pc.model == 1;
+    const int nx = m1 ? 5 : 4;
+    const double x0 = in.x0[0], y0 = in.x0[1], th0 = in.x0[2], v0 = in.x0[3], d0 = m1 ? in.x0[4] : 0.0;
     if (t == 0) {
         in.x_out[0] = x0; in.x_out[1] = y0; in.x_out[2] = th0; in.x_out[3] = v0;
+        if (m1) in.x_out[4] = d0;
     }
     const double dt = pc.dt_d;
     if (pc.vcap) {
         if (t == 0) {
-            double x = x0, y = y0, th = th0, v = v0;
+            double x = x0, y = y0, th = th0, v = v0, d = d0;
             for (int s = 0; s < T; ++s) {
                 double a = s_us[2 * s];
                 const double lim = (pc.v_max_d - v) / dt;
@@ -1220,12 +1259,15 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
                 if (a < pc.amin_d) a = pc.amin_d;
                 float sn, cs;
                 sincosf((float)th, &sn, &cs);
-                const double nx = x + v * (double)cs * dt, ny = y + v * (double)sn * dt;
-                const double nth = th + v * (double)tanf((float)s_us[2 * s + 1]) / pc.wheelbase_d * dt;
+                const double steer = m1 ? d : s_us[2 * s + 1];
+                const double nx_ = x + v * (double)cs * dt, ny = y + v * (double)sn * dt;
+                const double nth = th + v * (double)tanf((float)steer) / pc.wheelbase_d * dt;
                 const double nv = v + a * dt;
-                x = nx; y = ny; th = nth; v = nv;
-                in.x_out[4 * (s + 1)] = x; in.x_out[4 * (s + 1) + 1] = y;
-                in.x_out[4 * (s + 1) + 2] = th; in.x_out[4 * (s + 1) + 3] = v;
+                const double nd = m1 ? d + s_us[2 * s + 1] * dt : 0.0;
+                x = nx_; y = ny; th = nth; v = nv; d = nd;
+                double* o = in.x_out + (size_t)nx * (s + 1);
+                o[0] = x; o[1] = y; o[2] = th; o[3] = v;
+                if (m1) o[4] = d;
             }
         }
     } else {
@@ -1233,7 +1275,12 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
         const double a = on ? s_us[2 * t] : 0.0, dl = on ? s_us[2 * t + 1] : 0.0;
         const double pv = block_scan_incl(on ? a * dt : 0.0, s_scan);          // v_{t+1} - v0
         const double vt = v0 + (pv - (on ? a * dt : 0.0));                      // v_t
-        const double dth = on ? vt * (double)tanf((float)dl) / pc.wheelbase_d * dt : 0.0;
+        double steer = dl, pd = 0.0;
+        if (m1) {
+            pd = block_scan_incl(on ? dl * dt : 0.0, s_scan);                    // delta_{t+1} - delta0
+            steer = d0 + (pd - (on ? dl * dt : 0.0));                            // delta_t
+        }
+        const double dth = on ? vt * (double)tanf((float)steer) / pc.wheelbase_d * dt : 0.0;
         const double pth = block_scan_incl(dth, s_scan);                         // yaw_{t+1} - yaw0
         const double tht = th0 + (pth - dth);                                    // yaw_t
         float sn = 0.0f, cs = 0.0f;
@@ -1242,10 +1289,12 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
         const double px = block_scan_incl(dx, s_scan);
         const double py = block_scan_incl(dy, s_scan);
         if (on) {
-            in.x_out[4 * (t + 1)] = x0 + px;
-            in.x_out[4 * (t + 1) + 1] = y0 + py;
-            in.x_out[4 * (t + 1) + 2] = th0 + pth;
-            in.x_out[4 * (t + 1) + 3] = v0 + pv;
+            double* o = in.x_out + (size_t)nx * (t + 1);
+            o[0] = x0 + px;
+            o[1] = y0 + py;
+            o[2] = th0 + pth;
+            o[3] = v0 + pv;
+            if (m1) o[4] = d0 + pd;
         }
     }
     // warm start for the next iteration (Algorithm 1, last loop)

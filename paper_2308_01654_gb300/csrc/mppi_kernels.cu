@@ -43,7 +43,9 @@ SceneLayout make_layout(int T, int n_ref, int n_circ) {
 }
 
 // the staged blob and what each block builds after it (block_extra_bytes)
-size_t rollout_smem_bytes(const SceneLayout& L) { return (size_t)L.bytes + block_extra_bytes(L); }
+size_t rollout_smem_bytes(const SceneLayout& L) {
+    return (size_t)L.bytes + block_extra_bytes(L) + steer_slots_bytes();
+}
 
 // -----------------------------------------------------------------------------
 // prep: one pass over the inputs.  Positions are shifted into a frame centred on
@@ -134,7 +136,8 @@ __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 2) rollout_kernel(PlanCon
     if (!__syncthreads_and(stage_to_smem(smem, b.scene, L.bytes, &bar, &b.state->flags))) return;
     build_boxes(smem, L, b.table, pc.has_table != 0);
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) / G;
-    rollout_sample<G, TIME, BF16, STATS>(pc, L, smem, z, b.table, b.state->x0f, b.state->moving != 0,
+    rollout_sample<G, TIME, BF16, STATS>(pc, L, smem, z, b.table, b.state->x0f, b.state->delta0f,
+                                         b.state->moving != 0,
                                          (int)(b.state->jkey & 0xffffffffu), k, b.S, b.stats);
 }
 

@@ -339,3 +339,67 @@ def test_rollout_stats_are_consistent_and_leave_state():
         u, x, info = pl.plan(prob.x0, prob.ref, prob.circles)
         orc = oracle.plan(prob, U=U0, iter_=3)
         check_iteration(prob, (u, x, info, pl.get_costs()), orc)
+
+
+# ----------------------------------------------------------------------------- steering-rate model
+
+def test_paper_preset_steering_rate_model_parity():
+    """Table I setting on the 5-state model (state carries delta, control (a, omega))."""
+    prob = sc.paper_preset()                          # K=2560, T=16, dt=0.25, lambda=150
+    outs, _, _, _ = run_gpu(prob)
+    orc = oracle.plan(prob)
+    assert outs[0][1].shape == (prob.T + 1, 5)
+    rep = check_iteration(prob, outs[0], orc)
+    print("paper_preset", rep)
+
+
+def test_paper_preset_three_iterations_teacher_forced():
+    prob = sc.paper_preset()
+    prob.params.update(shift=1)
+    U = np.zeros((prob.T, 2))
+    with mp.Planner(prob.params) as pl:
+        for i in range(3):
+            pl.set_controls(U, i)
+            u, x, info = pl.plan(prob.x0, prob.ref, prob.circles)
+            orc = oracle.plan(prob, U=U, iter_=i)
+            check_iteration(prob, (u, x, info, pl.get_costs()), orc)
+            U = orc.U
+
+
+def test_steering_rate_groups_give_identical_costs():
+    prob = sc.paper_preset()
+    prob.params.update(K=700, T=23)
+    prob.x0 = np.array([0.0, 0.3, 0.05, 6.0, -0.04])
+    S = {}
+    for g in (1, 2, 8, -2, -4, -8, -16):
+        outs, _, _, _ = run_gpu(prob, params=dict(prob.params, group=g))
+        S[g] = outs[0][3]
+    for g in S:
+        np.testing.assert_array_equal(S[g], S[1], err_msg=f"group {g}")
+
+
+def test_steering_rate_with_speed_cap_off_and_device_entry_point():
+    torch = pytest.importorskip("torch")
+    prob = sc.paper_preset()
+    prob.params.update(K=1000, T=30, v_max=math.inf)
+    outs, _, _, _ = run_gpu(prob)
+    orc = oracle.plan(prob)
+    check_iteration(prob, outs[0], orc)
+    dev = torch.device("cuda:0")
+    with mp.Planner(prob.params, stream=torch.cuda.current_stream().cuda_stream) as pl:
+        u = torch.empty((prob.T, 2), dtype=torch.float64, device=dev)
+        x = torch.empty((prob.T + 1, 5), dtype=torch.float64, device=dev)
+        pl.plan_device(torch.tensor(prob.x0, dtype=torch.float64, device=dev),
+                       torch.tensor(prob.ref, dtype=torch.float64, device=dev),
+                       torch.tensor(prob.circles, dtype=torch.float64, device=dev), None, u, x, wait=True)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(x.cpu().numpy(), outs[0][1])
+
+
+def test_batch_engine_rejects_the_steering_rate_model():
+    prob = sc.paper_preset()
+    with mp.BatchPlanner(max_slots=2, max_batch=2, max_samples=4096, max_rollout_steps=100000, max_T=32,
+                         max_ref=1024, max_circ=16) as bp:
+        with pytest.raises(mp.MppiError) as e:
+            bp.plan([mp.BatchPlan(prob.params, 0, prob.x0[:4], prob.ref, prob.circles, None)])
+        assert e.value.status == -1
