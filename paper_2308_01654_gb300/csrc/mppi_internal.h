@@ -51,7 +51,6 @@ struct SceneLayout {
 // Per-plan constants in the precision the kernels use.
 struct PlanConst {
     int K, T;
-    int model;               // 0: control (a, delta); 1: state carries delta, control (a, omega)
     float dt, dt_over_L;
     float sig_a, sig_d, amin, amax, dmin, dmax;
     float w_dist, w_target, w_yaw, w_speed, w_safe, w_terminal;
@@ -71,6 +70,9 @@ struct PlanConst {
     double g_a, g_d;         // (1 + alpha) R_a, (1 + alpha) R_d
     double half_Ra, half_Rd; // R / 2
     int sg_enable, shift;
+    // last, so the members above keep their offsets (the weighted-sum kernel measurably
+    // slows down when they move)
+    int model;               // 0: control (a, delta); 1: state carries delta, control (a, omega)
 };
 
 SceneLayout make_layout(int T, int n_ref, int n_circ);
