@@ -525,6 +525,41 @@ def run_closed_loop(args, world, rank, local):
     dist_done(world)
 
 
+def scenario_report(name: str, cycles: int, device: int = 0) -> dict:
+    """One closed-loop primitive on the steering-rate model with the paper's preset: what its
+    qualitative gates look at (clearance, speed against v_G, steering, lateral offset)."""
+    import numpy as np
+
+    from paper_2308_01654_gb300 import closed_loop, scenarios
+    prob = scenarios.by_name(name)
+    res = closed_loop.run(prob, cycles=cycles, device=device)
+    xs = res.states
+    t = res.plan_ms[3:] if len(res.plan_ms) > 6 else res.plan_ms
+    return {"cycles": cycles, "min_clearance_m": res.min_clearance,
+            "max_speed": float(xs[:, 3].max()), "v_G": float(prob.params["v_max"]),
+            "max_abs_steer": float(np.abs(xs[:, 4]).max()), "max_abs_rate": float(np.abs(res.controls[:, 1]).max()),
+            "final_y": float(xs[-1, 1]), "final_speed": float(xs[-1, 3]), "final_x": float(xs[-1, 0]),
+            "plan_ms": {"p50": float(np.median(t)), "p99": float(np.percentile(t, 99))}}
+
+
+def run_scenarios(args, world, rank, local):
+    """The scenario primitives (merge, follow, avoid) as closed loops on one GPU."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    rep = {n: scenario_report(n, args.cycles, local) for n in ("merge", "follow", "avoid")}
+    p50 = float(np.median([r["plan_ms"]["p50"] for r in rep.values()]))
+    out = {"metric": "closed-loop plans/s (scenario primitives, steering-rate model, Table I preset)",
+           "value": 1e3 / p50, "unit": "plans/s", "n_gpus": world, "steps": 3 * args.cycles, "warmup": 3,
+           "ms_per_step": p50, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64-reduce", "data": "synthetic",
+           "config": {"workload": f"scenarios: merge, follow, avoid; {args.cycles} cycles of 0.25 s each; "
+                                  f"K=2560 T=16"},
+           "scenarios": rep}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------------------ serving
 
 def serving_trace(sessions, rate: float, seconds: float, seed: int = 5, variants: int = 4):
@@ -713,7 +748,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="roofline",
                     choices=["roofline", "roofline_bf16", "closed_loop", "single_plan", "batched", "serving",
-                             "closed_loop_run", "paper_preset"])
+                             "closed_loop_run", "paper_preset", "scenarios"])
     ap.add_argument("--cycles", type=int, default=200)
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--sessions", type=int, default=512)
@@ -743,6 +778,8 @@ def main():
         run_serving(args, world, rank, local)
     elif args.workload == "closed_loop_run":
         run_closed_loop(args, world, rank, local)
+    elif args.workload == "scenarios":
+        run_scenarios(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
 

@@ -22,7 +22,7 @@ from .scenarios import Problem, predicted_centres
 @dataclass
 class LoopResult:
     states: np.ndarray            # [cycles + 1][4] true vehicle states
-    controls: np.ndarray          # [cycles][2] applied controls u*_0
+    controls: np.ndarray          # [cycles][2] applied controls u*_0 ((a, delta), or (a, omega) for model 1)
     plan_ms: np.ndarray           # [cycles] wall time of each mppi_plan call
     min_clearance: float          # smallest ego-circle / obstacle-circle clearance over the run (m)
     statuses: List[int] = field(default_factory=list)
@@ -33,6 +33,20 @@ def vehicle_step(x: np.ndarray, a: float, delta: float, dt: float, wheelbase: fl
     px, py, th, v = x
     return np.array([px + v * math.cos(th) * dt, py + v * math.sin(th) * dt,
                      th + v * math.tan(delta) / wheelbase * dt, v + a * dt])
+
+
+def vehicle5_step(x: np.ndarray, a: float, omega: float, dt: float, wheelbase: float) -> np.ndarray:
+    """The environment's vehicle in the steering-rate form: the steering angle is a state
+    driven by the applied rate."""
+    return np.concatenate([vehicle_step(x[:4], a, x[4], dt, wheelbase), [x[4] + omega * dt]])
+
+
+def applied_accel(p: dict, a: float, v: float) -> float:
+    """The speed cap of the plans applies to the vehicle too: a <= (v_max - v) / dt."""
+    vmax = float(p["v_max"])
+    if math.isfinite(vmax):
+        a = max(min(a, (vmax - v) / float(p["dt"])), float(p["u_min"][0]))
+    return a
 
 
 def clearance(p: dict, x: np.ndarray, circles: np.ndarray) -> float:
@@ -68,7 +82,8 @@ def run(prob: Problem, cycles: int = 200, device: int = 0, use_table: Optional[b
             statuses.append(0)
             a, d = float(u[0, 0]), float(u[0, 1])
             controls.append((a, d))
-            x = vehicle_step(x, a, d, dt, L)
+            a = applied_accel(p, a, x[3])
+            x = vehicle5_step(x, a, d, dt, L) if int(p.get("model", 0)) == 1 else vehicle_step(x, a, d, dt, L)
             circ[:, 0] += circ[:, 3] * dt
             circ[:, 1] += circ[:, 4] * dt
             states.append(x.copy())

@@ -230,6 +230,45 @@ def paper_preset(seed: int = 0) -> Problem:
     return Problem(p, np.array([0.0, 0.0, yaw0, 7.0, 0.0]), ref, circles, None, "paper_preset")
 
 
+def car_circles(x: float, y: float, yaw: float = 0.0, speed: float = 0.0, length: float = 4.5,
+                width: float = 1.8) -> np.ndarray:
+    """A car-sized object as three circles along its length (Fig. 3), each the circle through
+    the corners of a third of the car, moving at `speed` along its heading."""
+    h = length / 6.0
+    r = math.hypot(h, width / 2.0)
+    c, s = math.cos(yaw), math.sin(yaw)
+    return np.array([[x + o * c, y + o * s, r, speed * c, speed * s] for o in (-2 * h, 0.0, 2 * h)])
+
+
+def _primitive(seed: int, name: str) -> Problem:
+    p = paper_preset(seed).params
+    p["session"] = {"merge": 1, "follow": 2, "avoid": 3}[name]
+    ref = straight_lane(800, 0.5)
+    return p, ref
+
+
+def scenario_merge(seed: int = 0) -> Problem:
+    """Lane merge: the vehicle starts on a parallel lane 3.5 m to the right of the reference lane
+    at 7 m/s and joins it; no objects."""
+    p, ref = _primitive(seed, "merge")
+    return Problem(p, np.array([0.0, -3.5, 0.0, 7.0, 0.0]), ref, np.zeros((0, 5)), None, "merge")
+
+
+def scenario_follow(seed: int = 0) -> Problem:
+    """Following: a car 30 m ahead in the lane drives at 4 m/s; the vehicle starts at 7 m/s.
+    The speed-dependent safe distance d_safe = 1.36 v + 11 m makes it drop back."""
+    p, ref = _primitive(seed, "follow")
+    return Problem(p, np.array([0.0, 0.0, 0.0, 7.0, 0.0]), ref, car_circles(30.0, 0.0, 0.0, 4.0), None, "follow")
+
+
+def scenario_avoid(seed: int = 0) -> Problem:
+    """Object avoidance (the collision-only cost with a 0.7 m margin): a stopped car 40 m ahead
+    reaches 1.0 m into the lane from the left."""
+    p, ref = _primitive(seed, "avoid")
+    p.update(collision_only=1, d_safe_c=0.0, d_safe_0=0.7)
+    return Problem(p, np.array([0.0, 0.0, 0.0, 7.0, 0.0]), ref, car_circles(40.0, 1.9, 0.0, 0.0), None, "avoid")
+
+
 def by_name(name: str, seed: int = 0) -> Problem:
     if name == "single_plan":
         return single_plan(seed)
@@ -241,4 +280,6 @@ def by_name(name: str, seed: int = 0) -> Problem:
         return roofline(seed, bf16=True)
     if name == "paper_preset":
         return paper_preset(seed)
+    if name in ("merge", "follow", "avoid"):
+        return {"merge": scenario_merge, "follow": scenario_follow, "avoid": scenario_avoid}[name](seed)
     raise KeyError(name)
