@@ -46,6 +46,7 @@ class OrcParams(C.Structure):
         ("seed", C.c_uint64),
         ("session", C.c_uint32),
         ("model", C.c_int32),
+        ("cost_to_go", C.c_int32),
     ]
 
 
@@ -89,6 +90,11 @@ def lib():
         L.orc_noise.argtypes = [C.POINTER(OrcParams), C.c_uint32, dp]
         L.orc_bicycle_step.argtypes = [dp, C.c_double, C.c_double, C.c_double, C.c_double, dp]
         L.orc_bicycle5_step.argtypes = [dp, C.c_double, C.c_double, C.c_double, C.c_double, dp]
+        L.orc_softmin_update_ctg.argtypes = [C.c_int32, C.c_int32, dp, dp, C.c_double, dp, dp]
+        L.orc_softmin_update_ctg.restype = C.c_int32
+        L.orc_rollout_cost_ctg.argtypes = [C.POINTER(OrcParams), dp, dp, dp, dp, C.c_int32, dp, C.c_int32,
+                                           dp, dp, dp, dp]
+        L.orc_rollout_cost_ctg.restype = C.c_double
         L.orc_nearest_ref.argtypes = [dp, C.c_int32, C.c_int32, C.c_double, C.c_double,
                                       C.POINTER(C.c_int32), dp, dp]
         L.orc_nearest_ref.restype = C.c_double
@@ -150,6 +156,7 @@ def make_params(p: Dict[str, object]) -> OrcParams:
     s.seed = int(p["seed"]) & 0xFFFFFFFFFFFFFFFF
     s.session = int(p["session"]) & 0xFFFFFFFF
     s.model = int(p.get("model", 0))
+    s.cost_to_go = int(p.get("cost_to_go", 0))
     return s
 
 
@@ -249,6 +256,31 @@ def softmin_update(S, eps, lam: float):
     info = OrcInfo()
     lib().orc_softmin_update(K, T, _dp(S), _dp(eps), lam, _dp(dU), C.byref(info), _dp(w))
     return dU, w, info
+
+
+def softmin_update_ctg(Sctg, eps, lam: float):
+    """Eq. (11) read per step: Sctg[T][K] costs from step t on, eps'[T][K][2]; returns (dU, eta_t)."""
+    Sctg = _f64(Sctg)
+    eps = _f64(eps)
+    T, K = Sctg.shape
+    dU = np.empty((T, 2))
+    eta = np.empty(T)
+    lib().orc_softmin_update_ctg(K, T, _dp(Sctg), _dp(eps), lam, _dp(dU), _dp(eta))
+    return dU, eta
+
+
+def rollout_cost_ctg(p, x0, U, z_k, ref, circles, centres=None):
+    """S of one sample and its cost from every step on: (S, ctg[T], eps'[T][2])."""
+    s = make_params(p)
+    c = _f64(circles).reshape(-1, 5)
+    eps = np.empty((s.T, 2))
+    ctg = np.empty(s.T)
+    m = C.c_double()
+    r = _f64(ref)
+    S = lib().orc_rollout_cost_ctg(C.byref(s), _dp(_f64(x0)), _dp(_f64(U)), _dp(_f64(z_k)), _dp(r), r.shape[0],
+                                   _dp(c), c.shape[0], _dp(None if centres is None else _f64(centres)),
+                                   _dp(eps), C.pointer(m), _dp(ctg))
+    return S, ctg, eps
 
 
 def savgol5(u) -> np.ndarray:

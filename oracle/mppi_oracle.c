@@ -374,6 +374,13 @@ double orc_rollout_cost(const orc_params* p, const double x0[4], const double* U
                         const double* ref, int32_t n_ref, const orc_circle* circ, int32_t n_circ,
                         const double* centres, double* eps_out, double* margin)
 {
+    return orc_rollout_cost_ctg(p, x0, U, z_k, ref, n_ref, circ, n_circ, centres, eps_out, margin, NULL);
+}
+
+double orc_rollout_cost_ctg(const orc_params* p, const double x0[4], const double* U, const double* z_k,
+                            const double* ref, int32_t n_ref, const orc_circle* circ, int32_t n_circ,
+                            const double* centres, double* eps_out, double* margin, double* ctg)
+{
     double x[5] = {x0[0], x0[1], x0[2], x0[3], p->model == 1 ? x0[4] : 0.0};
     double prev_x = x0[0], prev_y = x0[1];
     double* cxy = n_circ > 0 ? (double*)malloc(sizeof(double) * 2 * (size_t)n_circ) : NULL;
@@ -401,12 +408,20 @@ double orc_rollout_cost(const orc_params* p, const double x0[4], const double* U
         double qx = state_cost(p, xn, prev_x, prev_y, ref, n_ref, circ, n_circ, cxy, margin);
         double qu = control_cost(p, u, ep);
         S += qx + qu;
+        if (ctg) ctg[t] = qx + qu;          /* step costs for now, summed from the end below */
         last_qx = qx;
         prev_x = xn[0];
         prev_y = xn[1];
         memcpy(x, xn, sizeof(x));
     }
     S += p->w_terminal * last_qx;       /* phi(x_T) */
+    if (ctg) {
+        double acc = p->w_terminal * last_qx;
+        for (int32_t t = p->T - 1; t >= 0; --t) {
+            acc += ctg[t];
+            ctg[t] = acc;
+        }
+    }
     free(cxy);
     return S;
 }
@@ -451,6 +466,32 @@ int32_t orc_softmin_update(int32_t K, int32_t T, const double* S, const double* 
     }
     if (info) info->eta = eta;
     if (!weights) free(w);
+    return n_fin;
+}
+
+/* Eq. (11) read per step: at each t the weights come from the cost still to come. */
+int32_t orc_softmin_update_ctg(int32_t K, int32_t T, const double* Sctg, const double* eps, double lam,
+                               double* dU, double* eta_t)
+{
+    int32_t n_fin = 0;
+    for (int32_t k = 0; k < K; ++k)
+        if (isfinite(Sctg[k])) ++n_fin;
+    for (int32_t t = 0; t < T; ++t) {
+        const double* St = Sctg + (size_t)t * K;
+        double smin = INFINITY;
+        for (int32_t k = 0; k < K; ++k)
+            if (isfinite(St[k]) && St[k] < smin) smin = St[k];
+        double eta = 0.0, num[2] = {0.0, 0.0};
+        if (isfinite(smin)) {
+            for (int32_t k = 0; k < K; ++k) {
+                const double w = isfinite(St[k]) ? exp(-(St[k] - smin) / lam) : 0.0;
+                eta += w;
+                for (int c = 0; c < 2; ++c) num[c] += w * eps[((size_t)t * K + k) * 2 + c];
+            }
+        }
+        for (int c = 0; c < 2; ++c) dU[2 * t + c] = eta > 0.0 ? num[c] / eta : 0.0;
+        if (eta_t) eta_t[t] = eta;
+    }
     return n_fin;
 }
 
@@ -553,10 +594,12 @@ int orc_plan(const orc_params* p, uint32_t iter, const double x0[4],
     /* Algorithm 1: for m in parallel: roll out and accumulate S(tau_m) */
     double* S = S_out ? S_out : (double*)malloc(sizeof(double) * K);
     double* eps = eps_out ? eps_out : (double*)malloc(sizeof(double) * KT2);
+    double* ctg = p->cost_to_go ? (double*)malloc(sizeof(double) * (size_t)K * T) : NULL;
 #pragma omp parallel
     {
         double* zk = (double*)malloc(sizeof(double) * 2 * (size_t)T);
         double* ek = (double*)malloc(sizeof(double) * 2 * (size_t)T);
+        double* ck = (double*)malloc(sizeof(double) * (size_t)T);
 #pragma omp for schedule(dynamic, 16)
         for (int32_t k = 0; k < K; ++k) {
             for (int32_t t = 0; t < T; ++t) {
@@ -564,7 +607,10 @@ int orc_plan(const orc_params* p, uint32_t iter, const double x0[4],
                 zk[2 * t + 1] = z[((size_t)t * K + k) * 2 + 1];
             }
             double m;
-            S[k] = orc_rollout_cost(p, x0, U, zk, ref, n_ref, circ, n_circ, centres, ek, &m);
+            S[k] = orc_rollout_cost_ctg(p, x0, U, zk, ref, n_ref, circ, n_circ, centres, ek, &m,
+                                        ctg ? ck : NULL);
+            if (ctg)
+                for (int32_t t = 0; t < T; ++t) ctg[(size_t)t * K + k] = ck[t];
             if (margin_out) margin_out[k] = m;
             for (int32_t t = 0; t < T; ++t) {
                 eps[((size_t)t * K + k) * 2] = ek[2 * t];
@@ -573,12 +619,22 @@ int orc_plan(const orc_params* p, uint32_t iter, const double x0[4],
         }
         free(zk);
         free(ek);
+        free(ck);
     }
 
     /* Algorithm 1: S_min, then the update of Eq. (11) */
     double* dU = (double*)malloc(sizeof(double) * 2 * (size_t)T);
     orc_info local;
     int32_t n_fin = orc_softmin_update(K, T, S, eps, p->lam, dU, &local, NULL);
+    if (ctg) {
+        /* the per-step reading replaces the update; S_min, the argmin and eta stay those of
+           the whole cost (step 0) */
+        double* eta_t = (double*)malloc(sizeof(double) * (size_t)T);
+        orc_softmin_update_ctg(K, T, ctg, eps, p->lam, dU, eta_t);
+        local.eta = eta_t[0];
+        free(eta_t);
+        free(ctg);
+    }
     if (info) *info = local;
     int rc = 0;
     if (n_fin == 0) {

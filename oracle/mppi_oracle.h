@@ -50,6 +50,8 @@ typedef struct {
     uint32_t session;
     int32_t model;                         /* 0: state (x, y, yaw, v), control (a, delta);
                                               1: state (x, y, yaw, v, delta), control (a, omega) */
+    int32_t cost_to_go;                    /* 1: the update of step t weighs each sample by the cost
+                                              still to come from step t (Eq. (11) read per step) */
 } orc_params;
 
 /* state entries of a model: 4 or 5 */
@@ -97,11 +99,21 @@ double orc_obstacle_distance(const orc_params* p, const double x[4], const orc_c
 double orc_rollout_cost(const orc_params* p, const double x0[4], const double* U, const double* z_k,
                         const double* ref_xy, int32_t n_ref, const orc_circle* circ, int32_t n_circ,
                         const double* centres, double* eps_out, double* margin);
+/* The same with the cost from every step on: ctg[t] = sum of the step costs s >= t plus the
+   terminal cost (ctg[0] is the returned S up to summation order). */
+double orc_rollout_cost_ctg(const orc_params* p, const double x0[4], const double* U, const double* z_k,
+                            const double* ref_xy, int32_t n_ref, const orc_circle* circ, int32_t n_circ,
+                            const double* centres, double* eps_out, double* margin, double* ctg);
 
 /* ---- update (Eq. (11)), smoothing (Eq. (19)) and optimal rollout ---- */
 /* eps[(t*K + k)*2 + c]; dU[t*2 + c] = sum_k w_k eps'_{t,k} / eta.  Returns n_finite. */
 int32_t orc_softmin_update(int32_t K, int32_t T, const double* S, const double* eps, double lam,
                            double* dU, orc_info* info, double* weights);
+/* Eq. (11) with a per-step cost: Sctg[t*K + k] is sample k's cost from step t on; each step
+   gets its own S_min and softmin weights.  eta_t[T] (optional) receives the normalisers.
+   Returns the number of samples whose total cost Sctg[0][k] is finite. */
+int32_t orc_softmin_update_ctg(int32_t K, int32_t T, const double* Sctg, const double* eps, double lam,
+                               double* dU, double* eta_t);
 void orc_savgol5(int32_t T, const double* u_in, int32_t stride, double* u_out);
 void orc_rollout_states(const orc_params* p, const double x0[4], const double* u, double* xs);
 
