@@ -113,6 +113,9 @@ typedef struct {
                                    control (a, omega), delta advanced by omega * dt.  Model 1 makes x0
                                    5 entries and each row of x_out 5 entries (single-plan entry points
                                    only: the batch engine and the server run model 0). */
+    int32_t cost_to_go;         /* 1: the update of step t weighs each sample by its cost from step t on
+                                   (Eq. (11) read per step: S_min, softmin weights and normaliser per step);
+                                   0: by its whole cost.  Single-plan entry points only. */
 } mppi_params;
 
 /* Results of one iteration. */

@@ -54,7 +54,7 @@ class MppiParams(C.Structure):
         ("ego_offset", C.c_double * MAX_EGO), ("ego_radius", C.c_double * MAX_EGO),
         ("ref_mode", C.c_int32), ("sg_enable", C.c_int32), ("shift", C.c_int32), ("noise_bf16", C.c_int32),
         ("seed", C.c_uint64), ("session", C.c_uint32), ("group", C.c_int32), ("block", C.c_int32),
-        ("model", C.c_int32),
+        ("model", C.c_int32), ("cost_to_go", C.c_int32),
     ]
 
 
@@ -165,6 +165,7 @@ def make_params(p: Dict[str, object]) -> MppiParams:
     s.group = int(p.get("group", 0))
     s.block = int(p.get("block", 0))
     s.model = int(p.get("model", 0))
+    s.cost_to_go = int(p.get("cost_to_go", 0))
     return s
 
 

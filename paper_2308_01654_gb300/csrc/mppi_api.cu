@@ -95,6 +95,7 @@ static int check_params(const mppi_params* p, std::string& why) {
         if (!isfinite(p->ego_offset[e]) || !isfinite(p->ego_radius[e])) { why = "ego circles must be finite"; return MPPI_ERR_ARG; }
     if (p->ref_mode != 0 && p->ref_mode != 1) { why = "ref_mode must be 0 or 1"; return MPPI_ERR_ARG; }
     if (p->model != 0 && p->model != 1) { why = "model must be 0 or 1"; return MPPI_ERR_ARG; }
+    if (p->cost_to_go != 0 && p->cost_to_go != 1) { why = "cost_to_go must be 0 or 1"; return MPPI_ERR_ARG; }
     if (!valid_group(p->group)) {
         why = "group must be 0, 1, 2, 4, 8, 16, 32, -2, -4, -8 or -16";
         return MPPI_ERR_ARG;
@@ -119,6 +120,7 @@ static PlanConst make_const(const mppi_params& p) {
     c.K = p.K;
     c.T = p.T;
     c.model = p.model;
+    c.cost_to_go = p.cost_to_go;
     c.dt = (float)p.dt;
     c.dt_over_L = (float)(p.dt / p.wheelbase);
     c.sig_a = (float)p.sigma[0];
@@ -186,7 +188,8 @@ PlanConst make_const_shared(const mppi_params& p) { return make_const(p); }
 static void free_all(mppi_ctx* c) {
     PlanBuffers& b = c->b;
     void* dev[] = {b.state, b.scene, b.table, b.z, b.S, b.w, b.eta_part, b.min_part, b.min_idx_part,
-                   b.min_cnt_part, b.du_part, b.U, b.stats, b.fix_count, b.fix_list, c->d_in, c->d_out};
+                   b.min_cnt_part, b.du_part, b.U, b.stats, b.fix_count, b.fix_list, b.ctg_prefix, b.wt,
+                   b.eta_t, c->d_in, c->d_out};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_in) cudaFreeHost(c->h_in);
@@ -299,6 +302,9 @@ int mppi_create(const mppi_params* params, int device, void* cuda_stream, int32_
         {(void**)&b.stats, sizeof(unsigned long long) * 8},
         {(void**)&b.fix_count, sizeof(unsigned)},
         {(void**)&b.fix_list, sizeof(uint2) * (c->p.noise_bf16 ? NOISE_FIX_CAP : 1u)},
+        {(void**)&b.ctg_prefix, sizeof(float) * (c->p.cost_to_go ? (size_t)K * T : 1u)},
+        {(void**)&b.wt, sizeof(float) * (c->p.cost_to_go ? (size_t)K * T : 1u)},
+        {(void**)&b.eta_t, sizeof(double) * (size_t)T},
         {(void**)&c->d_in, sizeof(double) * c->in_elems},
         {(void**)&c->d_out, sizeof(double) * c->out_elems},
     };

@@ -565,7 +565,8 @@ static int build_submission(mppi_batch* B, Pipeline& p, mppi_request* req, int n
         if (!r.params || check_params_shared(r.params, why) != MPPI_OK)
             return bfail(B, MPPI_ERR_ARG, "plan " + std::to_string(i) + ": " + (r.params ? why : "params NULL"));
         const mppi_params& pr = *r.params;
-        if (pr.model != 0) return bfail(B, MPPI_ERR_ARG, "the batch engine runs model 0 (state x, y, yaw, v)");
+        if (pr.model != 0 || pr.cost_to_go != 0)
+            return bfail(B, MPPI_ERR_ARG, "the batch engine runs model 0 with whole-cost weights");
         if (pr.noise_bf16 != B->noise_bf16) return bfail(B, MPPI_ERR_ARG, "noise precision differs from the batch's");
         if (r.slot < 0 || r.slot >= B->max_slots || used[(size_t)r.slot])
             return bfail(B, MPPI_ERR_ARG, "slot out of range or used twice in one submission");

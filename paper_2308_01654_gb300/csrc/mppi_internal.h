@@ -73,6 +73,7 @@ struct PlanConst {
     // last, so the members above keep their offsets (the weighted-sum kernel measurably
     // slows down when they move)
     int model;               // 0: control (a, delta); 1: state carries delta, control (a, omega)
+    int cost_to_go;          // 1: per-step weights from the cost still to come
 };
 
 SceneLayout make_layout(int T, int n_ref, int n_circ);
@@ -93,6 +94,9 @@ struct PlanBuffers {
     unsigned long long* stats;  // [7] work counters (STATS launches only)
     unsigned* fix_count;     // bfloat16 noise: pairs whose rounding is taken again in binary64
     uint2* fix_list;         // [NOISE_FIX_CAP] their (step pair j, sample k); null: decided in place
+    float* ctg_prefix;       // [T][K] cost of steps 0..t-1 per sample (cost-to-go form), or null
+    float* wt;               // [T][K] per-step softmin weights (cost-to-go form)
+    double* eta_t;           // [T] per-step normalisers (cost-to-go form)
     int n_mblk, n_wblk, n_kt, n_tt, kt_size;
 };
 

@@ -870,7 +870,8 @@ template <int G, bool TIME, bool BF16, bool STATS>
 __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneLayout& L, const unsigned char* smem,
                                                const typename NoiseT<BF16>::type* __restrict__ z,
                                                const float2* table, float4 x0, float d0, bool moving, int jb0,
-                                               int k, double* S_out, unsigned long long* stats) {
+                                               int k, double* S_out, unsigned long long* stats,
+                                               float* prefix = nullptr) {
     const Scene sc = scene_of(L, smem);
     const int lane = threadIdx.x & 31;
     const int lane_g = threadIdx.x & (G - 1);
@@ -900,6 +901,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
             const StepIn s = dyn_step<BF16>(pc, sc.ctl[t], sc.c0[t], zz, tp, r, steer_slot(smem, L));
             const float qx = state_cost<G, STATS>(pc, L, sc, table, s, t, t, t, has_table, moving, dconst, lane,
                                                   lane_g, mask, jb, jbp, cnt);
+            if (prefix && lane_g == 0 && k < K) prefix[(size_t)t * K + k] = s_hi - s_c;   // cost of steps < t
             kahan_add(s_hi, s_c, qx + s.qu);    // Eq. (6)
             q_last = qx;
         }
@@ -996,15 +998,18 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
             const float qx = state_cost<1, STATS>(pc, L, sc, table, e, tm, t0, tb1, has_table, moving, dconst,
                                                   lane, 0, mask, jb, jbp, cnt);
             const float c = qx + e.qu;
+            float pre_own = 0.0f;
 #pragma unroll
             for (int j = 0; j < G; ++j) {
                 const float cj = __shfl_sync(mask, c, j, G);
                 const float qj = __shfl_sync(mask, qx, j, G);
                 if (t0 + j < T) {
+                    if (j == lane_g) pre_own = s_hi - s_c;
                     kahan_add(s_hi, s_c, cj);   // Eq. (6), in step order
                     q_last = qj;
                 }
             }
+            if (prefix && lane_g < nv && k < K) prefix[(size_t)(t0 + lane_g) * K + k] = pre_own;   // cost of steps < t
         }
     }
     if (lane_g == 0 && k < K) {
@@ -1123,7 +1128,7 @@ __device__ __forceinline__ double clampd(double x, double lo, double hi) { retur
 template <bool BF16>
 __device__ __forceinline__ void wsum_tile(const PlanConst& pc, const float4* ctl,
                                           const typename NoiseT<BF16>::type* __restrict__ z, const float* w, int kt,
-                                          int t0, int kt_size, double* du_part) {
+                                          int t0, int kt_size, double* du_part, const float* wt = nullptr) {
     __shared__ float red[8][WS_TT][2];
     const int K = pc.K, T = pc.T;
     const int t1 = min(T, t0 + WS_TT);
@@ -1138,6 +1143,10 @@ __device__ __forceinline__ void wsum_tile(const PlanConst& pc, const float4* ctl
     for (int t = t0; t < t1; ++t) {
         const float4 ct = ctl[t];
         float aa = 0.0f, ad = 0.0f;
+        if (wt) {                  // cost-to-go form: weights of this step
+#pragma unroll
+            for (int j = 0; j < WS_J; ++j) wj[j] = kj[j] < K ? wt[(size_t)t * K + kj[j]] : 0.0f;
+        }
 #pragma unroll
         for (int j = 0; j < WS_J; ++j) {
             if (kj[j] < K) {
@@ -1198,7 +1207,7 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
         double e = 0.0;
         for (int i = t; i < b.n_wblk; i += blockDim.x) e += b.eta_part[i];
         e = block_sum_d(e);
-        if (t == 0) s_eta = e;
+        if (t == 0) s_eta = pc.cost_to_go ? b.eta_t[0] : e;     // cost-to-go form: reported eta of step 0
     }
     __syncthreads();
     if (s_status != 0) {
@@ -1216,7 +1225,8 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
 #pragma unroll 8
         for (int kt = 0; kt < b.n_kt; ++kt) num += b.du_part[(size_t)kt * 2 * T + i];
         const bool ch = i & 1;
-        s_un[i] = clampd(b.U[i] + num / eta, ch ? pc.dmin_d : pc.amin_d, ch ? pc.dmax_d : pc.amax_d);
+        const double et = pc.cost_to_go ? b.eta_t[i >> 1] : eta;   // cost-to-go form: eta of the step
+        s_un[i] = clampd(b.U[i] + num / et, ch ? pc.dmin_d : pc.amin_d, ch ? pc.dmax_d : pc.amax_d);
     }
     __syncthreads();
     for (int i = t; i < 2 * T; i += blockDim.x) {

@@ -137,8 +137,8 @@ __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 2) rollout_kernel(PlanCon
     build_boxes(smem, L, b.table, pc.has_table != 0);
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     rollout_sample<G, TIME, BF16, STATS>(pc, L, smem, z, b.table, b.state->x0f, b.state->delta0f,
-                                         b.state->moving != 0,
-                                         (int)(b.state->jkey & 0xffffffffu), k, b.S, b.stats);
+                                         b.state->moving != 0, (int)(b.state->jkey & 0xffffffffu), k, b.S, b.stats,
+                                         pc.cost_to_go ? b.ctg_prefix : nullptr);
 }
 
 // -----------------------------------------------------------------------------
@@ -200,6 +200,39 @@ __global__ void __launch_bounds__(256) weights_kernel(int K, double lam, PlanBuf
 }
 
 // -----------------------------------------------------------------------------
+// cost-to-go form of Eq. (11): one block per step t.  The cost of sample k from step t on is
+// S_k - P_{t,k} (P: its cost of the steps before t, written by the rollout); the block takes
+// their minimum, then the weights exp(-(S~ - min) / lambda) (binary32 exponential of the
+// binary64 exponent) and their binary64 sum, the step's normaliser.
+// -----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) ctg_weights_kernel(int K, double lam, PlanBuffers b) {
+    const int t = blockIdx.x;
+    const float* P = b.ctg_prefix + (size_t)t * K;
+    MinRec r{INFINITY, 0x7fffffff, 0};
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const double s = b.S[k] - (double)P[k];
+        if (isfinite(s) && s < r.v) {
+            r.v = s;
+            r.i = k;
+        }
+    }
+    r = block_min(r);
+    __shared__ double s_min;
+    if (threadIdx.x == 0) s_min = r.v;
+    __syncthreads();
+    const double smin = s_min;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const double s = b.S[k] - (double)P[k];
+        const float w = isfinite(s) ? expf((float)((smin - s) / lam)) : 0.0f;
+        b.wt[(size_t)t * K + k] = w;
+        acc += (double)w;
+    }
+    acc = block_sum_d(acc);
+    if (threadIdx.x == 0) b.eta_t[t] = acc;
+}
+
+// -----------------------------------------------------------------------------
 // wsum: per step t, sum_k w_k eps'_{t,k}.  Each thread owns J samples of a k-tile,
 // recomputes eps' from z exactly as the rollout did, accumulates in binary32 over
 // its J samples and its warp (32 x J products), and the per-warp partials are
@@ -209,7 +242,8 @@ template <bool BF16>
 __global__ void __launch_bounds__(256) wsum_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
                                                    const typename NoiseT<BF16>::type* __restrict__ z) {
     const float4* ctl = reinterpret_cast<const float4*>(b.scene + L.off_ctl);
-    wsum_tile<BF16>(pc, ctl, z, b.w, blockIdx.x, blockIdx.y * WS_TT, b.kt_size, b.du_part);
+    wsum_tile<BF16>(pc, ctl, z, b.w, blockIdx.x, blockIdx.y * WS_TT, b.kt_size, b.du_part,
+                    pc.cost_to_go ? b.wt : nullptr);
 }
 
 // -----------------------------------------------------------------------------
@@ -357,7 +391,10 @@ cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const Pl
     if ((e = mark()) != cudaSuccess) return e;
     argmin_kernel<<<b.n_mblk, 256, 0, st>>>(pc.K, b);
     if ((e = mark()) != cudaSuccess) return e;
-    weights_kernel<<<b.n_wblk, 256, 0, st>>>(pc.K, pc.lam, b);
+    if (pc.cost_to_go)
+        ctg_weights_kernel<<<pc.T, 256, 0, st>>>(pc.K, pc.lam, b);
+    else
+        weights_kernel<<<b.n_wblk, 256, 0, st>>>(pc.K, pc.lam, b);
     if ((e = mark()) != cudaSuccess) return e;
     {
         dim3 grid(b.n_kt, b.n_tt);

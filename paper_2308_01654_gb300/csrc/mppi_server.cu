@@ -254,7 +254,8 @@ int mppi_server_enqueue(mppi_server* S, const mppi_params* params, int32_t sessi
                         const double* centres, uint64_t* request_id) {
     if (!S || !params || !x0 || !ref_xy || (n_circ > 0 && !circ)) return sfail(S, MPPI_ERR_ARG, "NULL argument");
     if (session < 0 || session >= S->cfg.max_sessions) return sfail(S, MPPI_ERR_ARG, "session out of range");
-    if (params->model != 0) return sfail(S, MPPI_ERR_ARG, "the server runs model 0 (state x, y, yaw, v)");
+    if (params->model != 0 || params->cost_to_go != 0)
+        return sfail(S, MPPI_ERR_ARG, "the server runs model 0 with whole-cost weights");
     if (params->T > S->cfg.max_T || n_ref > S->cfg.max_ref || n_circ > S->cfg.max_circ || n_ref < 2 || n_circ < 0 ||
         (long long)params->K > S->cfg.max_samples || (long long)params->K * params->T > S->cfg.max_rollout_steps)
         return sfail(S, MPPI_ERR_CAPACITY, "request above the server's capacities");

@@ -81,7 +81,7 @@ def default_params(K: int, T: int, dt: float, lam: float = 1.0,
         d_safe_c=0.0, d_safe_0=0.5, collision_only=0,
         n_ego=3, ego_offset=[0.0, 1.35, 2.7], ego_radius=[1.1, 1.1, 1.1],
         ref_mode=0, sg_enable=1, shift=0, noise_bf16=0,
-        seed=0, session=0, model=0,
+        seed=0, session=0, model=0, cost_to_go=0,
         **PAPER_WEIGHTS,
     )
 

@@ -51,7 +51,7 @@ def test_struct_layouts_match_the_header():
     # sizes follow from the field lists of include/mppi.h on an LP64 ABI
     assert ctypes.sizeof(mp.MppiInfo) == 32
     assert ctypes.sizeof(mp.MppiParams) == (4 * 2 + 8 * 2 + 8 * 6 + 8 * 4 + 8 * 6 + 8 * 2 + 8 * 2 + 4 * 2 + 8 * 16
-                                            + 4 * 4 + 8 + 4 * 4)
+                                            + 4 * 4 + 8 + 4 * 5 + 4)
 
 
 def test_default_params_are_the_papers_weights():

@@ -403,3 +403,45 @@ def test_batch_engine_rejects_the_steering_rate_model():
         with pytest.raises(mp.MppiError) as e:
             bp.plan([mp.BatchPlan(prob.params, 0, prob.x0[:4], prob.ref, prob.circles, None)])
         assert e.value.status == -1
+
+
+# ----------------------------------------------------------------------------- cost-to-go form
+
+@pytest.mark.parametrize("scene", ["curved_lane", "close_obstacles", "paper_preset"])
+def test_cost_to_go_update_parity(scene):
+    """Eq. (11) read per step: each step's weights from the cost still to come."""
+    if scene == "curved_lane":
+        prob = sc.closed_loop()
+        prob.params.update(K=2048, T=60)
+    elif scene == "close_obstacles":
+        prob = sc.tiny(K=1500, T=25, n_ref=60, n_obs=3, moving=True)
+        prob.params["d_safe_0"] = 2.0
+    else:
+        prob = sc.paper_preset()
+    prob.params["cost_to_go"] = 1
+    U = np.random.default_rng(7).normal(size=(prob.T, 2)) * [0.3, 0.02]
+    U = np.clip(U, prob.params["u_min"], prob.params["u_max"])
+    outs, _, _, _ = run_gpu(prob, U=U)
+    orc = oracle.plan(prob, U=U)
+    rep = check_iteration(prob, outs[0], orc)
+    print("cost_to_go", scene, rep)
+
+
+def test_cost_to_go_same_update_for_every_lane_split():
+    prob = sc.closed_loop()
+    prob.params.update(K=512, T=39, cost_to_go=1)
+    u = {}
+    for g in (1, 4, 32, -2, -8):
+        outs, _, _, _ = run_gpu(prob, params=dict(prob.params, group=g))
+        u[g] = outs[0][0]
+    for g in u:
+        np.testing.assert_array_equal(u[g], u[1], err_msg=f"group {g}")
+
+
+def test_cost_to_go_reading_changes_the_update():
+    prob = sc.closed_loop()
+    prob.params.update(K=2048, T=60)
+    a, _, _, _ = run_gpu(prob)
+    b, _, _, _ = run_gpu(prob, params=dict(prob.params, cost_to_go=1))
+    np.testing.assert_array_equal(a[0][3], b[0][3])                   # same sample costs
+    assert np.abs(a[0][0] - b[0][0]).max() > 1e-6                     # different update
