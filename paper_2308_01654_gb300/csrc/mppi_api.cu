@@ -596,6 +596,7 @@ int mppi_autotune(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n
         int n_sm = 0;
         CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
         const size_t smem = rollout_smem_bytes(L);
+        const bool ext = c->p.model == 1 || c->p.cost_to_go != 0;
         // lanes per sample: > 0 split the work of each step, < 0 split the steps
         const int groups[] = {1, 2, 4, 8, 16, 32, -2, -4, -8, -16};
         cudaError_t err = cudaSuccess;
@@ -613,13 +614,13 @@ int mppi_autotune(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n
                 long long per = (lanes + (long long)n_sm * m - 1) / ((long long)n_sm * m);
                 int th = (int)(((per + 31) / 32) * 32);
                 if (th < 32 || th > MAX_ROLLOUT_THREADS) continue;
-                if (rollout_max_blocks_per_sm(G, th, c->p.noise_bf16, smem) < m) continue;
+                if (rollout_max_blocks_per_sm(G, th, c->p.noise_bf16, smem, ext) < m) continue;
                 bool dup = false;
                 for (int i = 0; i < nc; ++i) dup |= cand[i] == th;
                 if (!dup) cand[nc++] = th;
             }
             for (int bi = 0; bi < nc && err == cudaSuccess; ++bi) {
-                if (rollout_max_blocks_per_sm(G, cand[bi], c->p.noise_bf16, smem) < 1) continue;
+                if (rollout_max_blocks_per_sm(G, cand[bi], c->p.noise_bf16, smem, ext) < 1) continue;
                 err = launch_rollout(pc, L, c->b, G, cand[bi], c->p.noise_bf16, c->stream);  // warm-up
                 if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
                 for (int r = 0; r < 3 && err == cudaSuccess; ++r)

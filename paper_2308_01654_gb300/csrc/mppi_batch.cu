@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 2) batch_rollout_kernel(B
         }
         const BatchInst& d = a.inst[td.x];
         const int k = td.y + (int)threadIdx.x / G;   // G lanes per sample
-        rollout_sample<G, TIME, BF16, false>(s_pc, s_L, smem, reinterpret_cast<const NT*>(a.z) + d.z_off,
+        rollout_sample<G, TIME, BF16, false, false>(s_pc, s_L, smem, reinterpret_cast<const NT*>(a.z) + d.z_off,
                                        a.table + d.table_off, s_x0, 0.0f, s_moving != 0, s_jb0, k, a.S + d.s_off,
                                        nullptr);
         __syncthreads();

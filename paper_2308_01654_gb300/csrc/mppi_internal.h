@@ -155,6 +155,7 @@ cudaError_t launch_rollout_stats(const PlanConst& pc, const SceneLayout& L, cons
 size_t rollout_smem_bytes(const SceneLayout& L);
 
 // Resident rollout blocks per SM for a launch shape (0 if it cannot launch).
-int rollout_max_blocks_per_sm(int group, int threads, int noise_bf16, size_t smem);
+// ext: the steering-rate model or the cost-to-go form is on (PlanConst model / cost_to_go)
+int rollout_max_blocks_per_sm(int group, int threads, int noise_bf16, size_t smem, bool ext);
 
 }  // namespace mppi

@@ -751,7 +751,9 @@ struct StepIn {
 };
 
 // Eq. (5): explicit Euler from x_t to x_{t+1} under the perturbed controls of step t.
-template <bool BF16>
+// EXT: compiled with the steering-rate model and the cost-to-go form (otherwise both are
+// compiled out: model 0 and whole-cost weights).
+template <bool BF16, bool EXT>
 __device__ __forceinline__ StepIn dyn_step(const PlanConst& pc, const float4 ct, float c0t, float2 zz, float2 tp,
                                            Roll& r, float2* ds) {
     const Perturbed pe = perturb(ct.x, ct.y, zz, pc.sig_a, pc.sig_d, pc.amin, pc.amax, pc.dmin, pc.dmax);
@@ -761,7 +763,7 @@ __device__ __forceinline__ StepIn dyn_step(const PlanConst& pc, const float4 ct,
     // model 0: the steering angle is the control; model 1: it is the state, advanced by the
     // steering rate (the second control) after its tangent is taken (right-hand side at x_t)
     float tn;
-    if (pc.model == 1) {
+    if (EXT && pc.model == 1) {
         float2 d = *ds;
         tn = tanf(d.x);
         kahan_add(d.x, d.y, __fmul_rn(pe.vd, pc.dt));
@@ -866,7 +868,7 @@ __device__ __forceinline__ float state_cost(const PlanConst& pc, const SceneLayo
 // bits).  Lane p evaluates the state cost of its step (the reference search warm-started
 // from its own previous step) and the step costs are added in step order, so S is bit for
 // bit that of G = 1.
-template <int G, bool TIME, bool BF16, bool STATS>
+template <int G, bool TIME, bool BF16, bool STATS, bool EXT>
 __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneLayout& L, const unsigned char* smem,
                                                const typename NoiseT<BF16>::type* __restrict__ z,
                                                const float2* table, float4 x0, float d0, bool moving, int jb0,
@@ -888,7 +890,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
     r.th = x0.z;
     r.v = x0.w;
     r.px_c = r.py_c = r.th_c = r.v_c = 0.0f;
-    if (pc.model == 1) *steer_slot(smem, L) = make_float2(d0, 0.0f);
+    if (EXT && pc.model == 1) *steer_slot(smem, L) = make_float2(d0, 0.0f);
     sincosf(r.th, &r.sth, &r.cth);
     r.tdp = fmaf(tp.x, tp.x, tp.y * tp.y);      // |P_0 - T_P|^2 with P_0 = (0, 0)
     int jb = jb0, jbp = jb0;   // closest segment of the last evaluated step and of the one before
@@ -898,10 +900,10 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
     if constexpr (!TIME) {
         for (int t = 0; t < T; ++t) {
             const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
-            const StepIn s = dyn_step<BF16>(pc, sc.ctl[t], sc.c0[t], zz, tp, r, steer_slot(smem, L));
+            const StepIn s = dyn_step<BF16, EXT>(pc, sc.ctl[t], sc.c0[t], zz, tp, r, steer_slot(smem, L));
             const float qx = state_cost<G, STATS>(pc, L, sc, table, s, t, t, t, has_table, moving, dconst, lane,
                                                   lane_g, mask, jb, jbp, cnt);
-            if (prefix && lane_g == 0 && k < K) prefix[(size_t)t * K + k] = s_hi - s_c;   // cost of steps < t
+            if (EXT && prefix && lane_g == 0 && k < K) prefix[(size_t)t * K + k] = s_hi - s_c;   // cost of steps < t
             kahan_add(s_hi, s_c, qx + s.qu);    // Eq. (6)
             q_last = qx;
         }
@@ -919,7 +921,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
                 for (int j = 0; j < nv; ++j) {
                     const int t = t0 + j;
                     const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
-                    const StepIn q = dyn_step<BF16>(pc, sc.ctl[t], sc.c0[t], zz, tp, r, steer_slot(smem, L));
+                    const StepIn q = dyn_step<BF16, EXT>(pc, sc.ctl[t], sc.c0[t], zz, tp, r, steer_slot(smem, L));
                     if (j == my) e = q;
                 }
             } else {
@@ -928,7 +930,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
             const Perturbed pe = perturb(ct.x, ct.y, NoiseT<BF16>::load(z + (size_t)tm * K + kk), pc.sig_a, pc.sig_d,
                                          pc.amin, pc.amax, pc.dmin, pc.dmax);
             float tn_own;
-            if (pc.model == 1) {
+            if (EXT && pc.model == 1) {
                 // steering angle through the block (every lane); the tangent of the angle at
                 // the start of the own step
                 float2 d = *steer_slot(smem, L);
@@ -1004,12 +1006,12 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
                 const float cj = __shfl_sync(mask, c, j, G);
                 const float qj = __shfl_sync(mask, qx, j, G);
                 if (t0 + j < T) {
-                    if (j == lane_g) pre_own = s_hi - s_c;
+                    if (EXT && j == lane_g) pre_own = s_hi - s_c;
                     kahan_add(s_hi, s_c, cj);   // Eq. (6), in step order
                     q_last = qj;
                 }
             }
-            if (prefix && lane_g < nv && k < K) prefix[(size_t)(t0 + lane_g) * K + k] = pre_own;   // cost of steps < t
+            if (EXT && prefix && lane_g < nv && k < K) prefix[(size_t)(t0 + lane_g) * K + k] = pre_own;   // cost of steps < t
         }
     }
     if (lane_g == 0 && k < K) {
@@ -1125,7 +1127,7 @@ __device__ __forceinline__ double clampd(double x, double lo, double hi) { retur
 // products); the per-warp partials are added in binary64 into du_part[kt][T][2].
 // -----------------------------------------------------------------------------
 
-template <bool BF16>
+template <bool BF16, bool CTG = false>
 __device__ __forceinline__ void wsum_tile(const PlanConst& pc, const float4* ctl,
                                           const typename NoiseT<BF16>::type* __restrict__ z, const float* w, int kt,
                                           int t0, int kt_size, double* du_part, const float* wt = nullptr) {
@@ -1143,7 +1145,7 @@ __device__ __forceinline__ void wsum_tile(const PlanConst& pc, const float4* ctl
     for (int t = t0; t < t1; ++t) {
         const float4 ct = ctl[t];
         float aa = 0.0f, ad = 0.0f;
-        if (wt) {                  // cost-to-go form: weights of this step
+        if (CTG) {                 // cost-to-go form: weights of this step
 #pragma unroll
             for (int j = 0; j < WS_J; ++j) wj[j] = kj[j] < K ? wt[(size_t)t * K + kj[j]] : 0.0f;
         }

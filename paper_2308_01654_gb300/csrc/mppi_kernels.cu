@@ -128,7 +128,7 @@ __global__ void philox_kernel(uint2 key, const uint4* ctr, uint4* out, int n) {
     if (i < n) out[i] = philox4x32_10(ctr[i], key);
 }
 
-template <int G, bool TIME, bool BF16, bool STATS>
+template <int G, bool TIME, bool BF16, bool STATS, bool EXT>
 __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 2) rollout_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
                                                         const typename NoiseT<BF16>::type* __restrict__ z) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 2) rollout_kernel(PlanCon
     if (!__syncthreads_and(stage_to_smem(smem, b.scene, L.bytes, &bar, &b.state->flags))) return;
     build_boxes(smem, L, b.table, pc.has_table != 0);
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) / G;
-    rollout_sample<G, TIME, BF16, STATS>(pc, L, smem, z, b.table, b.state->x0f, b.state->delta0f,
+    rollout_sample<G, TIME, BF16, STATS, EXT>(pc, L, smem, z, b.table, b.state->x0f, b.state->delta0f,
                                          b.state->moving != 0, (int)(b.state->jkey & 0xffffffffu), k, b.S, b.stats,
                                          pc.cost_to_go ? b.ctg_prefix : nullptr);
 }
@@ -238,12 +238,11 @@ __global__ void __launch_bounds__(256) ctg_weights_kernel(int K, double lam, Pla
 // its J samples and its warp (32 x J products), and the per-warp partials are
 // added in binary64.
 // -----------------------------------------------------------------------------
-template <bool BF16>
+template <bool BF16, bool CTG>
 __global__ void __launch_bounds__(256) wsum_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
                                                    const typename NoiseT<BF16>::type* __restrict__ z) {
     const float4* ctl = reinterpret_cast<const float4*>(b.scene + L.off_ctl);
-    wsum_tile<BF16>(pc, ctl, z, b.w, blockIdx.x, blockIdx.y * WS_TT, b.kt_size, b.du_part,
-                    pc.cost_to_go ? b.wt : nullptr);
+    wsum_tile<BF16, CTG>(pc, ctl, z, b.w, blockIdx.x, blockIdx.y * WS_TT, b.kt_size, b.du_part, b.wt);
 }
 
 // -----------------------------------------------------------------------------
@@ -256,13 +255,13 @@ __global__ void __launch_bounds__(1024) finalize_kernel(PlanConst pc, PlanBuffer
 // -----------------------------------------------------------------------------
 // host-side launchers
 // -----------------------------------------------------------------------------
-template <int G, bool TIME, bool BF16, bool STATS = false>
+template <int G, bool TIME, bool BF16, bool STATS, bool EXT>
 static cudaError_t launch_rollout_t(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int threads,
                                     cudaStream_t st) {
     const size_t smem = rollout_smem_bytes(L);
     static int configured_smem = -1;
     if (configured_smem < (int)smem) {
-        cudaError_t e = cudaFuncSetAttribute(rollout_kernel<G, TIME, BF16, STATS>,
+        cudaError_t e = cudaFuncSetAttribute(rollout_kernel<G, TIME, BF16, STATS, EXT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(smem < 48 * 1024 ? 48 * 1024 : smem));
         if (e != cudaSuccess) return e;
@@ -270,73 +269,77 @@ static cudaError_t launch_rollout_t(const PlanConst& pc, const SceneLayout& L, c
     }
     const long long total = (long long)pc.K * G;
     const int blocks = (int)((total + threads - 1) / threads);
-    rollout_kernel<G, TIME, BF16, STATS><<<blocks, threads, smem, st>>>(
+    rollout_kernel<G, TIME, BF16, STATS, EXT><<<blocks, threads, smem, st>>>(
         pc, L, b, reinterpret_cast<const typename NoiseT<BF16>::type*>(b.z));
     return cudaGetLastError();
 }
 
-template <bool BF16>
+// The launch shapes: lanes per sample as the group value (g > 0 split the work of each
+// step, g < 0 split the steps).
+#define MPPI_ROLLOUT_GROUPS(X) X(1, 1, false) X(2, 2, false) X(4, 4, false) X(8, 8, false) X(16, 16, false) \
+    X(32, 32, false) X(-2, 2, true) X(-4, 4, true) X(-8, 8, true) X(-16, 16, true)
+
+template <bool BF16, bool EXT>
 static cudaError_t launch_rollout_b(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int group,
                                     int threads, cudaStream_t st) {
     switch (group) {
-        case 1: return launch_rollout_t<1, false, BF16>(pc, L, b, threads, st);
-        case 2: return launch_rollout_t<2, false, BF16>(pc, L, b, threads, st);
-        case 4: return launch_rollout_t<4, false, BF16>(pc, L, b, threads, st);
-        case 8: return launch_rollout_t<8, false, BF16>(pc, L, b, threads, st);
-        case 16: return launch_rollout_t<16, false, BF16>(pc, L, b, threads, st);
-        case 32: return launch_rollout_t<32, false, BF16>(pc, L, b, threads, st);
-        case -2: return launch_rollout_t<2, true, BF16>(pc, L, b, threads, st);
-        case -4: return launch_rollout_t<4, true, BF16>(pc, L, b, threads, st);
-        case -8: return launch_rollout_t<8, true, BF16>(pc, L, b, threads, st);
-        case -16: return launch_rollout_t<16, true, BF16>(pc, L, b, threads, st);
+#define CASE(gv, g, time) \
+    case gv: return launch_rollout_t<g, time, BF16, false, EXT>(pc, L, b, threads, st);
+        MPPI_ROLLOUT_GROUPS(CASE)
+#undef CASE
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <int G, bool TIME, bool BF16>
+template <int G, bool TIME, bool BF16, bool EXT>
 static int max_blocks_t(int threads, size_t smem) {
     int n = 0;
-    if (cudaFuncSetAttribute(rollout_kernel<G, TIME, BF16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(rollout_kernel<G, TIME, BF16, false, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(smem < 48 * 1024 ? 48 * 1024 : smem)) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_kernel<G, TIME, BF16, false>, threads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_kernel<G, TIME, BF16, false, EXT>, threads, smem) !=
         cudaSuccess)
         return 0;
     return n;
 }
 
-template <bool BF16>
+template <bool BF16, bool EXT>
 static int max_blocks_b(int group, int threads, size_t smem) {
     switch (group) {
-        case 1: return max_blocks_t<1, false, BF16>(threads, smem);
-        case 2: return max_blocks_t<2, false, BF16>(threads, smem);
-        case 4: return max_blocks_t<4, false, BF16>(threads, smem);
-        case 8: return max_blocks_t<8, false, BF16>(threads, smem);
-        case 16: return max_blocks_t<16, false, BF16>(threads, smem);
-        case 32: return max_blocks_t<32, false, BF16>(threads, smem);
-        case -2: return max_blocks_t<2, true, BF16>(threads, smem);
-        case -4: return max_blocks_t<4, true, BF16>(threads, smem);
-        case -8: return max_blocks_t<8, true, BF16>(threads, smem);
-        case -16: return max_blocks_t<16, true, BF16>(threads, smem);
+#define CASE(gv, g, time) \
+    case gv: return max_blocks_t<g, time, BF16, EXT>(threads, smem);
+        MPPI_ROLLOUT_GROUPS(CASE)
+#undef CASE
         default: return 0;
     }
 }
 
-int rollout_max_blocks_per_sm(int group, int threads, int noise_bf16, size_t smem) {
-    return noise_bf16 ? max_blocks_b<true>(group, threads, smem) : max_blocks_b<false>(group, threads, smem);
+// ext: the steering-rate model or the cost-to-go form is on (the other instantiation)
+static bool ext_of(const PlanConst& pc) { return pc.model == 1 || pc.cost_to_go != 0; }
+
+int rollout_max_blocks_per_sm(int group, int threads, int noise_bf16, size_t smem, bool ext) {
+    if (ext)
+        return noise_bf16 ? max_blocks_b<true, true>(group, threads, smem) : max_blocks_b<false, true>(group, threads, smem);
+    return noise_bf16 ? max_blocks_b<true, false>(group, threads, smem) : max_blocks_b<false, false>(group, threads, smem);
 }
 
 cudaError_t launch_rollout_stats(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int noise_bf16,
                                  cudaStream_t st) {
-    return noise_bf16 ? launch_rollout_t<1, false, true, true>(pc, L, b, 128, st)
-                      : launch_rollout_t<1, false, false, true>(pc, L, b, 128, st);
+    if (ext_of(pc))
+        return noise_bf16 ? launch_rollout_t<1, false, true, true, true>(pc, L, b, 128, st)
+                          : launch_rollout_t<1, false, false, true, true>(pc, L, b, 128, st);
+    return noise_bf16 ? launch_rollout_t<1, false, true, true, false>(pc, L, b, 128, st)
+                      : launch_rollout_t<1, false, false, true, false>(pc, L, b, 128, st);
 }
 
 cudaError_t launch_rollout(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int group,
                            int threads, int noise_bf16, cudaStream_t st) {
     if (threads < 32 || threads > MAX_ROLLOUT_THREADS || threads % 32 != 0) return cudaErrorInvalidValue;
-    return noise_bf16 ? launch_rollout_b<true>(pc, L, b, group, threads, st)
-                      : launch_rollout_b<false>(pc, L, b, group, threads, st);
+    if (ext_of(pc))
+        return noise_bf16 ? launch_rollout_b<true, true>(pc, L, b, group, threads, st)
+                          : launch_rollout_b<false, true>(pc, L, b, group, threads, st);
+    return noise_bf16 ? launch_rollout_b<true, false>(pc, L, b, group, threads, st)
+                      : launch_rollout_b<false, false>(pc, L, b, group, threads, st);
 }
 
 cudaError_t launch_prep_noise(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
@@ -398,10 +401,16 @@ cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const Pl
     if ((e = mark()) != cudaSuccess) return e;
     {
         dim3 grid(b.n_kt, b.n_tt);
-        if (noise_bf16)
-            wsum_kernel<true><<<grid, 256, 0, st>>>(pc, L, b, reinterpret_cast<const __nv_bfloat162*>(b.z));
-        else
-            wsum_kernel<false><<<grid, 256, 0, st>>>(pc, L, b, reinterpret_cast<const float2*>(b.z));
+        const bool ctg = pc.cost_to_go != 0;
+        if (noise_bf16) {
+            const __nv_bfloat162* zb = reinterpret_cast<const __nv_bfloat162*>(b.z);
+            if (ctg) wsum_kernel<true, true><<<grid, 256, 0, st>>>(pc, L, b, zb);
+            else wsum_kernel<true, false><<<grid, 256, 0, st>>>(pc, L, b, zb);
+        } else {
+            const float2* zf = reinterpret_cast<const float2*>(b.z);
+            if (ctg) wsum_kernel<false, true><<<grid, 256, 0, st>>>(pc, L, b, zf);
+            else wsum_kernel<false, false><<<grid, 256, 0, st>>>(pc, L, b, zf);
+        }
         if ((e = mark()) != cudaSuccess) return e;
     }
     finalize_kernel<<<1, ((pc.T + 31) / 32) * 32, 0, st>>>(pc, b, in);
