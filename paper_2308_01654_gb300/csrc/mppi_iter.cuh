@@ -236,12 +236,9 @@ __device__ __forceinline__ float group_min(float v, unsigned mask) {
     return v;
 }
 
-// Closest point of the polyline (ties -> lowest segment) with a two-level box
-// hierarchy; a box is skipped only when its lower bound exceeds the best distance so
-// far (with a relative slack far above binary32 rounding), so no segment that can be
-// the closest is missed.  The scan keeps the two best distinct segments; when their
-// binary32 distances are within 4e-6 relative, the pair is re-ordered in binary64.
-// Work done by the pruned searches of one lane (only counted in the STATS instantiation).
+// Work done by the pruned searches of one lane (only counted in the STATS instantiation):
+// range boxes (prefix, suffix, level-2), chunk boxes, segments, binary64 refinements,
+// broad-phase circle tests, candidate circles, square roots taken for d_obj.
 struct Counters {
     unsigned l2, l1, seg, refine, circ, cand, pair;
 };
