@@ -587,6 +587,11 @@ __device__ __forceinline__ float2 circle_centre(const float4* circ, const float2
     return make_float2(fmaf(vv.x, st, c.x), fmaf(vv.y, st, c.y));
 }
 
+// Distance from a squared distance as d2 * rsqrt(d2) (a few ulp, against the many more
+// instructions of the correctly rounded square root); 0 at 0.  The obstacle term uses it
+// only inside the safety band, where c_safe is continuous in it.
+__device__ __forceinline__ float dist_of(float d2) { return d2 > 0.0f ? d2 * rsqrtf(d2) : 0.0f; }
+
 // Warp min / max of a float with one redux.sync on an order-preserving integer image
 // (non-negative floats keep their bits, negative ones have their magnitude bits flipped).
 __device__ __forceinline__ int f32_ord(float f) {
@@ -669,15 +674,23 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const unsigne
                 // equal ego radii: the closest ego circle gives the pair minimum (sqrt and the
                 // subtraction are monotone), one square root per circle
                 float d2m = INFINITY;
+                if (pc.n_ego == 3) {        // the paper's ego model: three circles, no bound checks
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    if (e >= pc.n_ego) break;
-                    const float dx = fmaf(pc.ego_off[e], cnth, nx) - cc.x, dy = fmaf(pc.ego_off[e], snth, ny) - cc.y;
-                    d2m = fminf(d2m, fmaf(dx, dx, dy * dy));
+                    for (int e = 0; e < 3; ++e) {
+                        const float dx = fmaf(pc.ego_off[e], cnth, nx) - cc.x, dy = fmaf(pc.ego_off[e], snth, ny) - cc.y;
+                        d2m = fminf(d2m, fmaf(dx, dx, dy * dy));
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        if (e >= pc.n_ego) break;
+                        const float dx = fmaf(pc.ego_off[e], cnth, nx) - cc.x, dy = fmaf(pc.ego_off[e], snth, ny) - cc.y;
+                        d2m = fminf(d2m, fmaf(dx, dx, dy * dy));
+                    }
                 }
                 if (d2m <= c.w) {
                     if (STATS) cnt.pair++;
-                    dobj = fminf(dobj, sqrtf(d2m) - (c.z + pc.ego_rad[0]));
+                    dobj = fminf(dobj, dist_of(d2m) - (c.z + pc.ego_rad[0]));
                 }
             } else {
 #pragma unroll
@@ -689,7 +702,7 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const unsigne
                     const float d2 = fmaf(dx, dx, dy * dy);
                     if (lim > 0.0f && d2 <= lim * lim) {
                         if (STATS) cnt.pair++;
-                        dobj = fminf(dobj, sqrtf(d2) - R);
+                        dobj = fminf(dobj, dist_of(d2) - R);
                     }
                 }
             }
