@@ -309,8 +309,10 @@ def _kernel_times(self) -> Dict[str, float]:
     return dict(zip(KERNELS, [float(v) for v in ms]))
 
 
-def _set_profiling(self, on: bool = True):
-    _check(lib().mppi_set_profiling(self._h, 1 if on else 0), self._h)
+def _set_profiling(self, on=True):
+    """True / 1: events around every kernel; 2: around the rollout only (the others stay chained)."""
+    mode = 2 if on == 2 else (1 if on else 0)
+    _check(lib().mppi_set_profiling(self._h, mode), self._h)
 
 
 Planner.kernel_times = _kernel_times

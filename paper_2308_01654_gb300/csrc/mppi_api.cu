@@ -164,6 +164,8 @@ static PlanConst make_const(const mppi_params& p) {
     c.lam = p.lam;
     c.dt_d = p.dt;
     c.wheelbase_d = p.wheelbase;
+    c.inv_dt_d = 1.0 / p.dt;
+    c.dt_over_wb_d = p.dt / p.wheelbase;
     c.amin_d = p.u_min[0];
     c.amax_d = p.u_max[0];
     c.dmin_d = p.u_min[1];
@@ -371,7 +373,7 @@ static int enqueue(mppi_ctx* c, const PlanInputs& in, int has_table) {
     PlanConst pc = c->pc;
     pc.has_table = has_table;
     CK(launch_iteration(pc, L, c->b, in, c->group, c->threads, c->p.noise_bf16, c->stream,
-                        c->profiling ? c->ev : nullptr),
+                        c->profiling ? c->ev : nullptr, c->profiling),
        "kernel launch");
     return MPPI_OK;
 }
@@ -752,15 +754,22 @@ int mppi_philox(uint64_t seed, const uint32_t* ctr, int32_t n, uint32_t* out) {
 int mppi_set_profiling(mppi_ctx* c, int32_t on) {
     if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
+    if (on < 0 || on > 2) return fail(c, MPPI_ERR_ARG, "profiling mode must be 0, 1 or 2");
     if (on && !c->ev[0])
         for (auto& e : c->ev) CK(cudaEventCreate(&e), "cudaEventCreate");
-    c->profiling = on ? 1 : 0;
+    c->profiling = on;
     return MPPI_OK;
 }
 
 int mppi_kernel_times(mppi_ctx* c, float* ms, int32_t n) {
     if (!c || !ms || n < N_KERNELS) return fail(c, MPPI_ERR_ARG, "ms must hold MPPI_N_KERNELS floats");
     if (!c->profiling) return fail(c, MPPI_ERR_ARG, "profiling is off");
+    if (c->profiling == 2) {
+        CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+        for (int i = 0; i < N_KERNELS; ++i) ms[i] = NAN;
+        CK(cudaEventElapsedTime(&ms[2], c->ev[2], c->ev[3]), "cudaEventElapsedTime");
+        return MPPI_OK;
+    }
     CK(cudaEventSynchronize(c->ev[N_KERNELS]), "cudaEventSynchronize");
     for (int i = 0; i < N_KERNELS; ++i) CK(cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]), "cudaEventElapsedTime");
     return MPPI_OK;

@@ -26,6 +26,19 @@ constexpr int FLAG_NONFINITE_INPUT = 1;
 constexpr int FLAG_TIMEOUT = 2;
 
 // -----------------------------------------------------------------------------
+// Programmatic dependent launch.  The kernels of an iteration after the first are launched
+// with programmatic stream serialisation: a kernel may be scheduled while its predecessor
+// drains, and waits here (griddepcontrol.wait: until the predecessor grid has completed and
+// its memory operations are visible) before it reads anything.  Every chained kernel waits
+// before its first dependent access, so grids still complete strictly in stream order.
+// pdl_trigger lets the next kernel be scheduled before this one ends; single-wave kernels
+// call it, kernels with many waves leave it to their exit so the next kernel's blocks do not
+// take SM space from their later waves.  Without the launch attribute both return at once.
+// -----------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// -----------------------------------------------------------------------------
 // Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11):
 // ten rounds of two 32x32->64 multiplications whose halves are XORed with the
 // other two counter words and the round key; the key advances by the Weyl

@@ -74,6 +74,8 @@ struct PlanConst {
     // slows down when they move)
     int model;               // 0: control (a, delta); 1: state carries delta, control (a, omega)
     int cost_to_go;          // 1: per-step weights from the cost still to come
+    double inv_dt_d;         // 1 / dt
+    double dt_over_wb_d;     // dt / wheelbase
 };
 
 SceneLayout make_layout(int T, int n_ref, int n_circ);
@@ -129,11 +131,12 @@ struct PlanInputs {
 };
 
 // Launch the whole iteration (prep, noise, rollout, reductions, update) on a stream.
-// ev: optional array of N_KERNELS + 1 events recorded around the kernels (per-kernel timing).
+// ev: optional array of N_KERNELS + 1 events; ev_mode 1 records them around every kernel
+// (per-kernel timing), 2 only ev[2] and ev[3] around the rollout (the rest stays chained).
 constexpr int N_KERNELS = 7;   // prep, noise, rollout, argmin, weights, wsum, finalize
 cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
                              const PlanInputs& in, int group, int threads, int noise_bf16, cudaStream_t st,
-                             cudaEvent_t* ev = nullptr);
+                             cudaEvent_t* ev = nullptr, int ev_mode = 1);
 
 // prep + noise only (no change to the warm start or the iteration counter) and the
 // reset of the fields prep accumulates into; used by the autotuner.

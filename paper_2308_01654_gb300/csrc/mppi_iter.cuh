@@ -1104,17 +1104,22 @@ static __device__ double block_sum_d(double v) {
     return v;
 }
 
-static __device__ double block_scan_incl(double v, double* sh) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+// Block-wide inclusive scans in binary64 over the first nwa warps of the block; the other
+// warps add nothing and only take part in the barriers.  The active warps add in the same
+// order whatever the block size (warp scan, then the scan of the warp totals).
+static __device__ double block_scan_incl(double v, double* sh, int nwa) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w < nwa) {
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double n = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += n;
+        for (int o = 1; o < 32; o <<= 1) {
+            const double n = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += n;
+        }
+        if (lane == 31) sh[w] = v;
     }
-    if (lane == 31) sh[w] = v;
     __syncthreads();
     if (w == 0) {
-        double s = lane < nw ? sh[lane] : 0.0;
+        double s = lane < nwa ? sh[lane] : 0.0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const double n = __shfl_up_sync(0xffffffffu, s, o);
@@ -1123,7 +1128,45 @@ static __device__ double block_scan_incl(double v, double* sh) {
         sh[lane] = s;
     }
     __syncthreads();
-    if (w > 0) v += sh[w - 1];
+    if (w > 0 && w < nwa) v += sh[w - 1];
+    __syncthreads();
+    return v;
+}
+
+// Two independent scans in one pass (one set of barriers).
+static __device__ double2 block_scan2_incl(double2 v, double2* sh, int nwa) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w < nwa) {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double nx = __shfl_up_sync(0xffffffffu, v.x, o);
+            const double ny = __shfl_up_sync(0xffffffffu, v.y, o);
+            if (lane >= o) {
+                v.x += nx;
+                v.y += ny;
+            }
+        }
+        if (lane == 31) sh[w] = v;
+    }
+    __syncthreads();
+    if (w == 0) {
+        double2 s = lane < nwa ? sh[lane] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double nx = __shfl_up_sync(0xffffffffu, s.x, o);
+            const double ny = __shfl_up_sync(0xffffffffu, s.y, o);
+            if (lane >= o) {
+                s.x += nx;
+                s.y += ny;
+            }
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    if (w > 0 && w < nwa) {
+        v.x += sh[w - 1].x;
+        v.y += sh[w - 1].y;
+    }
     __syncthreads();
     return v;
 }
@@ -1191,35 +1234,69 @@ __device__ __forceinline__ void wsum_tile(const PlanConst& pc, const float4* ctl
 
 // -----------------------------------------------------------------------------
 // finalize: u <- clamp(u + du), u* = clamp(SG(u)), x* = F-rollout of u*, warm start.
-// One block, one thread per step (T <= 1024).  x* is a chain of prefix sums:
-// v_t from sum a dt, yaw from sum v tan(delta)/L dt, x and y from sum v (cos, sin) dt.
-// The sums run in binary64; tan, sin and cos are taken in binary32 (relative error a
-// few 1e-8 per term, far below the rollouts' own rounding), which keeps this one-block
-// kernel off the slow binary64 transcendental path.
+// One block with blockDim.x >= T (every launch gives T rounded up to a warp, or 1024), so a
+// thread holds at most two of the 2T control entries and at most one step.  x* is a chain
+// of prefix sums: v_t from sum a dt, yaw from sum v tan(delta)/L dt, x and y from sum
+// v (cos, sin) dt; with the speed cap v_{t+1} is a clamp of v_t and one thread steps the
+// speeds through, the other sums stay scans.  The sums run in binary64; tan, sin and cos
+// are taken in binary32 (relative error a few 1e-8 per term, far below the rollouts' own
+// rounding).  binary64 arithmetic is scarce on this part (a few lanes per SM and clock),
+// so divisions are replaced by products with reciprocals formed once (1 / eta, 1 / 35,
+// 1 / dt, dt / L): each such product is within an ulp of the quotient.
 // -----------------------------------------------------------------------------
 __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBuffers& b, const PlanInputs& in) {
     __shared__ double s_un[2 * 1024];
     __shared__ double s_us[2 * 1024];
+    __shared__ double s_v[1024 + 1];
+    __shared__ double2 s_scan2[32];
     __shared__ double s_scan[32];
-    __shared__ double s_eta;
+    __shared__ double s_eta, s_inv_eta;
     __shared__ int s_status;
     DevState* st = b.state;
     const int T = pc.T;
-    const int t = threadIdx.x;
-    if (t == 0) {
-        const int flags = st->flags;
-        int status = 0;
-        if (flags & FLAG_NONFINITE_INPUT) status = -1;
-        else if (flags & FLAG_TIMEOUT) status = -5;
-        else if (st->n_finite == 0) status = -4;
-        s_status = status;
+    const int t = threadIdx.x, bd = blockDim.x;
+    const int nwa = (T + 31) >> 5;                 // warps that hold steps
+    const bool ctg = pc.cost_to_go != 0;
+
+    // this thread's control entries i0 = t and i1 = t + bd: their nominal values and the sums
+    // over the k-tiles of the weighted noise (k-tile order), all loads issued up front
+    const int i0 = t, i1 = t + bd;
+    const bool h0 = i0 < 2 * T, h1 = i1 < 2 * T;
+    const double U0 = h0 ? b.U[i0] : 0.0, U1 = h1 ? b.U[i1] : 0.0;
+    double n0 = 0.0, n1 = 0.0;
+    {
+        const double* dp = b.du_part;
+        const size_t stride = 2 * (size_t)T;
+        int kt = 0;
+        for (; kt + 16 <= b.n_kt; kt += 16) {
+            double a0[16], a1[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                a0[j] = h0 ? dp[(size_t)(kt + j) * stride + i0] : 0.0;
+                a1[j] = h1 ? dp[(size_t)(kt + j) * stride + i1] : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                n0 += a0[j];
+                n1 += a1[j];
+            }
+        }
+        for (; kt < b.n_kt; ++kt) {
+            if (h0) n0 += dp[(size_t)kt * stride + i0];
+            if (h1) n1 += dp[(size_t)kt * stride + i1];
+        }
     }
     {
         // eta: the per-block partial sums of the weights kernel, reduced by the whole block
         double e = 0.0;
-        for (int i = t; i < b.n_wblk; i += blockDim.x) e += b.eta_part[i];
+        for (int i = t; i < b.n_wblk; i += bd) e += b.eta_part[i];
         e = block_sum_d(e);
-        if (t == 0) s_eta = pc.cost_to_go ? b.eta_t[0] : e;     // cost-to-go form: reported eta of step 0
+        if (t == 0) {
+            const int flags = st->flags, nf = st->n_finite;
+            s_status = (flags & FLAG_NONFINITE_INPUT) ? -1 : (flags & FLAG_TIMEOUT) ? -5 : nf == 0 ? -4 : 0;
+            s_eta = ctg ? b.eta_t[0] : e;     // cost-to-go form: reported eta of step 0
+            s_inv_eta = 1.0 / e;
+        }
     }
     __syncthreads();
     if (s_status != 0) {
@@ -1231,18 +1308,17 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
         }
         return;
     }
-    const double eta = s_eta;
-    for (int i = t; i < 2 * T; i += blockDim.x) {
-        double num = 0.0;
-#pragma unroll 8
-        for (int kt = 0; kt < b.n_kt; ++kt) num += b.du_part[(size_t)kt * 2 * T + i];
-        const bool ch = i & 1;
-        const double et = pc.cost_to_go ? b.eta_t[i >> 1] : eta;   // cost-to-go form: eta of the step
-        s_un[i] = clampd(b.U[i] + num / et, ch ? pc.dmin_d : pc.amin_d, ch ? pc.dmax_d : pc.amax_d);
-    }
+    const double eta = s_eta, inv_eta = s_inv_eta;
+    const int ch = t & 1;                          // bd is a multiple of 32: i0 and i1 share the channel
+    const double lo = ch ? pc.dmin_d : pc.amin_d, hi = ch ? pc.dmax_d : pc.amax_d;
+    if (h0) s_un[i0] = clampd(U0 + (ctg ? n0 / b.eta_t[i0 >> 1] : n0 * inv_eta), lo, hi);
+    if (h1) s_un[i1] = clampd(U1 + (ctg ? n1 / b.eta_t[i1 >> 1] : n1 * inv_eta), lo, hi);
     __syncthreads();
-    for (int i = t; i < 2 * T; i += blockDim.x) {
-        const int tt = i >> 1, ch = i & 1;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int i = r ? i1 : i0;
+        if (!(r ? h1 : h0)) continue;
+        const int tt = i >> 1;
         double val;
         if (pc.sg_enable) {
             const double cf[5] = {-3.0, 12.0, 17.0, 12.0, -3.0};
@@ -1252,7 +1328,7 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
                 const int s = min(max(tt + j, 0), T - 1);
                 acc += cf[j + 2] * s_un[2 * s + ch];
             }
-            val = clampd(acc / 35.0, ch ? pc.dmin_d : pc.amin_d, ch ? pc.dmax_d : pc.amax_d);
+            val = clampd(acc * (1.0 / 35.0), lo, hi);
         } else {
             val = s_un[i];
         }
@@ -1261,8 +1337,7 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
     }
     __syncthreads();
 
-    // x*: prefix sums in binary64 (sequential when the speed cap makes v nonlinear).  Model 1
-    // carries the steering angle as a fifth state: delta_t = delta_0 + sum of omega dt.
+    // x*.  Model 1 carries the steering angle as a fifth state: delta_t = delta_0 + sum of omega dt.
     const bool m1 = pc.model == 1;
     const int nx = m1 ? 5 : 4;
     const double x0 = in.x0[0], y0 = in.x0[1], th0 = in.x0[2], v0 = in.x0[3], d0 = m1 ? in.x0[4] : 0.0;
@@ -1271,59 +1346,54 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
         if (m1) in.x_out[4] = d0;
     }
     const double dt = pc.dt_d;
+    const bool on = t < T;
+    const double a = on ? s_us[2 * t] : 0.0, dl = on ? s_us[2 * t + 1] : 0.0;
+    double2 p1 = make_double2(0.0, 0.0);           // (v_{t+1} - v0 without the cap, delta_{t+1} - delta0)
+    if (!pc.vcap || m1)
+        p1 = block_scan2_incl(make_double2(on && !pc.vcap ? a * dt : 0.0, on && m1 ? dl * dt : 0.0), s_scan2, nwa);
+    double vt, vn;                                  // v_t and v_{t+1}
     if (pc.vcap) {
         if (t == 0) {
-            double x = x0, y = y0, th = th0, v = v0, d = d0;
+            double v = v0;
             for (int s = 0; s < T; ++s) {
-                double a = s_us[2 * s];
-                const double lim = (pc.v_max_d - v) / dt;
-                if (a > lim) a = lim;
-                if (a < pc.amin_d) a = pc.amin_d;
-                float sn, cs;
-                sincosf((float)th, &sn, &cs);
-                const double steer = m1 ? d : s_us[2 * s + 1];
-                const double nx_ = x + v * (double)cs * dt, ny = y + v * (double)sn * dt;
-                const double nth = th + v * (double)tanf((float)steer) / pc.wheelbase_d * dt;
-                const double nv = v + a * dt;
-                const double nd = m1 ? d + s_us[2 * s + 1] * dt : 0.0;
-                x = nx_; y = ny; th = nth; v = nv; d = nd;
-                double* o = in.x_out + (size_t)nx * (s + 1);
-                o[0] = x; o[1] = y; o[2] = th; o[3] = v;
-                if (m1) o[4] = d;
+                double as = s_us[2 * s];
+                const double lim = (pc.v_max_d - v) * pc.inv_dt_d;
+                if (as > lim) as = lim;
+                if (as < pc.amin_d) as = pc.amin_d;
+                s_v[s] = v;
+                v = v + as * dt;
             }
+            s_v[T] = v;
         }
+        __syncthreads();
+        vt = on ? s_v[t] : 0.0;
+        vn = on ? s_v[t + 1] : 0.0;
     } else {
-        const bool on = t < T;
-        const double a = on ? s_us[2 * t] : 0.0, dl = on ? s_us[2 * t + 1] : 0.0;
-        const double pv = block_scan_incl(on ? a * dt : 0.0, s_scan);          // v_{t+1} - v0
-        const double vt = v0 + (pv - (on ? a * dt : 0.0));                      // v_t
-        double steer = dl, pd = 0.0;
-        if (m1) {
-            pd = block_scan_incl(on ? dl * dt : 0.0, s_scan);                    // delta_{t+1} - delta0
-            steer = d0 + (pd - (on ? dl * dt : 0.0));                            // delta_t
-        }
-        const double dth = on ? vt * (double)tanf((float)steer) / pc.wheelbase_d * dt : 0.0;
-        const double pth = block_scan_incl(dth, s_scan);                         // yaw_{t+1} - yaw0
-        const double tht = th0 + (pth - dth);                                    // yaw_t
-        float sn = 0.0f, cs = 0.0f;
-        if (on) sincosf((float)tht, &sn, &cs);
-        const double dx = on ? vt * (double)cs * dt : 0.0, dy = on ? vt * (double)sn * dt : 0.0;
-        const double px = block_scan_incl(dx, s_scan);
-        const double py = block_scan_incl(dy, s_scan);
-        if (on) {
-            double* o = in.x_out + (size_t)nx * (t + 1);
-            o[0] = x0 + px;
-            o[1] = y0 + py;
-            o[2] = th0 + pth;
-            o[3] = v0 + pv;
-            if (m1) o[4] = d0 + pd;
-        }
+        vt = v0 + (p1.x - (on ? a * dt : 0.0));
+        vn = v0 + p1.x;
+    }
+    double steer = dl;
+    if (m1) steer = d0 + (p1.y - (on ? dl * dt : 0.0));                     // delta_t
+    const double dth = on ? vt * (double)tanf((float)steer) * pc.dt_over_wb_d : 0.0;
+    const double pth = block_scan_incl(dth, s_scan, nwa);                    // yaw_{t+1} - yaw0
+    const double tht = th0 + (pth - dth);                                    // yaw_t
+    float sn = 0.0f, cs = 0.0f;
+    if (on) sincosf((float)tht, &sn, &cs);
+    const double2 pxy = block_scan2_incl(make_double2(on ? vt * (double)cs * dt : 0.0, on ? vt * (double)sn * dt : 0.0),
+                                         s_scan2, nwa);
+    if (on) {
+        double* o = in.x_out + (size_t)nx * (t + 1);
+        o[0] = x0 + pxy.x;
+        o[1] = y0 + pxy.y;
+        o[2] = th0 + pth;
+        o[3] = vn;
+        if (m1) o[4] = d0 + p1.y;
     }
     // warm start for the next iteration (Algorithm 1, last loop)
-    for (int i = t; i < 2 * T; i += blockDim.x) {
-        const int tt = i >> 1, ch = i & 1;
+    for (int i = t; i < 2 * T; i += bd) {
+        const int tt = i >> 1, c = i & 1;
         const int src = pc.shift ? min(tt + 1, T - 1) : tt;
-        b.U[i] = s_us[2 * src + ch];
+        b.U[i] = s_us[2 * src + c];
     }
     if (t == 0) {
         st->status = 0;

@@ -47,12 +47,31 @@ size_t rollout_smem_bytes(const SceneLayout& L) {
     return (size_t)L.bytes + block_extra_bytes(L) + steer_slots_bytes();
 }
 
+// A launch chained to the previous kernel on the stream (programmatic stream serialisation,
+// see pdl_wait): its blocks may be scheduled while the predecessor drains.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                  Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // -----------------------------------------------------------------------------
 // prep: one pass over the inputs.  Positions are shifted into a frame centred on
 // (x0, y0) in binary64 before rounding, so binary32 keeps its resolution where
 // the rollouts happen.
 // -----------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) prep_kernel(PlanConst pc, SceneLayout L, PlanInputs in, PlanBuffers b) {
+    pdl_trigger();
     prep_scene(pc, L, in, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
@@ -66,6 +85,7 @@ template <bool BF16>
 __global__ void __launch_bounds__(256) noise_kernel(PlanConst pc, const DevState* st,
                                                     typename NoiseT<BF16>::type* z, unsigned* fix_count,
                                                     uint2* fix_list) {
+    pdl_wait();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (k >= pc.K) return;
@@ -99,6 +119,8 @@ __global__ void __launch_bounds__(256) noise_kernel(PlanConst pc, const DevState
 // over every SM's binary64 pipe.
 __global__ void __launch_bounds__(32) noise_fix_kernel(PlanConst pc, const DevState* st, __nv_bfloat162* z,
                                                        const unsigned* fix_count, const uint2* fix_list) {
+    pdl_wait();
+    pdl_trigger();
     const unsigned n = min(*fix_count, NOISE_FIX_CAP);
     const uint32_t it = (uint32_t)st->iter;
     const size_t K = (size_t)pc.K;
@@ -115,12 +137,14 @@ static cudaError_t launch_noise(const PlanConst& pc, const PlanBuffers& b, int n
     dim3 grid((pc.K + 255) / 256, (pc.T + 1) / 2);
     if (noise_bf16) {
         __nv_bfloat162* z = reinterpret_cast<__nv_bfloat162*>(b.z);
-        noise_kernel<true><<<grid, 256, 0, st>>>(pc, b.state, z, b.fix_count, b.fix_list);
-        noise_fix_kernel<<<4 * 152, 32, 0, st>>>(pc, b.state, z, b.fix_count, b.fix_list);
-    } else {
-        noise_kernel<false><<<grid, 256, 0, st>>>(pc, b.state, reinterpret_cast<float2*>(b.z), nullptr, nullptr);
+        cudaError_t e = launch_chained(noise_kernel<true>, grid, dim3(256), 0, st, pc, (const DevState*)b.state, z,
+                                       b.fix_count, b.fix_list);
+        if (e != cudaSuccess) return e;
+        return launch_chained(noise_fix_kernel, dim3(4 * 152), dim3(32), 0, st, pc, (const DevState*)b.state, z,
+                              (const unsigned*)b.fix_count, (const uint2*)b.fix_list);
     }
-    return cudaGetLastError();
+    return launch_chained(noise_kernel<false>, grid, dim3(256), 0, st, pc, (const DevState*)b.state,
+                          reinterpret_cast<float2*>(b.z), (unsigned*)nullptr, (uint2*)nullptr);
 }
 
 __global__ void philox_kernel(uint2 key, const uint4* ctr, uint4* out, int n) {
@@ -133,18 +157,22 @@ __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 2) rollout_kernel(PlanCon
                                                         const typename NoiseT<BF16>::type* __restrict__ z) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long bar;
+    pdl_wait();
     if (!__syncthreads_and(stage_to_smem(smem, b.scene, L.bytes, &bar, &b.state->flags))) return;
     build_boxes(smem, L, b.table, pc.has_table != 0);
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     rollout_sample<G, TIME, BF16, STATS, EXT>(pc, L, smem, z, b.table, b.state->x0f, b.state->delta0f,
                                          b.state->moving != 0, (int)(b.state->jkey & 0xffffffffu), k, b.S, b.stats,
                                          pc.cost_to_go ? b.ctg_prefix : nullptr);
+    pdl_trigger();   // after the block's samples: the rollout may run in several waves
 }
 
 // -----------------------------------------------------------------------------
 // argmin over S with ties to the lowest index; non-finite costs are skipped.
 // -----------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) argmin_kernel(int K, PlanBuffers b) {
+    pdl_wait();
+    pdl_trigger();
     MinRec r{INFINITY, 0x7fffffff, 0};
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
         const double s = b.S[k];
@@ -187,6 +215,8 @@ __global__ void __launch_bounds__(256) argmin_kernel(int K, PlanBuffers b) {
 // softmin weights in binary64 (Eq. (11)); eta partial sums per block.
 // -----------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) weights_kernel(int K, double lam, PlanBuffers b) {
+    pdl_wait();
+    pdl_trigger();
     const double smin = b.state->s_min;
     double acc = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
@@ -206,6 +236,8 @@ __global__ void __launch_bounds__(256) weights_kernel(int K, double lam, PlanBuf
 // binary64 exponent) and their binary64 sum, the step's normaliser.
 // -----------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) ctg_weights_kernel(int K, double lam, PlanBuffers b) {
+    pdl_wait();
+    pdl_trigger();
     const int t = blockIdx.x;
     const float* P = b.ctg_prefix + (size_t)t * K;
     MinRec r{INFINITY, 0x7fffffff, 0};
@@ -241,6 +273,8 @@ __global__ void __launch_bounds__(256) ctg_weights_kernel(int K, double lam, Pla
 template <bool BF16, bool CTG>
 __global__ void __launch_bounds__(256) wsum_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
                                                    const typename NoiseT<BF16>::type* __restrict__ z) {
+    pdl_wait();
+    pdl_trigger();
     const float4* ctl = reinterpret_cast<const float4*>(b.scene + L.off_ctl);
     wsum_tile<BF16, CTG>(pc, ctl, z, b.w, blockIdx.x, blockIdx.y * WS_TT, b.kt_size, b.du_part, b.wt);
 }
@@ -249,6 +283,7 @@ __global__ void __launch_bounds__(256) wsum_kernel(PlanConst pc, SceneLayout L, 
 // finalize (see finalize_block)
 // -----------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) finalize_kernel(PlanConst pc, PlanBuffers b, PlanInputs in) {
+    pdl_wait();
     finalize_block(pc, b, in);
 }
 
@@ -269,9 +304,8 @@ static cudaError_t launch_rollout_t(const PlanConst& pc, const SceneLayout& L, c
     }
     const long long total = (long long)pc.K * G;
     const int blocks = (int)((total + threads - 1) / threads);
-    rollout_kernel<G, TIME, BF16, STATS, EXT><<<blocks, threads, smem, st>>>(
-        pc, L, b, reinterpret_cast<const typename NoiseT<BF16>::type*>(b.z));
-    return cudaGetLastError();
+    return launch_chained(rollout_kernel<G, TIME, BF16, STATS, EXT>, dim3(blocks), dim3(threads), smem, st, pc, L, b,
+                          reinterpret_cast<const typename NoiseT<BF16>::type*>(b.z));
 }
 
 // The launch shapes: lanes per sample as the group value (g > 0 split the work of each
@@ -369,16 +403,20 @@ cudaError_t launch_reset_state(DevState* st, cudaStream_t s) {
 
 cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
                              const PlanInputs& in, int group, int threads, int noise_bf16, cudaStream_t st,
-                             cudaEvent_t* ev) {
+                             cudaEvent_t* ev, int ev_mode) {
+    // ev_mode 1: an event before the first kernel and after each (every boundary timed, none
+    // chained); 2: only the two around the rollout (ev[2], ev[3]), the other kernels stay chained
     cudaError_t e;
     int stage = 0;
     auto mark = [&]() -> cudaError_t {
-        if (!ev) return cudaGetLastError();
         cudaError_t r = cudaGetLastError();
-        if (r != cudaSuccess) return r;
-        return cudaEventRecord(ev[stage++], st);
+        if (r != cudaSuccess || !ev) return r;
+        const int s = stage++;
+        if (ev_mode == 2 && s != 2 && s != 3) return cudaSuccess;
+        return cudaEventRecord(ev[s], st);
     };
-    if (ev && (e = cudaEventRecord(ev[stage++], st)) != cudaSuccess) return e;
+    if (ev && ev_mode != 2 && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
+    ++stage;
     {
         int items = L.n_ref;
         items = max(items, L.T);
@@ -392,28 +430,31 @@ cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const Pl
     if ((e = mark()) != cudaSuccess) return e;
     if ((e = launch_rollout(pc, L, b, group, threads, noise_bf16, st)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
-    argmin_kernel<<<b.n_mblk, 256, 0, st>>>(pc.K, b);
+    if ((e = launch_chained(argmin_kernel, dim3(b.n_mblk), dim3(256), 0, st, pc.K, b)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
     if (pc.cost_to_go)
-        ctg_weights_kernel<<<pc.T, 256, 0, st>>>(pc.K, pc.lam, b);
+        e = launch_chained(ctg_weights_kernel, dim3(pc.T), dim3(256), 0, st, pc.K, pc.lam, b);
     else
-        weights_kernel<<<b.n_wblk, 256, 0, st>>>(pc.K, pc.lam, b);
+        e = launch_chained(weights_kernel, dim3(b.n_wblk), dim3(256), 0, st, pc.K, pc.lam, b);
+    if (e != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
     {
         dim3 grid(b.n_kt, b.n_tt);
         const bool ctg = pc.cost_to_go != 0;
         if (noise_bf16) {
             const __nv_bfloat162* zb = reinterpret_cast<const __nv_bfloat162*>(b.z);
-            if (ctg) wsum_kernel<true, true><<<grid, 256, 0, st>>>(pc, L, b, zb);
-            else wsum_kernel<true, false><<<grid, 256, 0, st>>>(pc, L, b, zb);
+            e = ctg ? launch_chained(wsum_kernel<true, true>, grid, dim3(256), 0, st, pc, L, b, zb)
+                    : launch_chained(wsum_kernel<true, false>, grid, dim3(256), 0, st, pc, L, b, zb);
         } else {
             const float2* zf = reinterpret_cast<const float2*>(b.z);
-            if (ctg) wsum_kernel<false, true><<<grid, 256, 0, st>>>(pc, L, b, zf);
-            else wsum_kernel<false, false><<<grid, 256, 0, st>>>(pc, L, b, zf);
+            e = ctg ? launch_chained(wsum_kernel<false, true>, grid, dim3(256), 0, st, pc, L, b, zf)
+                    : launch_chained(wsum_kernel<false, false>, grid, dim3(256), 0, st, pc, L, b, zf);
         }
+        if (e != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
     }
-    finalize_kernel<<<1, ((pc.T + 31) / 32) * 32, 0, st>>>(pc, b, in);
+    if ((e = launch_chained(finalize_kernel, dim3(1), dim3(((pc.T + 31) / 32) * 32), 0, st, pc, b, in)) != cudaSuccess)
+        return e;
     return mark();
 }
 
