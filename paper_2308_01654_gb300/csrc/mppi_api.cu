@@ -165,6 +165,7 @@ static PlanConst make_const(const mppi_params& p) {
     c.dt_d = p.dt;
     c.wheelbase_d = p.wheelbase;
     c.inv_dt_d = 1.0 / p.dt;
+    c.inv_lam_f = (float)(1.0 / p.lam);
     c.dt_over_wb_d = p.dt / p.wheelbase;
     c.amin_d = p.u_min[0];
     c.amax_d = p.u_max[0];
@@ -189,8 +190,7 @@ PlanConst make_const_shared(const mppi_params& p) { return make_const(p); }
 
 static void free_all(mppi_ctx* c) {
     PlanBuffers& b = c->b;
-    void* dev[] = {b.state, b.scene, b.table, b.z, b.S, b.w, b.eta_part, b.min_part, b.min_idx_part,
-                   b.min_cnt_part, b.du_part, b.U, b.stats, b.fix_count, b.fix_list, b.ctg_prefix, b.wt,
+    void* dev[] = {b.state, b.scene, b.table, b.z, b.S, b.w, b.eta_part, b.kmin_part, b.du_part, b.du, b.tt_count, b.U, b.stats, b.fix_count, b.fix_list, b.ctg_prefix, b.wt,
                    b.eta_t, c->d_in, c->d_out};
     for (void* p : dev)
         if (p) cudaFree(p);
@@ -275,8 +275,7 @@ int mppi_create(const mppi_params* params, int device, void* cuda_stream, int32_
     }
     const int K = params->K, T = params->T;
     PlanBuffers& b = c->b;
-    b.n_mblk = (int)std::min<long long>((K + 255) / 256, 296);
-    b.n_wblk = b.n_mblk;
+    b.n_wblk = (int)std::min<long long>((K + 255) / 256, 296);
     b.kt_size = 256 * WS_J;
     b.n_kt = (K + b.kt_size - 1) / b.kt_size;
     b.n_tt = (T + WS_TT - 1) / WS_TT;
@@ -296,10 +295,11 @@ int mppi_create(const mppi_params* params, int device, void* cuda_stream, int32_
         {(void**)&b.S, sizeof(double) * K},
         {(void**)&b.w, sizeof(float) * K},
         {(void**)&b.eta_part, sizeof(double) * b.n_wblk},
-        {(void**)&b.min_part, sizeof(double) * b.n_mblk},
-        {(void**)&b.min_idx_part, sizeof(int) * b.n_mblk},
-        {(void**)&b.min_cnt_part, sizeof(int) * b.n_mblk},
+        // one record per rollout block: at most K blocks (|group| <= 32 lanes a sample, >= 32 threads)
+        {(void**)&b.kmin_part, sizeof(ulonglong2) * (size_t)K},
         {(void**)&b.du_part, sizeof(double) * 2 * (size_t)T * b.n_kt},
+        {(void**)&b.du, sizeof(double) * 2 * (size_t)T},
+        {(void**)&b.tt_count, sizeof(unsigned) * (size_t)b.n_tt},
         {(void**)&b.U, sizeof(double) * 2 * (size_t)T},
         {(void**)&b.stats, sizeof(unsigned long long) * 8},
         {(void**)&b.fix_count, sizeof(unsigned)},
@@ -328,6 +328,7 @@ int mppi_create(const mppi_params* params, int device, void* cuda_stream, int32_
     s0.jkey = ~0ull;
     e = cudaMemcpyAsync(b.state, &s0, sizeof(s0), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.U, 0, sizeof(double) * 2 * (size_t)T, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.tt_count, 0, sizeof(unsigned) * (size_t)b.n_tt, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "context initialisation"));
     *out_ctx = c;

@@ -231,10 +231,9 @@ __global__ void __launch_bounds__(256) batch_weights_kernel(BatchArgs a) {
     float* w = a.w + d.s_off;
     double acc = 0.0;
     for (int k = threadIdx.x; k < d.pc.K; k += blockDim.x) {
-        const double s = S[k];
-        const double wk = isfinite(s) ? exp((smin - s) / d.pc.lam) : 0.0;
-        w[k] = (float)wk;
-        acc += wk;
+        const float wk = softmin_weight(S[k], smin, d.pc.inv_lam_f);
+        w[k] = wk;
+        acc += (double)wk;
     }
     acc = block_sum_d(acc);
     if (threadIdx.x == 0) st->eta = acc;

@@ -19,7 +19,7 @@ struct __align__(16) DevState {
     double eta;                  // sum of softmin weights
     int32_t argmin;
     int32_t n_finite;
-    unsigned int ticket;         // last-block-done counter of the argmin reduction
+    unsigned int ticket;         // last-block-done counter of the argmin reduction (rollout kernel)
     int32_t jb0;                 // reference segment closest to x0
     unsigned long long jkey;     // packed (distance bits, index) for the jb0 search
     float4 x0f;                  // (0, 0, yaw0, v0): x0 in the local frame
@@ -76,6 +76,7 @@ struct PlanConst {
     int cost_to_go;          // 1: per-step weights from the cost still to come
     double inv_dt_d;         // 1 / dt
     double dt_over_wb_d;     // dt / wheelbase
+    float inv_lam_f;         // 1 / lambda
 };
 
 SceneLayout make_layout(int T, int n_ref, int n_circ);
@@ -88,10 +89,10 @@ struct PlanBuffers {
     double* S;               // [K]
     float* w;                // [K] softmin weights
     double* eta_part;        // [n_wblk]
-    double* min_part;        // [n_mblk] (value)
-    int* min_idx_part;       // [n_mblk]
-    int* min_cnt_part;       // [n_mblk]
+    ulonglong2* kmin_part;   // [K] per rollout block: (cost order key, (finite count << 32) | index)
     double* du_part;         // [n_kt][T][2]
+    double* du;              // [T][2] sum over the k-tiles (wsum's last block per step tile), or null
+    unsigned* tt_count;      // [n_tt] k-tile blocks done per step tile (zero between launches)
     double* U;               // [T][2] nominal controls (the warm start)
     unsigned long long* stats;  // [7] work counters (STATS launches only)
     unsigned* fix_count;     // bfloat16 noise: pairs whose rounding is taken again in binary64
@@ -99,7 +100,7 @@ struct PlanBuffers {
     float* ctg_prefix;       // [T][K] cost of steps 0..t-1 per sample (cost-to-go form), or null
     float* wt;               // [T][K] per-step softmin weights (cost-to-go form)
     double* eta_t;           // [T] per-step normalisers (cost-to-go form)
-    int n_mblk, n_wblk, n_kt, n_tt, kt_size;
+    int n_wblk, n_kt, n_tt, kt_size;
 };
 
 // Shared memory each rollout block builds after the staged blob: the level-2 boxes, the

@@ -1088,6 +1088,103 @@ static __device__ MinRec block_min(MinRec a) {
     return a;
 }
 
+// -----------------------------------------------------------------------------
+// argmin with integer keys: a finite binary64 cost maps to a 64-bit key with the same order
+// (sign bit set: all bits flipped, else the sign bit set; -0 is taken as +0), so the
+// reductions compare integers instead of using the binary64 pipe.  Ties go to the lowest
+// index; n counts the finite costs.
+// -----------------------------------------------------------------------------
+struct KeyRec {
+    unsigned long long key;
+    int i;
+    int n;
+};
+
+__device__ __forceinline__ unsigned long long order_key(double s) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(s + 0.0);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double key_value(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
+__device__ __forceinline__ KeyRec key_combine(KeyRec a, KeyRec b) {
+    KeyRec r = (b.key < a.key || (b.key == a.key && b.i < a.i)) ? b : a;
+    r.n = a.n + b.n;
+    return r;
+}
+
+static __device__ KeyRec block_keymin(KeyRec a) {
+    __shared__ unsigned long long sk[32];
+    __shared__ int si[32], sn[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        KeyRec b;
+        b.key = __shfl_xor_sync(0xffffffffu, a.key, o);
+        b.i = __shfl_xor_sync(0xffffffffu, a.i, o);
+        b.n = __shfl_xor_sync(0xffffffffu, a.n, o);
+        a = key_combine(a, b);
+    }
+    if (lane == 0) {
+        sk[w] = a.key;
+        si[w] = a.i;
+        sn[w] = a.n;
+    }
+    __syncthreads();
+    if (w == 0) {
+        a = lane < nw ? KeyRec{sk[lane], si[lane], sn[lane]} : KeyRec{~0ull, 0x7fffffff, 0};
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            KeyRec b;
+            b.key = __shfl_xor_sync(0xffffffffu, a.key, o);
+            b.i = __shfl_xor_sync(0xffffffffu, a.i, o);
+            b.n = __shfl_xor_sync(0xffffffffu, a.n, o);
+            a = key_combine(a, b);
+        }
+    }
+    __syncthreads();
+    return a;
+}
+
+// The argmin of Algorithm 1 (S_min and its sample) folded into the end of the rollout kernel:
+// each block reduces the costs of its own samples k0 .. k0 + nk - 1 (written by the block
+// before the barrier) into one record, and the last block to finish (ticket) combines the
+// records of all blocks in block order.  Every block takes part, also one whose staging
+// timed out (with an empty record), so the ticket always completes and returns to zero.
+__device__ __forceinline__ void rollout_argmin_tail(int K, const PlanBuffers& b, int k0, int nk, bool valid) {
+    __shared__ bool last;
+    __syncthreads();
+    KeyRec r{~0ull, 0x7fffffff, 0};
+    const int k = k0 + (int)threadIdx.x;
+    if (valid && (int)threadIdx.x < nk && k < K) {
+        const double s = b.S[k];
+        if (isfinite(s)) r = KeyRec{order_key(s), k, 1};
+    }
+    r = block_keymin(r);
+    if (threadIdx.x == 0) {
+        b.kmin_part[blockIdx.x] = make_ulonglong2(r.key, ((unsigned long long)(unsigned)r.n << 32) | (unsigned)r.i);
+        __threadfence();
+        last = atomicAdd(&b.state->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    KeyRec q{~0ull, 0x7fffffff, 0};
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        const ulonglong2 p = __ldcg(&b.kmin_part[i]);
+        q = key_combine(q, KeyRec{p.x, (int)(unsigned)(p.y & 0xffffffffull), (int)(p.y >> 32)});
+    }
+    q = block_keymin(q);
+    if (threadIdx.x == 0) {
+        b.state->s_min = q.n > 0 ? key_value(q.key) : INFINITY;
+        b.state->argmin = q.n > 0 ? q.i : -1;
+        b.state->n_finite = q.n;
+        b.state->ticket = 0u;
+    }
+}
+
 static __device__ double block_sum_d(double v) {
     __shared__ double sh[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -1172,6 +1269,17 @@ static __device__ double2 block_scan2_incl(double2 v, double2* sh, int nwa) {
 }
 
 __device__ __forceinline__ double clampd(double x, double lo, double hi) { return fmin(fmax(x, lo), hi); }
+
+// -----------------------------------------------------------------------------
+// Softmin weight of Eq. (11), exp(-(S - S_min) / lambda): the difference is formed in
+// binary64 (costs are large next to their spread), rounded to binary32 and scaled by
+// 1 / lambda, and the exponential is taken in binary32 (relative error of the weight a few
+// 1e-7 times the exponent, far below the update's tolerance); zero for a non-finite cost.
+// binary64 transcendentals are the slow path on this part.
+// -----------------------------------------------------------------------------
+__device__ __forceinline__ float softmin_weight(double s, double smin, float inv_lam) {
+    return isfinite(s) ? expf((float)(smin - s) * inv_lam) : 0.0f;
+}
 
 // -----------------------------------------------------------------------------
 // wsum tile: per step t in [t0, t0 + WS_TT), sum over the k-tile kt (kt_size samples)
@@ -1264,7 +1372,10 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
     const bool h0 = i0 < 2 * T, h1 = i1 < 2 * T;
     const double U0 = h0 ? b.U[i0] : 0.0, U1 = h1 ? b.U[i1] : 0.0;
     double n0 = 0.0, n1 = 0.0;
-    {
+    if (b.du) {                                    // already summed by the weighted-sum kernel
+        if (h0) n0 = b.du[i0];
+        if (h1) n1 = b.du[i1];
+    } else {
         const double* dp = b.du_part;
         const size_t stride = 2 * (size_t)T;
         int kt = 0;

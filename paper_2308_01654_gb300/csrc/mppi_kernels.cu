@@ -3,7 +3,7 @@
 //   prep      reference polyline, obstacle circles and controls -> scene blob (local frame, binary32)
 //   noise     Philox4x32-10 + Box-Muller -> z[T][K]                    (Algorithm 1 GenerateRandomNoise)
 //   rollout   fused Euler rollout of Eq. (5) + step costs of Eq. (12)-(18) -> S[K]
-//   argmin    S_min and its index, last-block reduction                (Algorithm 1, S_min)
+//             with S_min and its index from the rollout's last block      (Algorithm 1, S_min)
 //   weights   w_k = exp(-(S_k - S_min) / lambda), eta partials in binary64  (Eq. (11))
 //   wsum      sum_k w_k eps'_{t,k} per step, eps' recomputed from z      (Eq. (11))
 //   finalize  u + du, clamp, Savitzky-Golay (Eq. (19)), clamp, x* by prefix scans, warm start
@@ -158,72 +158,30 @@ __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 2) rollout_kernel(PlanCon
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long bar;
     pdl_wait();
-    if (!__syncthreads_and(stage_to_smem(smem, b.scene, L.bytes, &bar, &b.state->flags))) return;
-    build_boxes(smem, L, b.table, pc.has_table != 0);
-    const int k = (blockIdx.x * blockDim.x + threadIdx.x) / G;
-    rollout_sample<G, TIME, BF16, STATS, EXT>(pc, L, smem, z, b.table, b.state->x0f, b.state->delta0f,
-                                         b.state->moving != 0, (int)(b.state->jkey & 0xffffffffu), k, b.S, b.stats,
-                                         pc.cost_to_go ? b.ctg_prefix : nullptr);
+    const bool staged = __syncthreads_and(stage_to_smem(smem, b.scene, L.bytes, &bar, &b.state->flags));
+    if (staged) {
+        build_boxes(smem, L, b.table, pc.has_table != 0);
+        const int k = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+        rollout_sample<G, TIME, BF16, STATS, EXT>(pc, L, smem, z, b.table, b.state->x0f, b.state->delta0f,
+                                             b.state->moving != 0, (int)(b.state->jkey & 0xffffffffu), k, b.S,
+                                             b.stats, pc.cost_to_go ? b.ctg_prefix : nullptr);
+    }
     pdl_trigger();   // after the block's samples: the rollout may run in several waves
-}
-
-// -----------------------------------------------------------------------------
-// argmin over S with ties to the lowest index; non-finite costs are skipped.
-// -----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) argmin_kernel(int K, PlanBuffers b) {
-    pdl_wait();
-    pdl_trigger();
-    MinRec r{INFINITY, 0x7fffffff, 0};
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
-        const double s = b.S[k];
-        if (isfinite(s)) {
-            r.n += 1;
-            if (s < r.v) {
-                r.v = s;
-                r.i = k;
-            }
-        }
-    }
-    r = block_min(r);
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
-        b.min_part[blockIdx.x] = r.v;
-        b.min_idx_part[blockIdx.x] = r.i;
-        b.min_cnt_part[blockIdx.x] = r.n;
-        __threadfence();
-        last = atomicAdd(&b.state->ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    MinRec q{INFINITY, 0x7fffffff, 0};
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-        const MinRec p{((volatile double*)b.min_part)[i], ((volatile int*)b.min_idx_part)[i],
-                       ((volatile int*)b.min_cnt_part)[i]};
-        q = min_combine(q, p);
-    }
-    q = block_min(q);
-    if (threadIdx.x == 0) {
-        b.state->s_min = q.v;
-        b.state->argmin = q.n > 0 ? q.i : -1;
-        b.state->n_finite = q.n;
-        b.state->ticket = 0u;
-    }
+    rollout_argmin_tail(pc.K, b, (int)(blockIdx.x * blockDim.x / G), (int)(blockDim.x / G), staged);
 }
 
 // -----------------------------------------------------------------------------
 // softmin weights in binary64 (Eq. (11)); eta partial sums per block.
 // -----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) weights_kernel(int K, double lam, PlanBuffers b) {
+__global__ void __launch_bounds__(256) weights_kernel(int K, float inv_lam, PlanBuffers b) {
     pdl_wait();
     pdl_trigger();
     const double smin = b.state->s_min;
     double acc = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
-        const double s = b.S[k];
-        const double w = isfinite(s) ? exp((smin - s) / lam) : 0.0;
-        b.w[k] = (float)w;
-        acc += w;
+        const float w = softmin_weight(b.S[k], smin, inv_lam);
+        b.w[k] = w;
+        acc += (double)w;
     }
     acc = block_sum_d(acc);
     if (threadIdx.x == 0) b.eta_part[blockIdx.x] = acc;
@@ -232,10 +190,10 @@ __global__ void __launch_bounds__(256) weights_kernel(int K, double lam, PlanBuf
 // -----------------------------------------------------------------------------
 // cost-to-go form of Eq. (11): one block per step t.  The cost of sample k from step t on is
 // S_k - P_{t,k} (P: its cost of the steps before t, written by the rollout); the block takes
-// their minimum, then the weights exp(-(S~ - min) / lambda) (binary32 exponential of the
-// binary64 exponent) and their binary64 sum, the step's normaliser.
+// their minimum, then the weights exp(-(S~ - min) / lambda) (softmin_weight) and their
+// binary64 sum, the step's normaliser.
 // -----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) ctg_weights_kernel(int K, double lam, PlanBuffers b) {
+__global__ void __launch_bounds__(256) ctg_weights_kernel(int K, float inv_lam, PlanBuffers b) {
     pdl_wait();
     pdl_trigger();
     const int t = blockIdx.x;
@@ -255,8 +213,7 @@ __global__ void __launch_bounds__(256) ctg_weights_kernel(int K, double lam, Pla
     const double smin = s_min;
     double acc = 0.0;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        const double s = b.S[k] - (double)P[k];
-        const float w = isfinite(s) ? expf((float)((smin - s) / lam)) : 0.0f;
+        const float w = softmin_weight(b.S[k] - (double)P[k], smin, inv_lam);
         b.wt[(size_t)t * K + k] = w;
         acc += (double)w;
     }
@@ -277,6 +234,32 @@ __global__ void __launch_bounds__(256) wsum_kernel(PlanConst pc, SceneLayout L, 
     pdl_trigger();
     const float4* ctl = reinterpret_cast<const float4*>(b.scene + L.off_ctl);
     wsum_tile<BF16, CTG>(pc, ctl, z, b.w, blockIdx.x, blockIdx.y * WS_TT, b.kt_size, b.du_part, b.wt);
+    // the last k-tile block of this step tile (ticket) adds the k-tile partials of its steps in
+    // k-tile order into du, so the one-block update reads 2T sums instead of 2T x n_kt partials
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&b.tt_count[blockIdx.y], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int T = pc.T, t0 = blockIdx.y * WS_TT, n = 2 * (min(T, t0 + WS_TT) - t0);
+    const int n_kt = gridDim.x;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const size_t e = (size_t)2 * t0 + i;
+        double num = 0.0;
+        int kt = 0;
+        for (; kt + 8 <= n_kt; kt += 8) {
+            double v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = __ldcg(&b.du_part[(size_t)(kt + j) * 2 * T + e]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) num += v[j];
+        }
+        for (; kt < n_kt; ++kt) num += __ldcg(&b.du_part[(size_t)kt * 2 * T + e]);
+        b.du[e] = num;
+    }
+    if (threadIdx.x == 0) b.tt_count[blockIdx.y] = 0u;
 }
 
 // -----------------------------------------------------------------------------
@@ -430,12 +413,12 @@ cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const Pl
     if ((e = mark()) != cudaSuccess) return e;
     if ((e = launch_rollout(pc, L, b, group, threads, noise_bf16, st)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
-    if ((e = launch_chained(argmin_kernel, dim3(b.n_mblk), dim3(256), 0, st, pc.K, b)) != cudaSuccess) return e;
+    // argmin: folded into the rollout kernel (its last block); the stage keeps its event
     if ((e = mark()) != cudaSuccess) return e;
     if (pc.cost_to_go)
-        e = launch_chained(ctg_weights_kernel, dim3(pc.T), dim3(256), 0, st, pc.K, pc.lam, b);
+        e = launch_chained(ctg_weights_kernel, dim3(pc.T), dim3(256), 0, st, pc.K, pc.inv_lam_f, b);
     else
-        e = launch_chained(weights_kernel, dim3(b.n_wblk), dim3(256), 0, st, pc.K, pc.lam, b);
+        e = launch_chained(weights_kernel, dim3(b.n_wblk), dim3(256), 0, st, pc.K, pc.inv_lam_f, b);
     if (e != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
     {
