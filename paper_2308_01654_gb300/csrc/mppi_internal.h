@@ -101,6 +101,7 @@ struct PlanBuffers {
     float* wt;               // [T][K] per-step softmin weights (cost-to-go form)
     double* eta_t;           // [T] per-step normalisers (cost-to-go form)
     int n_wblk, n_kt, n_tt, kt_size;
+    int tt_len;              // steps per step tile of the weighted sum (<= WS_TT)
 };
 
 // Shared memory each rollout block builds after the staged blob: the level-2 boxes, the

@@ -36,8 +36,15 @@ __device__ __forceinline__ float seg_heading(const double* ref, int i) {
     return atan2f((float)hy, (float)hx);
 }
 
+// The preparation in independent phases: 0 controls and x0, 1 vertices, 2 segments and the
+// segment nearest x0, 3 level-1 boxes, 4 circles and the lane direction, 5 the per-step
+// centre table, 6 the largest step of each tabulated centre.  phase < 0 runs them all in
+// turn (one block per plan in the batched planner); the single-plan kernel gives each phase
+// its own row of blocks, so the phases run side by side instead of one after another.
+constexpr int PREP_PHASES = 7;
+
 __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayout& L, const PlanInputs& in,
-                                           const PlanBuffers& b, int tid, int nth) {
+                                           const PlanBuffers& b, int tid, int nth, int phase = -1) {
     const double ox = in.x0[0], oy = in.x0[1];
     unsigned char* sc = b.scene;
     float4* ctl = reinterpret_cast<float4*>(sc + L.off_ctl);
@@ -49,74 +56,97 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
     float4* circ = reinterpret_cast<float4*>(sc + L.off_circ);
     float2* vel = reinterpret_cast<float2*>(sc + L.off_vel);
     float* disp = reinterpret_cast<float*>(sc + L.off_disp);
+    const bool all = phase < 0;
+    const int lane = tid & 31, wid = tid >> 5, nwarps = nth >> 5;
     bool bad = false;
 
-    if (tid == 0) {
-        if (b.fix_count) *b.fix_count = 0u;
-        for (int i = 0; i < (pc.model == 1 ? 5 : 4); ++i) bad |= !isfinite(in.x0[i]);
-        b.state->x0f = make_float4(0.0f, 0.0f, (float)in.x0[2], (float)in.x0[3]);
-        b.state->delta0f = pc.model == 1 ? (float)in.x0[4] : 0.0f;
-    }
-    for (int t = tid; t < L.T; t += nth) {
-        const double ua = b.U[2 * t], ud = b.U[2 * t + 1];
-        ctl[t] = make_float4((float)ua, (float)ud, (float)(pc.g_a * ua), (float)(pc.g_d * ud));
-        c0[t] = (float)(pc.half_Ra * ua * ua + pc.half_Rd * ud * ud);
-    }
-    for (int i = tid; i < L.n_ref; i += nth) {
-        bad |= !isfinite(in.ref[2 * i]) || !isfinite(in.ref[2 * i + 1]);
-        vert[i] = local_vertex(in.ref, i, ox, oy);
-    }
-    for (int i = tid; i < L.n_seg; i += nth) {
-        const float4 s = seg_record(in.ref, i, ox, oy);
-        seg[i] = s;
-        head[i] = seg_heading(in.ref, i);
-        // closest segment (or vertex) to x0 itself: the rollouts' first warm start
-        const float2 a = local_vertex(in.ref, i, ox, oy);
-        const float d2 = pc.ref_mode == 0 ? seg_dist2(0.0f, 0.0f, a, s) : fmaf(a.x, a.x, a.y * a.y);
-        const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)i;
-        atomicMin(&b.state->jkey, key);
-    }
-    // level-1 boxes: one thread per chunk (its REF_L1 + 1 vertex loads are independent)
-    for (int c = tid; c < L.n_l1; c += nth) {
-        const int v0 = c * REF_L1, v1 = min(v0 + REF_L1, L.n_seg);
-        float4 bb = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
-#pragma unroll
-        for (int j = 0; j <= REF_L1; ++j) {
-            if (v0 + j <= v1) {
-                const float2 p = local_vertex(in.ref, v0 + j, ox, oy);
-                bb.x = fminf(bb.x, p.x); bb.y = fminf(bb.y, p.y);
-                bb.z = fmaxf(bb.z, p.x); bb.w = fmaxf(bb.w, p.y);
-            }
+    if (all || phase == 0) {
+        if (tid == 0) {
+            if (b.fix_count) *b.fix_count = 0u;
+            for (int i = 0; i < (pc.model == 1 ? 5 : 4); ++i) bad |= !isfinite(in.x0[i]);
+            b.state->x0f = make_float4(0.0f, 0.0f, (float)in.x0[2], (float)in.x0[3]);
+            b.state->delta0f = pc.model == 1 ? (float)in.x0[4] : 0.0f;
         }
-        l1[c] = bb;
+        for (int t = tid; t < L.T; t += nth) {
+            const double ua = b.U[2 * t], ud = b.U[2 * t + 1];
+            ctl[t] = make_float4((float)ua, (float)ud, (float)(pc.g_a * ua), (float)(pc.g_d * ud));
+            c0[t] = (float)(pc.half_Ra * ua * ua + pc.half_Rd * ud * ud);
+        }
     }
-    const int lane = tid & 31, wid = tid >> 5, nwarps = nth >> 5;
-    for (int k = tid; k < L.n_circ; k += nth) {
-        const double* c = in.circ + 5 * k;
-        for (int j = 0; j < 5; ++j) bad |= !isfinite(c[j]);
-        const float r = (float)c[2];
-        // band limit (m + r + r_ego)^2 for the constant-d_safe, equal-ego-radius case
-        const float m = pc.collision_only ? fmaxf(pc.d_safe_0, 0.0f) : pc.d_safe_0;
-        const float lim = m + r + pc.ego_rad[0];
-        circ[k] = make_float4((float)(c[0] - ox), (float)(c[1] - oy), r, lim > 0.0f ? lim * lim : -1.0f);
-        vel[k] = make_float2((float)c[3], (float)c[4]);
-        if (c[3] != 0.0 || c[4] != 0.0) atomicOr(&b.state->moving, 1);
-        if (!in.centres) disp[k] = (float)(sqrt(c[3] * c[3] + c[4] * c[4]) * pc.dt_d * 1.001) + 1e-5f;
+    if (all || phase == 1) {
+        for (int i = tid; i < L.n_ref; i += nth) {
+            bad |= !isfinite(in.ref[2 * i]) || !isfinite(in.ref[2 * i + 1]);
+            vert[i] = local_vertex(in.ref, i, ox, oy);
+        }
     }
-    // unit lane direction (first to last vertex): the axis the rollout blocks sort the circles on
-    if (tid == 0) {
-        const double ex = in.ref[2 * (L.n_ref - 1)] - in.ref[0], ey = in.ref[2 * (L.n_ref - 1) + 1] - in.ref[1];
-        const double el = sqrt(ex * ex + ey * ey);
-        const bool ok = el > 0.0 && isfinite(el);
-        *reinterpret_cast<float4*>(sc + L.off_proj) =
-            make_float4(ok ? (float)(ex / el) : 1.0f, ok ? (float)(ey / el) : 0.0f, 0.0f, 0.0f);
+    if (all || phase == 2) {
+        // closest segment (or vertex) to x0 itself, the rollouts' first warm start: a packed
+        // (distance bits, index) minimum, reduced in the warp before one atomic per warp
+        unsigned long long best = ~0ull;
+        for (int i = tid; i < L.n_seg; i += nth) {
+            const float4 s = seg_record(in.ref, i, ox, oy);
+            seg[i] = s;
+            head[i] = seg_heading(in.ref, i);
+            const float2 a = local_vertex(in.ref, i, ox, oy);
+            const float d2 = pc.ref_mode == 0 ? seg_dist2(0.0f, 0.0f, a, s) : fmaf(a.x, a.x, a.y * a.y);
+            const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)i;
+            best = key < best ? key : best;
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+            best = other < best ? other : best;
+        }
+        if (lane == 0 && best != ~0ull) atomicMin(&b.state->jkey, best);
     }
-    if (in.centres) {
+    if (all || phase == 3) {
+        // level-1 boxes: one thread per chunk (its REF_L1 + 1 vertex loads are independent)
+        for (int c = tid; c < L.n_l1; c += nth) {
+            const int v0 = c * REF_L1, v1 = min(v0 + REF_L1, L.n_seg);
+            float4 bb = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
+#pragma unroll
+            for (int j = 0; j <= REF_L1; ++j) {
+                if (v0 + j <= v1) {
+                    const float2 p = local_vertex(in.ref, v0 + j, ox, oy);
+                    bb.x = fminf(bb.x, p.x); bb.y = fminf(bb.y, p.y);
+                    bb.z = fmaxf(bb.z, p.x); bb.w = fmaxf(bb.w, p.y);
+                }
+            }
+            l1[c] = bb;
+        }
+    }
+    if (all || phase == 4) {
+        for (int k = tid; k < L.n_circ; k += nth) {
+            const double* c = in.circ + 5 * k;
+            for (int j = 0; j < 5; ++j) bad |= !isfinite(c[j]);
+            const float r = (float)c[2];
+            // band limit (m + r + r_ego)^2 for the constant-d_safe, equal-ego-radius case
+            const float m = pc.collision_only ? fmaxf(pc.d_safe_0, 0.0f) : pc.d_safe_0;
+            const float lim = m + r + pc.ego_rad[0];
+            circ[k] = make_float4((float)(c[0] - ox), (float)(c[1] - oy), r, lim > 0.0f ? lim * lim : -1.0f);
+            vel[k] = make_float2((float)c[3], (float)c[4]);
+            if (c[3] != 0.0 || c[4] != 0.0) atomicOr(&b.state->moving, 1);
+            // bound on the step of a constant-velocity centre, |v| dt with 0.1 % and 1e-5 m to spare
+            // (binary32 square root: its error is far inside that margin)
+            if (!in.centres) disp[k] = sqrtf((float)(c[3] * c[3] + c[4] * c[4])) * pc.dt * 1.001f + 1e-5f;
+        }
+        // unit lane direction (first to last vertex): the axis the rollout blocks sort the circles on
+        if (tid == 0) {
+            const double ex = in.ref[2 * (L.n_ref - 1)] - in.ref[0], ey = in.ref[2 * (L.n_ref - 1) + 1] - in.ref[1];
+            const double el = sqrt(ex * ex + ey * ey);
+            const bool ok = el > 0.0 && isfinite(el);
+            *reinterpret_cast<float4*>(sc + L.off_proj) =
+                make_float4(ok ? (float)(ex / el) : 1.0f, ok ? (float)(ey / el) : 0.0f, 0.0f, 0.0f);
+        }
+    }
+    if (in.centres && (all || phase == 5)) {
         for (int i = tid; i < L.T * L.n_circ; i += nth) {
             const double cx = in.centres[2 * i], cy = in.centres[2 * i + 1];
             bad |= !isfinite(cx) || !isfinite(cy);
             b.table[i] = make_float2((float)(cx - ox), (float)(cy - oy));
         }
+    }
+    if (in.centres && (all || phase == 6)) {
         // the largest step of each tabulated centre (from the rounded entries the rollouts
         // read): one warp per circle, the lanes stride over the steps
         for (int k = wid; k < L.n_circ; k += nwarps) {
@@ -1282,19 +1312,22 @@ __device__ __forceinline__ float softmin_weight(double s, double smin, float inv
 }
 
 // -----------------------------------------------------------------------------
-// wsum tile: per step t in [t0, t0 + WS_TT), sum over the k-tile kt (kt_size samples)
+// wsum tile: per step t in [t0, t0 + TT) (TT <= WS_TT, a compile-time bound so the step
+// loop unrolls; the partial of each step does not depend on how the steps are tiled), sum
+// over the k-tile kt (kt_size samples)
 // of w_k eps'_{t,k}.  Each thread owns WS_J samples, recomputes eps' from z exactly
 // as the rollout did, accumulates in binary32 over its samples and its warp (32 x WS_J
 // products); the per-warp partials are added in binary64 into du_part[kt][T][2].
 // -----------------------------------------------------------------------------
 
-template <bool BF16, bool CTG = false>
+template <bool BF16, bool CTG = false, int TT = WS_TT>
 __device__ __forceinline__ void wsum_tile(const PlanConst& pc, const float4* ctl,
                                           const typename NoiseT<BF16>::type* __restrict__ z, const float* w, int kt,
                                           int t0, int kt_size, double* du_part, const float* wt = nullptr) {
-    __shared__ float red[8][WS_TT][2];
+    static_assert(TT >= 1 && TT <= WS_TT, "step tile");
+    __shared__ float red[8][TT][2];
     const int K = pc.K, T = pc.T;
-    const int t1 = min(T, t0 + WS_TT);
+    const int t1 = min(T, t0 + TT);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float wj[WS_J];
     int kj[WS_J];

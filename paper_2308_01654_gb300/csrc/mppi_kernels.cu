@@ -68,11 +68,11 @@ static cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 bloc
 // -----------------------------------------------------------------------------
 // prep: one pass over the inputs.  Positions are shifted into a frame centred on
 // (x0, y0) in binary64 before rounding, so binary32 keeps its resolution where
-// the rollouts happen.
+// the rollouts happen.  One row of blocks per phase of prep_scene (blockIdx.y).
 // -----------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) prep_kernel(PlanConst pc, SceneLayout L, PlanInputs in, PlanBuffers b) {
     pdl_trigger();
-    prep_scene(pc, L, in, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    prep_scene(pc, L, in, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, blockIdx.y);
 }
 
 // -----------------------------------------------------------------------------
@@ -227,13 +227,13 @@ __global__ void __launch_bounds__(256) ctg_weights_kernel(int K, float inv_lam, 
 // its J samples and its warp (32 x J products), and the per-warp partials are
 // added in binary64.
 // -----------------------------------------------------------------------------
-template <bool BF16, bool CTG>
+template <bool BF16, bool CTG, int TT>
 __global__ void __launch_bounds__(256) wsum_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
                                                    const typename NoiseT<BF16>::type* __restrict__ z) {
     pdl_wait();
     pdl_trigger();
     const float4* ctl = reinterpret_cast<const float4*>(b.scene + L.off_ctl);
-    wsum_tile<BF16, CTG>(pc, ctl, z, b.w, blockIdx.x, blockIdx.y * WS_TT, b.kt_size, b.du_part, b.wt);
+    wsum_tile<BF16, CTG, TT>(pc, ctl, z, b.w, blockIdx.x, blockIdx.y * TT, b.kt_size, b.du_part, b.wt);
     // the last k-tile block of this step tile (ticket) adds the k-tile partials of its steps in
     // k-tile order into du, so the one-block update reads 2T sums instead of 2T x n_kt partials
     __shared__ bool last;
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256) wsum_kernel(PlanConst pc, SceneLayout L, 
     __syncthreads();
     if (!last) return;
     __threadfence();
-    const int T = pc.T, t0 = blockIdx.y * WS_TT, n = 2 * (min(T, t0 + WS_TT) - t0);
+    const int T = pc.T, t0 = blockIdx.y * TT, n = 2 * (min(T, t0 + TT) - t0);
     const int n_kt = gridDim.x;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const size_t e = (size_t)2 * t0 + i;
@@ -273,6 +273,17 @@ __global__ void __launch_bounds__(1024) finalize_kernel(PlanConst pc, PlanBuffer
 // -----------------------------------------------------------------------------
 // host-side launchers
 // -----------------------------------------------------------------------------
+template <bool BF16, bool CTG>
+static cudaError_t launch_wsum(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
+                               const typename NoiseT<BF16>::type* z, dim3 grid, cudaStream_t st) {
+    switch (b.tt_len) {
+        case 8: return launch_chained(wsum_kernel<BF16, CTG, 8>, grid, dim3(256), 0, st, pc, L, b, z);
+        case 4: return launch_chained(wsum_kernel<BF16, CTG, 4>, grid, dim3(256), 0, st, pc, L, b, z);
+        case 2: return launch_chained(wsum_kernel<BF16, CTG, 2>, grid, dim3(256), 0, st, pc, L, b, z);
+        case 1: return launch_chained(wsum_kernel<BF16, CTG, 1>, grid, dim3(256), 0, st, pc, L, b, z);
+        default: return cudaErrorInvalidValue;
+    }
+}
 template <int G, bool TIME, bool BF16, bool STATS, bool EXT>
 static cudaError_t launch_rollout_t(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int threads,
                                     cudaStream_t st) {
@@ -366,7 +377,7 @@ cudaError_t launch_prep_noise(const PlanConst& pc, const SceneLayout& L, const P
     items = max(items, L.n_circ);
     if (in.centres) items = max(items, L.T * L.n_circ);
     const int blocks = min(max((items + 255) / 256, 1), 148);
-    prep_kernel<<<blocks, 256, 0, st>>>(pc, L, in, b);
+    prep_kernel<<<dim3(blocks, PREP_PHASES), 256, 0, st>>>(pc, L, in, b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_noise(pc, b, noise_bf16, st);
@@ -406,7 +417,7 @@ cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const Pl
         items = max(items, L.n_circ);
         if (in.centres) items = max(items, L.T * L.n_circ);
         const int blocks = min(max((items + 255) / 256, 1), 148);
-        prep_kernel<<<blocks, 256, 0, st>>>(pc, L, in, b);
+        prep_kernel<<<dim3(blocks, PREP_PHASES), 256, 0, st>>>(pc, L, in, b);
         if ((e = mark()) != cudaSuccess) return e;
     }
     if ((e = launch_noise(pc, b, noise_bf16, st)) != cudaSuccess) return e;
@@ -426,12 +437,10 @@ cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const Pl
         const bool ctg = pc.cost_to_go != 0;
         if (noise_bf16) {
             const __nv_bfloat162* zb = reinterpret_cast<const __nv_bfloat162*>(b.z);
-            e = ctg ? launch_chained(wsum_kernel<true, true>, grid, dim3(256), 0, st, pc, L, b, zb)
-                    : launch_chained(wsum_kernel<true, false>, grid, dim3(256), 0, st, pc, L, b, zb);
+            e = ctg ? launch_wsum<true, true>(pc, L, b, zb, grid, st) : launch_wsum<true, false>(pc, L, b, zb, grid, st);
         } else {
             const float2* zf = reinterpret_cast<const float2*>(b.z);
-            e = ctg ? launch_chained(wsum_kernel<false, true>, grid, dim3(256), 0, st, pc, L, b, zf)
-                    : launch_chained(wsum_kernel<false, false>, grid, dim3(256), 0, st, pc, L, b, zf);
+            e = ctg ? launch_wsum<false, true>(pc, L, b, zf, grid, st) : launch_wsum<false, false>(pc, L, b, zf, grid, st);
         }
         if (e != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
