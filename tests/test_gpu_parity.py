@@ -288,6 +288,32 @@ def test_all_costs_non_finite_leaves_controls():
         assert it == 0
 
 
+@pytest.mark.parametrize("case", ["signed", "all_equal"])
+def test_argmin_over_signed_and_tied_costs(case):
+    """S_min and its sample (Algorithm 1) over costs of both signs, and over costs that are all
+    exactly equal (every sample ties: the lowest index wins).  Only the control cost is on, so
+    a sample's cost is sum_t (1/2 u^T R u + (1 + alpha) u^T R eps): with a small nominal u the
+    noise term gives costs of either sign; with u = 0 every cost is exactly 0."""
+    prob = sc.single_plan()
+    prob.params.update(K=1000, T=40, seed=17)
+    for w in ("w_dist", "w_target", "w_yaw", "w_speed", "w_safe", "w_terminal"):
+        prob.params[w] = 0.0
+    with mp.Planner(prob.params) as pl:
+        if case == "signed":
+            pl.set_controls(np.column_stack([np.full(40, 0.05), np.zeros(40)]), 0)
+        u, x, info = pl.plan(prob.x0, prob.ref, prob.circles)
+        S = pl.get_costs()
+    if case == "signed":
+        assert (S < 0).sum() > 50 and (S > 0).sum() > 50
+    else:
+        assert np.all(S == 0.0)
+    assert info["n_finite"] == int(np.isfinite(S).sum()) == 1000
+    assert info["s_min"] == S.min()
+    assert info["argmin"] == int(np.flatnonzero(S == S.min())[0])
+    if case == "all_equal":
+        assert info["argmin"] == 0
+
+
 def test_capacity_is_enforced():
     prob = sc.single_plan()
     prob.params.update(K=64, T=8)
