@@ -69,25 +69,25 @@ class MppiInfo(C.Structure):
 _lib = None
 
 # every entry point of include/mppi.h with its ctypes signature
-_VP, _DP, _FP, _U32P = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float), C.POINTER(C.c_uint32)
+_VP = C.c_void_p
 SIGNATURES = {
     "mppi_default_params": (C.c_int, [C.POINTER(MppiParams), C.c_int32, C.c_int32, C.c_double]),
     "mppi_create": (C.c_int, [C.POINTER(MppiParams), C.c_int, _VP, C.c_int32, C.c_int32, C.POINTER(_VP)]),
     "mppi_destroy": (C.c_int, [_VP]),
     "mppi_set_stream": (C.c_int, [_VP, _VP]),
-    "mppi_plan": (C.c_int, [_VP, _DP, _DP, C.c_int32, _DP, C.c_int32, _DP, _DP, _DP, C.POINTER(MppiInfo)]),
+    "mppi_plan": (C.c_int, [_VP, _VP, _VP, C.c_int32, _VP, C.c_int32, _VP, _VP, _VP, C.POINTER(MppiInfo)]),
     "mppi_plan_device": (C.c_int, [_VP, _VP, _VP, C.c_int32, _VP, C.c_int32, _VP, _VP, _VP, C.POINTER(MppiInfo)]),
     "mppi_sync": (C.c_int, [_VP, C.POINTER(MppiInfo)]),
-    "mppi_rollout_stats": (C.c_int, [_VP, _DP, _DP, C.c_int32, _DP, C.c_int32, _DP, C.POINTER(C.c_uint64)]),
-    "mppi_autotune": (C.c_int, [_VP, _DP, _DP, C.c_int32, _DP, C.c_int32, _DP, C.c_char_p,
+    "mppi_rollout_stats": (C.c_int, [_VP, _VP, _VP, C.c_int32, _VP, C.c_int32, _VP, C.POINTER(C.c_uint64)]),
+    "mppi_autotune": (C.c_int, [_VP, _VP, _VP, C.c_int32, _VP, C.c_int32, _VP, C.c_char_p,
                                 C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
-    "mppi_set_controls": (C.c_int, [_VP, _DP, C.c_uint64]),
-    "mppi_get_controls": (C.c_int, [_VP, _DP, C.POINTER(C.c_uint64)]),
-    "mppi_get_costs": (C.c_int, [_VP, _DP]),
-    "mppi_get_noise": (C.c_int, [_VP, _FP]),
-    "mppi_philox": (C.c_int, [C.c_uint64, _U32P, C.c_int32, _U32P]),
+    "mppi_set_controls": (C.c_int, [_VP, _VP, C.c_uint64]),
+    "mppi_get_controls": (C.c_int, [_VP, _VP, C.POINTER(C.c_uint64)]),
+    "mppi_get_costs": (C.c_int, [_VP, _VP]),
+    "mppi_get_noise": (C.c_int, [_VP, _VP]),
+    "mppi_philox": (C.c_int, [C.c_uint64, _VP, C.c_int32, _VP]),
     "mppi_set_profiling": (C.c_int, [_VP, C.c_int32]),
-    "mppi_kernel_times": (C.c_int, [_VP, _FP, C.c_int32]),
+    "mppi_kernel_times": (C.c_int, [_VP, _VP, C.c_int32]),
     "mppi_argmin_noalloc": (C.c_int, [_VP, C.c_int32, _VP, _VP, _VP, _VP]),
     "mppi_batch_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_int32,
                                     C.c_int32, C.c_int32, C.c_int, C.POINTER(_VP)]),
@@ -98,19 +98,19 @@ SIGNATURES = {
     "mppi_batch_autotune": (C.c_int, [_VP, _VP, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "mppi_box_to_circles": (C.c_int32, [C.c_double] * 7 + [C.c_int32, _VP, C.c_int32]),
     "mppi_batch_set_launch": (C.c_int, [_VP, C.c_int32, C.c_int32]),
-    "mppi_batch_set_controls": (C.c_int, [_VP, C.c_int32, _DP, C.c_int32, C.c_uint64]),
-    "mppi_batch_get_controls": (C.c_int, [_VP, C.c_int32, _DP, C.c_int32, C.POINTER(C.c_uint64)]),
+    "mppi_batch_set_controls": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, C.c_uint64]),
+    "mppi_batch_get_controls": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, C.POINTER(C.c_uint64)]),
     "mppi_batch_last_error": (C.c_char_p, [_VP]),
     "mppi_server_create": (C.c_int, [_VP, C.POINTER(_VP)]),
     "mppi_server_destroy": (C.c_int, [_VP]),
-    "mppi_server_autotune": (C.c_int, [_VP, _VP, _DP, _DP, C.c_int32, _DP, C.c_int32, C.c_int32,
+    "mppi_server_autotune": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int32, _VP, C.c_int32, C.c_int32,
                                        C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
-    "mppi_server_enqueue": (C.c_int, [_VP, _VP, C.c_int32, _DP, _DP, C.c_int32, _DP, C.c_int32, _DP,
+    "mppi_server_enqueue": (C.c_int, [_VP, _VP, C.c_int32, _VP, _VP, C.c_int32, _VP, C.c_int32, _VP,
                                       C.POINTER(C.c_uint64)]),
-    "mppi_server_poll": (C.c_int, [_VP, _VP, C.c_int32, _DP, _DP, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
+    "mppi_server_poll": (C.c_int, [_VP, _VP, C.c_int32, _VP, _VP, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
     "mppi_server_pending": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_uint64),
                                       C.POINTER(C.c_uint64)]),
-    "mppi_server_set_controls": (C.c_int, [_VP, C.c_int32, _DP, C.c_int32, C.c_uint64]),
+    "mppi_server_set_controls": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, C.c_uint64]),
     "mppi_server_last_error": (C.c_char_p, [_VP]),
     "mppi_status_string": (C.c_char_p, [C.c_int]),
     "mppi_last_error": (C.c_char_p, [_VP]),
@@ -174,7 +174,15 @@ def _f64(a) -> np.ndarray:
 
 
 def _dp(a: Optional[np.ndarray]):
-    return None if a is None else a.ctypes.data_as(_DP)
+    """Address of an array's data for a void* parameter (None stays NULL).  Through the buffer
+    protocol when the array is writable (a few times cheaper than ndarray.ctypes, which is most
+    of the binding's cost per call), else through ndarray.ctypes (read-only or empty arrays)."""
+    if a is None:
+        return None
+    try:
+        return C.addressof(C.c_char.from_buffer(a))
+    except (TypeError, ValueError, BufferError):
+        return a.ctypes.data
 
 
 class Planner:
@@ -295,7 +303,7 @@ class Planner:
 
     def get_noise(self) -> np.ndarray:
         z = np.empty((self.T, self.K, 2), dtype=np.float32)
-        _check(lib().mppi_get_noise(self._h, z.ctypes.data_as(_FP)), self._h)
+        _check(lib().mppi_get_noise(self._h, _dp(z)), self._h)
         return z
 
 
@@ -326,7 +334,7 @@ def box_to_circles(x: float, y: float, yaw: float, length: float, width: float, 
     cap = n if n > 0 else (max(1, int(np.ceil(length / width))) if ok else 1)
     out = np.zeros((cap, 5), dtype=np.float64)
     rc = lib().mppi_box_to_circles(float(x), float(y), float(yaw), float(length), float(width), float(vx),
-                                   float(vy), int(n), out.ctypes.data_as(_VP), cap)
+                                   float(vy), int(n), _dp(out), cap)
     if rc < 0:
         raise MppiError(rc, "mppi_box_to_circles")
     return out[:rc]
@@ -336,8 +344,7 @@ def philox(seed: int, ctr) -> np.ndarray:
     """Raw Philox4x32-10 words computed on the GPU for counters ctr[n][4]."""
     c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
     out = np.empty_like(c)
-    rc = lib().mppi_philox(int(seed) & 0xFFFFFFFFFFFFFFFF, c.ctypes.data_as(_U32P), c.shape[0],
-                           out.ctypes.data_as(_U32P))
+    rc = lib().mppi_philox(int(seed) & 0xFFFFFFFFFFFFFFFF, _dp(c), c.shape[0], _dp(out))
     _check(rc)
     return out
 
@@ -353,8 +360,8 @@ INF = math.inf
 
 class MppiRequest(C.Structure):
     _fields_ = [("params", C.POINTER(MppiParams)), ("slot", C.c_int32),
-                ("x0", _DP), ("ref_xy", _DP), ("n_ref", C.c_int32), ("circ", _DP), ("n_circ", C.c_int32),
-                ("centres", _DP), ("u_out", _DP), ("x_out", _DP), ("info", C.POINTER(MppiInfo)),
+                ("x0", _VP), ("ref_xy", _VP), ("n_ref", C.c_int32), ("circ", _VP), ("n_circ", C.c_int32),
+                ("centres", _VP), ("u_out", _VP), ("x_out", _VP), ("info", C.POINTER(MppiInfo)),
                 ("status", C.c_int32)]
 
 
