@@ -62,7 +62,6 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
 
     if (all || phase == 0) {
         if (tid == 0) {
-            if (b.fix_count) *b.fix_count = 0u;
             for (int i = 0; i < (pc.model == 1 ? 5 : 4); ++i) bad |= !isfinite(in.x0[i]);
             b.state->x0f = make_float4(0.0f, 0.0f, (float)in.x0[2], (float)in.x0[3]);
             b.state->delta0f = pc.model == 1 ? (float)in.x0[4] : 0.0f;
@@ -1443,6 +1442,7 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
         }
     }
     __syncthreads();
+    if (t == 0 && b.fix_count) *b.fix_count = 0u;    // the bf16 fix-up list of the next iteration's noise
     if (s_status != 0) {
         if (t == 0) {
             st->status = s_status;

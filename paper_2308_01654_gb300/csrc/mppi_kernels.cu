@@ -380,6 +380,7 @@ cudaError_t launch_prep_noise(const PlanConst& pc, const SceneLayout& L, const P
     prep_kernel<<<dim3(blocks, PREP_PHASES), 256, 0, st>>>(pc, L, in, b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (b.fix_count && (e = cudaMemsetAsync(b.fix_count, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
     return launch_noise(pc, b, noise_bf16, st);
 }
 
@@ -397,7 +398,7 @@ cudaError_t launch_reset_state(DevState* st, cudaStream_t s) {
 
 cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
                              const PlanInputs& in, int group, int threads, int noise_bf16, cudaStream_t st,
-                             cudaEvent_t* ev, int ev_mode) {
+                             cudaEvent_t* ev, int ev_mode, const IterFork* fork) {
     // ev_mode 1: an event before the first kernel and after each (every boundary timed, none
     // chained); 2: only the two around the rollout (ev[2], ev[3]), the other kernels stay chained
     cudaError_t e;
@@ -411,6 +412,17 @@ cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const Pl
     };
     if (ev && ev_mode != 2 && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
     ++stage;
+    const bool forked = fork && fork->side;
+    if (forked) {
+        // noise (and the bf16 fix-up) on the side stream, after everything queued on st so far
+        if ((e = cudaEventRecord(fork->fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(fork->side, fork->fork, 0)) != cudaSuccess) return e;
+        if ((e = launch_noise(pc, b, noise_bf16, fork->side)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(fork->join, fork->side)) != cudaSuccess) return e;
+    }
+    if (fork && fork->h2d_bytes &&
+        (e = cudaMemcpyAsync(fork->h2d_dst, fork->h2d_src, fork->h2d_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return e;
     {
         int items = L.n_ref;
         items = max(items, L.T);
@@ -420,7 +432,9 @@ cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const Pl
         prep_kernel<<<dim3(blocks, PREP_PHASES), 256, 0, st>>>(pc, L, in, b);
         if ((e = mark()) != cudaSuccess) return e;
     }
-    if ((e = launch_noise(pc, b, noise_bf16, st)) != cudaSuccess) return e;
+    if (forked) e = cudaStreamWaitEvent(st, fork->join, 0);
+    else e = launch_noise(pc, b, noise_bf16, st);
+    if (e != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
     if ((e = launch_rollout(pc, L, b, group, threads, noise_bf16, st)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
