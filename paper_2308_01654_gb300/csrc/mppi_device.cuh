@@ -127,6 +127,39 @@ template <> struct NoiseT<true> {
 };
 
 // -----------------------------------------------------------------------------
+// L2 residency of the noise.  z is written once and read twice (rollout, then weighted sum);
+// it is smaller than L2 but, stored with the default policy, about half of it is evicted before
+// the second read.  The noise kernel stores it with an evict-last policy and the weighted sum,
+// its last reader, loads it as streaming data.
+// -----------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long l2_keep_policy() {
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ void store_keep(float2* p, float2 v, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol)
+                 : "memory");
+}
+
+__device__ __forceinline__ void store_keep(__nv_bfloat162* p, __nv_bfloat162 v, unsigned long long pol) {
+    const unsigned bits = *reinterpret_cast<const unsigned*>(&v);
+    asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(bits), "l"(pol) : "memory");
+}
+
+// last read of the noise: streaming load
+template <bool BF16>
+__device__ __forceinline__ float2 load_last(const typename NoiseT<BF16>::type* p) {
+    if constexpr (BF16) {
+        const unsigned bits = __ldcs(reinterpret_cast<const unsigned*>(p));
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&bits));
+    } else {
+        return __ldcs(p);
+    }
+}
+
+// -----------------------------------------------------------------------------
 // Control perturbation with the noise check of Sec. III-A: v = clamp(u + sigma z)
 // and eps' = v - u.  Written with explicit rounding so the rollout and the update
 // kernels produce the same bits.

@@ -1345,7 +1345,7 @@ __device__ __forceinline__ void wsum_tile(const PlanConst& pc, const float4* ctl
 #pragma unroll
         for (int j = 0; j < WS_J; ++j) {
             if (kj[j] < K) {
-                const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kj[j]);
+                const float2 zz = load_last<BF16>(z + (size_t)t * K + kj[j]);
                 const Perturbed pe =
                     perturb(ct.x, ct.y, zz, pc.sig_a, pc.sig_d, pc.amin, pc.amax, pc.dmin, pc.dmax);
                 aa = fmaf(wj[j], pe.ea, aa);

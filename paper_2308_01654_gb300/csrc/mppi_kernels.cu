@@ -93,11 +93,12 @@ __global__ void __launch_bounds__(256) noise_kernel(PlanConst pc, const DevState
     const uint4 w = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)k, it, pc.session), make_uint2(pc.key0, pc.key1));
     const size_t K = (size_t)pc.K;
     const bool two = 2 * j + 1 < pc.T;
+    const unsigned long long keep = l2_keep_policy();
     if constexpr (BF16) {
         const float2 za = box_muller(uniform24(w.x), uniform24(w.y));
         const float2 zb = box_muller(uniform24(w.z), uniform24(w.w));
-        z[(size_t)(2 * j) * K + k] = NoiseT<true>::pack(za);
-        if (two) z[(size_t)(2 * j + 1) * K + k] = NoiseT<true>::pack(zb);
+        store_keep(z + (size_t)(2 * j) * K + k, NoiseT<true>::pack(za), keep);
+        if (two) store_keep(z + (size_t)(2 * j + 1) * K + k, NoiseT<true>::pack(zb), keep);
         const bool fix = near_bf16_midpoint(za.x) || near_bf16_midpoint(za.y) ||
                          (two && (near_bf16_midpoint(zb.x) || near_bf16_midpoint(zb.y)));
         if (fix) {
@@ -110,8 +111,8 @@ __global__ void __launch_bounds__(256) noise_kernel(PlanConst pc, const DevState
             }
         }
     } else {
-        z[(size_t)(2 * j) * K + k] = make_noise<false>(uniform24(w.x), uniform24(w.y));
-        if (two) z[(size_t)(2 * j + 1) * K + k] = make_noise<false>(uniform24(w.z), uniform24(w.w));
+        store_keep(z + (size_t)(2 * j) * K + k, make_noise<false>(uniform24(w.x), uniform24(w.y)), keep);
+        if (two) store_keep(z + (size_t)(2 * j + 1) * K + k, make_noise<false>(uniform24(w.z), uniform24(w.w)), keep);
     }
 }
 
