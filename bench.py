@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "rollout-steps/s (K*T) of one MPPI iteration"
 UNIT = "rollout-steps/s"
-KERNEL_LAUNCHES_PER_STEP = 6   # prep, noise, rollout (with the argmin), weights, wsum, finalize (+1 noise fix-up for bf16 noise)
+KERNEL_LAUNCHES_PER_STEP = 5   # prep + noise, rollout (with the argmin), weights, wsum, finalize (+1 noise fix-up for bf16 noise)
 
 
 # ------------------------------------------------------------------------ helpers

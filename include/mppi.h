@@ -216,9 +216,11 @@ int mppi_philox(uint64_t seed, const uint32_t* ctr, int32_t n, uint32_t* out);
 /* Per-kernel timing with CUDA events on the context's stream (the library's own
    tracing; no effect on results).  on = 1: each iteration records MPPI_N_KERNELS + 1
    events; mppi_kernel_times() waits for the last iteration and writes the durations in
-   milliseconds of its kernels, in launch order: prep, noise, rollout, argmin, weights,
-   wsum, finalize.  An event between two kernels ends their chaining (the second kernel
-   is otherwise scheduled while the first drains), so on = 1 lengthens the iteration.
+   milliseconds of its stages, in launch order: prep (scene preparation and noise, one
+   launch), noise (the bfloat16 form's fix-up; empty otherwise), rollout (ends with the
+   argmin), argmin (empty), weights, wsum, finalize.  An event between two kernels ends
+   their chaining (the second kernel is otherwise scheduled while the first drains), so
+   on = 1 lengthens the iteration.
    on = 2: only the two events around the rollout kernel; mppi_kernel_times() writes its
    duration and NaN for the others.  on = 0: off.  Other values: MPPI_ERR_ARG. */
 #define MPPI_N_KERNELS 7

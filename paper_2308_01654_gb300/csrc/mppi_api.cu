@@ -36,9 +36,6 @@ struct mppi_ctx {
     long long graph_key = -1, seen_key = -1;
     size_t graph_n_in = 0;
     cudaEvent_t ev[N_KERNELS + 1] = {};
-    // second stream for the noise, which runs beside the input copy and prep (IterFork)
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
 };
 
@@ -203,9 +200,6 @@ static void free_all(mppi_ctx* c) {
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->graph) cudaGraphExecDestroy(c->graph);
-    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
-    if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
 }
 
@@ -279,10 +273,6 @@ int mppi_create(const mppi_params* params, int device, void* cuda_stream, int32_
         if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaStreamCreate"));
         c->stream = c->own_stream;
     }
-    e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
-    if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "side stream / events"));
     const int K = params->K, T = params->T;
     PlanBuffers& b = c->b;
     b.n_wblk = (int)std::min<long long>((K + 255) / 256, 296);
@@ -390,12 +380,8 @@ static int enqueue(mppi_ctx* c, const PlanInputs& in, int has_table) {
     const SceneLayout L = make_layout(c->p.T, in.n_ref, in.n_circ);
     PlanConst pc = c->pc;
     pc.has_table = has_table;
-    IterFork fk;
-    fk.side = c->side;
-    fk.fork = c->ev_fork;
-    fk.join = c->ev_join;
     CK(launch_iteration(pc, L, c->b, in, c->group, c->threads, c->p.noise_bf16, c->stream,
-                        c->profiling ? c->ev : nullptr, c->profiling, &fk),
+                        c->profiling ? c->ev : nullptr, c->profiling),
        "kernel launch");
     return MPPI_OK;
 }
@@ -463,18 +449,12 @@ static int stage_host_inputs(mppi_ctx* c, const double* x0, const double* ref_xy
 // The whole host-buffer iteration (input copy, kernels, output and status copies) in
 // stream order; captured into a graph by mppi_plan.
 static cudaError_t plan_sequence(mppi_ctx* c, const PlanInputs& in, size_t n_in) {
+    cudaError_t e = cudaMemcpyAsync(c->d_in, c->h_in, n_in * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return e;
     const SceneLayout L = make_layout(c->p.T, in.n_ref, in.n_circ);
     PlanConst pc = c->pc;
     pc.has_table = in.centres ? 1 : 0;
-    // the input copy goes after the fork, so the noise runs beside the copy and prep
-    IterFork fk;
-    fk.side = c->side;
-    fk.fork = c->ev_fork;
-    fk.join = c->ev_join;
-    fk.h2d_src = c->h_in;
-    fk.h2d_dst = c->d_in;
-    fk.h2d_bytes = n_in * sizeof(double);
-    cudaError_t e = launch_iteration(pc, L, c->b, in, c->group, c->threads, c->p.noise_bf16, c->stream, nullptr, 1, &fk);
+    e = launch_iteration(pc, L, c->b, in, c->group, c->threads, c->p.noise_bf16, c->stream, nullptr);
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(c->h_out, c->d_out, c->out_elems * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return e;

@@ -132,26 +132,15 @@ struct PlanInputs {
     double* x_out;           // [T+1][4]
 };
 
-// The noise depends on nothing of the iteration's inputs, so it can run on a second stream beside
-// the input copy and prep: the iteration forks there (event fork) and joins back (event join)
-// before the rollout.  h2d_*: an optional input copy issued after the fork on the main stream.
-struct IterFork {
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
-    const void* h2d_src = nullptr;
-    void* h2d_dst = nullptr;
-    size_t h2d_bytes = 0;
-};
-
 // Launch the whole iteration (prep, noise, rollout, reductions, update) on a stream.
 // ev: optional array of N_KERNELS + 1 events; ev_mode 1 records them around every kernel
-// (per-kernel timing; with a fork, the noise stage is the part of the noise not hidden by
-// prep), 2 only ev[2] and ev[3] around the rollout (the rest stays chained).  fork: null runs
-// every kernel in line on st.
+// (per-kernel timing: the prep stage is the prep + noise launch, the noise stage the bf16
+// fix-up, the argmin stage empty since the rollout kernel ends with the argmin), 2 only ev[2]
+// and ev[3] around the rollout (the rest stays chained).
 constexpr int N_KERNELS = 7;   // prep, noise, rollout, argmin, weights, wsum, finalize
 cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
                              const PlanInputs& in, int group, int threads, int noise_bf16, cudaStream_t st,
-                             cudaEvent_t* ev = nullptr, int ev_mode = 1, const IterFork* fork = nullptr);
+                             cudaEvent_t* ev = nullptr, int ev_mode = 1);
 
 // prep + noise only (no change to the warm start or the iteration counter) and the
 // reset of the fields prep accumulates into; used by the autotuner.

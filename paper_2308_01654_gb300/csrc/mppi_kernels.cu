@@ -2,6 +2,7 @@
 //
 //   prep      reference polyline, obstacle circles and controls -> scene blob (local frame, binary32)
 //   noise     Philox4x32-10 + Box-Muller -> z[T][K]                    (Algorithm 1 GenerateRandomNoise)
+//             (prep and noise are one launch, their blocks side by side)
 //   rollout   fused Euler rollout of Eq. (5) + step costs of Eq. (12)-(18) -> S[K]
 //             with S_min and its index from the rollout's last block      (Algorithm 1, S_min)
 //   weights   w_k = exp(-(S_k - S_min) / lambda), eta partials in binary64  (Eq. (11))
@@ -66,28 +67,14 @@ static cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 bloc
 }
 
 // -----------------------------------------------------------------------------
-// prep: one pass over the inputs.  Positions are shifted into a frame centred on
-// (x0, y0) in binary64 before rounding, so binary32 keeps its resolution where
-// the rollouts happen.  One row of blocks per phase of prep_scene (blockIdx.y).
-// -----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) prep_kernel(PlanConst pc, SceneLayout L, PlanInputs in, PlanBuffers b) {
-    pdl_trigger();
-    prep_scene(pc, L, in, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, blockIdx.y);
-}
-
-// -----------------------------------------------------------------------------
 // noise: one thread per (step pair j, sample k); coalesced stores along k.  The
 // bfloat16 form stores the binary32 normals rounded and lists the pairs that lie within
 // the binary32 error bound of a rounding midpoint; noise_fix_kernel takes their rounding
 // again on the exact (binary64) normals, so the stored codes are those of the exact values.
 // -----------------------------------------------------------------------------
 template <bool BF16>
-__global__ void __launch_bounds__(256) noise_kernel(PlanConst pc, const DevState* st,
-                                                    typename NoiseT<BF16>::type* z, unsigned* fix_count,
-                                                    uint2* fix_list) {
-    pdl_wait();
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
+__device__ __forceinline__ void noise_pair(const PlanConst& pc, const DevState* st, typename NoiseT<BF16>::type* z,
+                                           unsigned* fix_count, uint2* fix_list, int k, int j) {
     if (k >= pc.K) return;
     const uint32_t it = (uint32_t)st->iter;
     const uint4 w = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)k, it, pc.session), make_uint2(pc.key0, pc.key1));
@@ -116,6 +103,31 @@ __global__ void __launch_bounds__(256) noise_kernel(PlanConst pc, const DevState
     }
 }
 
+// -----------------------------------------------------------------------------
+// prep + noise, the first launch of an iteration.  prep makes one pass over the inputs:
+// positions are shifted into a frame centred on (x0, y0) in binary64 before rounding, so
+// binary32 keeps its resolution where the rollouts happen.  Its blocks come first in the grid
+// (prep_x blocks for each phase of prep_scene), the noise blocks (nkb per step pair) after
+// them: prep needs the inputs and noise only the seed and the iteration counter, so the two
+// run side by side, and the next kernel chains to this one launch.  Launch bounds of the
+// noise (eight blocks of 256 per SM).
+// -----------------------------------------------------------------------------
+template <bool BF16>
+__global__ void __launch_bounds__(256, 8) prep_noise_kernel(PlanConst pc, SceneLayout L, PlanInputs in,
+                                                            PlanBuffers b, int prep_x, int nkb,
+                                                            typename NoiseT<BF16>::type* z) {
+    const int n_prep = prep_x * PREP_PHASES;
+    const int lin = (int)blockIdx.x;
+    if (lin < n_prep) {
+        pdl_trigger();
+        const int phase = lin / prep_x, bx = lin - phase * prep_x;
+        prep_scene(pc, L, in, b, bx * blockDim.x + threadIdx.x, prep_x * blockDim.x, phase);
+        return;
+    }
+    const int r = lin - n_prep, j = r / nkb, kb = r - j * nkb;
+    noise_pair<BF16>(pc, b.state, z, b.fix_count, b.fix_list, kb * blockDim.x + threadIdx.x, j);
+}
+
 // One warp per block and four blocks per SM, so the few binary64 Box-Muller pairs spread
 // over every SM's binary64 pipe.
 __global__ void __launch_bounds__(32) noise_fix_kernel(PlanConst pc, const DevState* st, __nv_bfloat162* z,
@@ -134,18 +146,30 @@ __global__ void __launch_bounds__(32) noise_fix_kernel(PlanConst pc, const DevSt
     }
 }
 
-static cudaError_t launch_noise(const PlanConst& pc, const PlanBuffers& b, int noise_bf16, cudaStream_t st) {
-    dim3 grid((pc.K + 255) / 256, (pc.T + 1) / 2);
-    if (noise_bf16) {
-        __nv_bfloat162* z = reinterpret_cast<__nv_bfloat162*>(b.z);
-        cudaError_t e = launch_chained(noise_kernel<true>, grid, dim3(256), 0, st, pc, (const DevState*)b.state, z,
-                                       b.fix_count, b.fix_list);
-        if (e != cudaSuccess) return e;
-        return launch_chained(noise_fix_kernel, dim3(4 * 152), dim3(32), 0, st, pc, (const DevState*)b.state, z,
-                              (const unsigned*)b.fix_count, (const uint2*)b.fix_list);
-    }
-    return launch_chained(noise_kernel<false>, grid, dim3(256), 0, st, pc, (const DevState*)b.state,
-                          reinterpret_cast<float2*>(b.z), (unsigned*)nullptr, (uint2*)nullptr);
+static cudaError_t launch_prep_noise_k(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
+                                       const PlanInputs& in, int noise_bf16, cudaStream_t st) {
+    int items = L.n_ref;
+    items = max(items, L.T);
+    items = max(items, L.n_circ);
+    if (in.centres) items = max(items, L.T * L.n_circ);
+    const int prep_x = min(max((items + 255) / 256, 1), 148);
+    const int nkb = (pc.K + 255) / 256, njp = (pc.T + 1) / 2;
+    const long long blocks = (long long)prep_x * PREP_PHASES + (long long)nkb * njp;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (noise_bf16)
+        prep_noise_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(pc, L, in, b, prep_x, nkb,
+                                                                  reinterpret_cast<__nv_bfloat162*>(b.z));
+    else
+        prep_noise_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(pc, L, in, b, prep_x, nkb,
+                                                                   reinterpret_cast<float2*>(b.z));
+    return cudaGetLastError();
+}
+
+// the bfloat16 form's fix-up of the listed pairs, chained after the prep + noise launch
+static cudaError_t launch_noise_fix(const PlanConst& pc, const PlanBuffers& b, cudaStream_t st) {
+    return launch_chained(noise_fix_kernel, dim3(4 * 152), dim3(32), 0, st, pc, (const DevState*)b.state,
+                          reinterpret_cast<__nv_bfloat162*>(b.z), (const unsigned*)b.fix_count,
+                          (const uint2*)b.fix_list);
 }
 
 __global__ void philox_kernel(uint2 key, const uint4* ctr, uint4* out, int n) {
@@ -373,16 +397,10 @@ cudaError_t launch_rollout(const PlanConst& pc, const SceneLayout& L, const Plan
 
 cudaError_t launch_prep_noise(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
                               const PlanInputs& in, int noise_bf16, cudaStream_t st) {
-    int items = L.n_ref;
-    items = max(items, L.T);
-    items = max(items, L.n_circ);
-    if (in.centres) items = max(items, L.T * L.n_circ);
-    const int blocks = min(max((items + 255) / 256, 1), 148);
-    prep_kernel<<<dim3(blocks, PREP_PHASES), 256, 0, st>>>(pc, L, in, b);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     if (b.fix_count && (e = cudaMemsetAsync(b.fix_count, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
-    return launch_noise(pc, b, noise_bf16, st);
+    if ((e = launch_prep_noise_k(pc, L, b, in, noise_bf16, st)) != cudaSuccess) return e;
+    return noise_bf16 ? launch_noise_fix(pc, b, st) : cudaSuccess;
 }
 
 // resets the per-iteration fields that prep accumulates into (after a prep without finalize)
@@ -399,7 +417,7 @@ cudaError_t launch_reset_state(DevState* st, cudaStream_t s) {
 
 cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
                              const PlanInputs& in, int group, int threads, int noise_bf16, cudaStream_t st,
-                             cudaEvent_t* ev, int ev_mode, const IterFork* fork) {
+                             cudaEvent_t* ev, int ev_mode) {
     // ev_mode 1: an event before the first kernel and after each (every boundary timed, none
     // chained); 2: only the two around the rollout (ev[2], ev[3]), the other kernels stay chained
     cudaError_t e;
@@ -413,29 +431,10 @@ cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const Pl
     };
     if (ev && ev_mode != 2 && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
     ++stage;
-    const bool forked = fork && fork->side;
-    if (forked) {
-        // noise (and the bf16 fix-up) on the side stream, after everything queued on st so far
-        if ((e = cudaEventRecord(fork->fork, st)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(fork->side, fork->fork, 0)) != cudaSuccess) return e;
-        if ((e = launch_noise(pc, b, noise_bf16, fork->side)) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(fork->join, fork->side)) != cudaSuccess) return e;
-    }
-    if (fork && fork->h2d_bytes &&
-        (e = cudaMemcpyAsync(fork->h2d_dst, fork->h2d_src, fork->h2d_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return e;
-    {
-        int items = L.n_ref;
-        items = max(items, L.T);
-        items = max(items, L.n_circ);
-        if (in.centres) items = max(items, L.T * L.n_circ);
-        const int blocks = min(max((items + 255) / 256, 1), 148);
-        prep_kernel<<<dim3(blocks, PREP_PHASES), 256, 0, st>>>(pc, L, in, b);
-        if ((e = mark()) != cudaSuccess) return e;
-    }
-    if (forked) e = cudaStreamWaitEvent(st, fork->join, 0);
-    else e = launch_noise(pc, b, noise_bf16, st);
-    if (e != cudaSuccess) return e;
+    // prep and noise in one launch (the "prep" stage), the bf16 fix-up chained after it (the "noise" stage)
+    if ((e = launch_prep_noise_k(pc, L, b, in, noise_bf16, st)) != cudaSuccess) return e;
+    if ((e = mark()) != cudaSuccess) return e;
+    if (noise_bf16 && (e = launch_noise_fix(pc, b, st)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
     if ((e = launch_rollout(pc, L, b, group, threads, noise_bf16, st)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;

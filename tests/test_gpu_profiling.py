@@ -22,7 +22,11 @@ def test_profiling_modes_time_the_kernels_and_leave_results_unchanged():
             out[mode] = (u, x)
             if mode == 1:
                 kt = pl.kernel_times()
-                assert set(kt) == set(mp.KERNELS) and all(v > 0.0 for v in kt.values())
+                assert set(kt) == set(mp.KERNELS)
+                # prep and noise are one launch and the rollout ends with the argmin: those two
+                # stages hold no kernel of their own (fp32 noise)
+                assert all(kt[k] > 0.0 for k in ("prep", "rollout", "weights", "wsum", "finalize"))
+                assert kt["noise"] >= 0.0 and kt["argmin"] >= 0.0
             elif mode == 2:
                 kt = pl.kernel_times()
                 assert kt["rollout"] > 0.0
