@@ -27,6 +27,10 @@ struct mppi_ctx {
     double* h_in = nullptr;      // pinned staging of the same layout
     double* h_out = nullptr;     // pinned staging of outputs
     DevState* h_state = nullptr; // pinned copy of the device record
+    // device addresses of the two pinned buffers: mppi_plan's finalize writes u*, x* and the
+    // record straight into host memory (no copy back)
+    double* h_out_dev = nullptr;
+    DevState* h_state_dev = nullptr;
     size_t in_elems = 0, out_elems = 0;
     int group = 1;
     int threads = 128;
@@ -329,6 +333,11 @@ int mppi_create(const mppi_params* params, int device, void* cuda_stream, int32_
         cudaGetLastError();
         return bail(fail(nullptr, MPPI_ERR_OOM, "pinned host allocation failed"));
     }
+    if (cudaHostGetDevicePointer((void**)&c->h_out_dev, c->h_out, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&c->h_state_dev, c->h_state, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(nullptr, MPPI_ERR_CUDA, "pinned host buffers are not mapped for the device"));
+    }
     DevState s0;
     memset(&s0, 0, sizeof(s0));
     s0.jkey = ~0ull;
@@ -454,11 +463,7 @@ static cudaError_t plan_sequence(mppi_ctx* c, const PlanInputs& in, size_t n_in)
     const SceneLayout L = make_layout(c->p.T, in.n_ref, in.n_circ);
     PlanConst pc = c->pc;
     pc.has_table = in.centres ? 1 : 0;
-    e = launch_iteration(pc, L, c->b, in, c->group, c->threads, c->p.noise_bf16, c->stream, nullptr);
-    if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(c->h_out, c->d_out, c->out_elems * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-    if (e != cudaSuccess) return e;
-    return cudaMemcpyAsync(c->h_state, c->b.state, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream);
+    return launch_iteration(pc, L, c->b, in, c->group, c->threads, c->p.noise_bf16, c->stream, nullptr);
 }
 
 int mppi_plan(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n_ref, const mppi_circle* circ,
@@ -470,13 +475,15 @@ int mppi_plan(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n_ref
     size_t n_in = 0;
     int rc = stage_host_inputs(c, x0, ref_xy, n_ref, circ, n_circ, centres, in, false, &n_in);
     if (rc != MPPI_OK) return rc;
+    // outputs and the record go straight to the pinned host buffers (written by finalize)
+    in.u_out = c->h_out_dev;
+    in.x_out = c->h_out_dev + 2 * (size_t)T;
+    in.state_out = c->h_state_dev;
     if (c->profiling) {
         CK(cudaMemcpyAsync(c->d_in, c->h_in, n_in * sizeof(double), cudaMemcpyHostToDevice, c->stream), "input copy");
         rc = enqueue(c, in, in.centres ? 1 : 0);
         if (rc != MPPI_OK) return rc;
-        CK(cudaMemcpyAsync(c->h_out, c->d_out, c->out_elems * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
-           "output copy");
-        rc = wait_status(c, info);
+        rc = wait_status(c, info, true);
     } else {
         // shape key: the graph bakes in sizes, the layout and the launch shape
         const long long key =

@@ -130,6 +130,7 @@ struct PlanInputs {
     int n_ref, n_circ;
     double* u_out;           // [T][2]
     double* x_out;           // [T+1][4]
+    DevState* state_out = nullptr;   // when set, finalize copies the device record here (pinned host)
 };
 
 // Launch the whole iteration (prep, noise, rollout, reductions, update) on a stream.

@@ -1384,6 +1384,16 @@ __device__ __forceinline__ void wsum_tile(const PlanConst& pc, const float4* ctl
 // so divisions are replaced by products with reciprocals formed once (1 / eta, 1 / 35,
 // 1 / dt, dt / L): each such product is within an ulp of the quotient.
 // -----------------------------------------------------------------------------
+// The device record into a host-mapped mirror (16-byte words), so a host-buffer iteration needs
+// no copy back of its status.
+__device__ __forceinline__ void copy_state(const DevState* st, DevState* out) {
+    if (!out) return;
+    const ulonglong2* src = reinterpret_cast<const ulonglong2*>(st);
+    ulonglong2* dst = reinterpret_cast<ulonglong2*>(out);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(DevState) / 16); ++i) dst[i] = src[i];
+}
+
 __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBuffers& b, const PlanInputs& in) {
     __shared__ double s_un[2 * 1024];
     __shared__ double s_us[2 * 1024];
@@ -1449,6 +1459,7 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
             st->flags = 0;
             st->moving = 0;
             st->jkey = ~0ull;
+            copy_state(st, in.state_out);
         }
         return;
     }
@@ -1547,6 +1558,7 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
         st->flags = 0;
         st->moving = 0;
         st->jkey = ~0ull;
+        copy_state(st, in.state_out);
     }
 }
 
