@@ -99,14 +99,16 @@ __device__ __forceinline__ __nv_bfloat16 bf16_from_f64(double z) {
     return __float2bfloat16_rn((float)__longlong_as_double((long long)b));
 }
 
-// True when a binary32 normal may sit on the other side of a bfloat16 rounding
-// midpoint than the exact normal: within the binary32 Box-Muller error bound
-// (4e-7 * max(1, |z|)) of the midpoint, or so small that the bound covers the spacing.
+// True when a binary32 normal may sit on the other side of a bfloat16 rounding midpoint than
+// the exact normal: within the binary32 Box-Muller error bound of the midpoint.  That bound is
+// relative (u = 2^-24): logf is within 1 ulp (2u relative) and the scaling by -2 is exact;
+// sqrtf halves that (u) and rounds (u); sincospif is within 1 ulp (2u) of an exact argument,
+// so relatively also next to its zeros; the product rounds (u).  In all |z - z_exact| <= 5u |z|
+// ~ 2.98e-7 |z| to first order, and the window is 3.2e-7 |z|.  (|z| is never below ~1e-10:
+// u0 <= 1 - 2^-24, and the sine and cosine of pi times an odd multiple of 2^-23 exceed 3e-7.)
 __device__ __forceinline__ bool near_bf16_midpoint(float z) {
-    const float az = fabsf(z);
-    if (az < 1e-4f) return true;
     const float mid = __uint_as_float((__float_as_uint(z) & 0xFFFF0000u) | 0x8000u);
-    return fabsf(z - mid) <= 4e-7f * fmaxf(1.0f, az);
+    return fabsf(z - mid) <= 3.2e-7f * fabsf(z);
 }
 
 // -----------------------------------------------------------------------------

@@ -23,7 +23,14 @@ def test_roofline_workload_full_parity(bf16):
     with mp.Planner(prob.params) as pl:
         u, x, info = pl.plan(prob.x0, prob.ref, prob.circles)
         S = pl.get_costs()
+        z = pl.get_noise() if bf16 else None
     orc = oracle.plan(prob)
+    if bf16:
+        # every one of the 26.2 million bfloat16 codes is the rounding of the exact normal
+        zo = oracle.noise(prob.params, info["iter"])
+        mism = int(np.count_nonzero(z.astype(np.float64) != zo))
+        assert mism == 0, mism
+        del z, zo
     rep = assert_costs(S, orc.S, orc.margin)
     assert argmin_ok(info["argmin"], orc.S)
     if info["argmin"] == orc.info.argmin:

@@ -56,16 +56,21 @@ def test_philox_words_bit_exact():
         np.testing.assert_array_equal(got[:512], exp)
 
 
-@pytest.mark.parametrize("K,T", [(1000, 7), (2048, 16), (3, 1)])
+@pytest.mark.parametrize("K,T", [(1000, 7), (2048, 16), (3, 1), (65536, 64)])
 def test_noise_matches_oracle(K, T):
     prob = sc.tiny(K=K, T=T)
     prob.params.update(seed=0xABCDEF12345, session=3)
     outs, z, _, _ = run_gpu(prob)
     zo = oracle.noise(prob.params, outs[0][2]["iter"])
-    # binary32 Box-Muller (logf, sqrtf, sincospif) against binary64: a few ulps of |z|, plus
-    # an absolute floor for values near zero where cos / sin cancel
+    # binary32 Box-Muller (logf, sqrtf, sincospif) against binary64: the error is relative to |z|
+    # (1 ulp for logf and for sincospif of an exact argument, rounding of sqrt and of the
+    # product: at most ~2.98e-7 |z| to first order), also next to the zeros of cos / sin.  The
+    # bfloat16 form's midpoint window relies on this bound (3.2e-7 |z|); the largest case holds
+    # 8.4 million normals.
     err = np.abs(z.astype(np.float64) - zo)
-    assert np.all(err <= 4e-7 * np.maximum(np.abs(zo), 1.0)), err.max()
+    rel = err / np.abs(zo)
+    assert np.all(err <= 3.2e-7 * np.abs(zo)), rel.max()
+    print(f"noise K={K} T={T}: largest relative error {rel.max():.3e} ({rel.max() / 2.0 ** -24:.2f} x 2^-24)")
 
 
 def test_bf16_noise_is_the_rounded_normal():
