@@ -96,6 +96,24 @@ def test_batch_agrees_with_the_single_plan_path():
         np.testing.assert_allclose(bpl.x, x, rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("K", [16384, 32768])
+def test_weighted_sum_step_tiles_do_not_change_the_update(K):
+    """The single-plan weighted sum tiles the steps by 2 (8 k-tiles) or 4 (16 k-tiles) at T = 100,
+    the batch engine always by 8: the per-step partial sums do not depend on the tiling, so the two
+    updates agree to the rounding of the normaliser (summed in a different order)."""
+    rng = np.random.Generator(np.random.PCG64(29))
+    p = sc.uneven_instance(rng, 0, seed=29)
+    p.params.update(K=K, T=100, session=7)
+    with batch_for([p]) as bp:
+        plans = plans_of([p])
+        bp.plan(plans)
+    with mp.Planner(p.params) as pl:
+        u, x, info = pl.plan(p.x0, p.ref, p.circles, p.centres)
+    assert plans[0].info.argmin == info["argmin"] and plans[0].info.s_min == info["s_min"]
+    np.testing.assert_allclose(plans[0].u, u, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(plans[0].x, x, rtol=1e-12, atol=1e-12)
+
+
 def test_batch_matches_the_oracle():
     probs = mixed_problems(n=6)
     with batch_for(probs) as bp:

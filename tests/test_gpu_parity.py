@@ -239,16 +239,20 @@ def test_device_entry_point_matches_host_entry_point():
 
 # ----------------------------------------------------------------------------- errors and state
 
-def test_non_finite_input_is_rejected_and_state_kept():
+@pytest.mark.parametrize("where", ["ref", "x0", "circles", "centres"])
+@pytest.mark.parametrize("value", [np.nan, np.inf, -np.inf])
+def test_non_finite_input_is_rejected_and_state_kept(where, value):
     prob = sc.single_plan()
     prob.params.update(K=256, T=10)
     with mp.Planner(prob.params) as pl:
         U0 = np.full((10, 2), 0.01)
         pl.set_controls(U0, 5)
-        bad = prob.ref.copy()
-        bad[3, 0] = np.nan
+        args = {"x0": prob.x0.copy(), "ref": prob.ref.copy(), "circles": prob.circles.copy(),
+                "centres": sc.predicted_centres(prob.circles, 10, prob.params["dt"])}
+        a = args[where]
+        a.flat[a.size // 2] = value
         with pytest.raises(mp.MppiError) as e:
-            pl.plan(prob.x0, bad, prob.circles)
+            pl.plan(args["x0"], args["ref"], args["circles"], args["centres"])
         assert e.value.status == -1
         U, it = pl.get_controls()
         np.testing.assert_array_equal(U, U0)
