@@ -107,7 +107,8 @@ typedef struct {
     int32_t group;              /* lanes per sample in the rollout kernel: 0 = choose; 1,2,4,8,16,32 = the
                                    lanes split the search and obstacle work of each step; -2,-4,-8,-16 = that
                                    many lanes split the steps (lane p evaluates the cost of steps p, p+|g|, ...) */
-    int32_t block;              /* threads per block of the rollout kernel: 0 = choose, else a multiple of 32 up to 448 */
+    int32_t block;              /* threads per block of the rollout kernel: 0 = choose, else a multiple of 32 up to
+                                   896 (the batch engine and the server take at most 448) */
     int32_t model;              /* 0: state (x, y, yaw, v), control (a, delta) with delta the steering angle;
                                    1: the steering-rate form of Eq. (5): state (x, y, yaw, v, delta),
                                    control (a, omega), delta advanced by omega * dt.  Model 1 makes x0
@@ -172,7 +173,7 @@ int mppi_plan_device(mppi_ctx* ctx, const double* d_x0, const double* d_ref_xy, 
 
 /* Autotuner: times the rollout kernel for every lanes-per-sample group (1..32, -2..-16) and
    block size (64, 128, 256, and sizes that spread the lanes evenly over the SMs with
-   1 to 4 resident blocks each) on the given inputs (host arrays, as for mppi_plan) and
+   1 to 4 resident blocks each, up to 896 threads) on the given inputs (host arrays, as for mppi_plan) and
    keeps the fastest for this context; *group and *block receive the choice (either
    may be NULL).  The warm start and the iteration counter are not changed.  With a
    cache_path (may be NULL) the choice is looked up first and stored after tuning,

@@ -113,7 +113,7 @@ static int check_params(const mppi_params* p, std::string& why) {
         return MPPI_ERR_ARG;
     }
     if (!(p->block == 0 || valid_block(p->block))) {
-        why = "block must be 0 or a multiple of 32 in [32, 448]";
+        why = "block must be 0 or a multiple of 32 in [32, 896]";
         return MPPI_ERR_ARG;
     }
     return MPPI_OK;
@@ -387,7 +387,7 @@ static int check_sizes(mppi_ctx* c, int32_t n_ref, int32_t n_circ) {
     const SceneLayout L = make_layout(c->p.T, n_ref, n_circ);
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-    if ((int)rollout_smem_bytes(L) + 1024 > max_smem)
+    if ((int)rollout_smem_bytes(L, c->threads, c->p.model == 1) + 1024 > max_smem)
         return fail(c, MPPI_ERR_CAPACITY, "reference + circles + horizon exceed shared memory");
     return MPPI_OK;
 }
@@ -564,7 +564,7 @@ static std::string gpu_name(int device) {
 
 static std::string tune_key(mppi_ctx* c, int n_ref, int n_circ) {
     char buf[256];
-    snprintf(buf, sizeof(buf), "%s|%d|%d|%d|%d|%d|r2", gpu_name(c->device).c_str(), c->p.K, c->p.T, n_ref, n_circ,
+    snprintf(buf, sizeof(buf), "%s|%d|%d|%d|%d|%d|r3", gpu_name(c->device).c_str(), c->p.K, c->p.T, n_ref, n_circ,
              c->p.noise_bf16);
     return buf;
 }
@@ -620,7 +620,7 @@ int mppi_autotune(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n
         int bg = c->group, bt = c->threads;
         int n_sm = 0;
         CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
-        const size_t smem = rollout_smem_bytes(L);
+        const bool model1 = c->p.model == 1;
         const bool ext = c->p.model == 1 || c->p.cost_to_go != 0;
         // lanes per sample: > 0 split the work of each step, < 0 split the steps
         const int groups[] = {1, 2, 4, 8, 16, 32, -2, -4, -8, -16};
@@ -639,13 +639,16 @@ int mppi_autotune(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n
                 long long per = (lanes + (long long)n_sm * m - 1) / ((long long)n_sm * m);
                 int th = (int)(((per + 31) / 32) * 32);
                 if (th < 32 || th > MAX_ROLLOUT_THREADS) continue;
-                if (rollout_max_blocks_per_sm(G, th, c->p.noise_bf16, smem, ext) < m) continue;
+                if (rollout_max_blocks_per_sm(G, th, c->p.noise_bf16, rollout_smem_bytes(L, th, model1), ext) < m)
+                    continue;
                 bool dup = false;
                 for (int i = 0; i < nc; ++i) dup |= cand[i] == th;
                 if (!dup) cand[nc++] = th;
             }
             for (int bi = 0; bi < nc && err == cudaSuccess; ++bi) {
-                if (rollout_max_blocks_per_sm(G, cand[bi], c->p.noise_bf16, smem, ext) < 1) continue;
+                if (rollout_max_blocks_per_sm(G, cand[bi], c->p.noise_bf16, rollout_smem_bytes(L, cand[bi], model1),
+                                              ext) < 1)
+                    continue;
                 err = launch_rollout(pc, L, c->b, G, cand[bi], c->p.noise_bf16, c->stream);  // warm-up
                 if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
                 for (int r = 0; r < 3 && err == cudaSuccess; ++r)

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256) batch_noise_kernel(BatchArgs a) {
 
 // G lanes per sample; TIME: they split the steps, else the work of each step (rollout_sample).
 template <int G, bool TIME, bool BF16>
-__global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 2) batch_rollout_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(BATCH_MAX_THREADS, 2) batch_rollout_kernel(BatchArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long bar;
     __shared__ PlanConst s_pc;
@@ -445,7 +445,7 @@ int mppi_batch_create(int32_t max_slots, int32_t max_batch, int64_t max_samples,
     B->max_tiles = max_samples / 16 + max_batch;
     const SceneLayout Lmax = make_layout(max_T, max_ref, max_circ);
     B->max_scene = up((size_t)Lmax.bytes);
-    B->rollout_smem = up(rollout_smem_bytes(Lmax));   // blob and the boxes built after it
+    B->rollout_smem = up(rollout_smem_bytes(Lmax, BATCH_MAX_THREADS, false));   // blob and the boxes built after it
     B->max_in = 4 + 2 * (size_t)max_ref + 5 * (size_t)max_circ + 2 * (size_t)max_T * max_circ;
     B->max_out = out_elems(max_T);
     auto bail = [&](int st) {
@@ -774,7 +774,7 @@ int mppi_batch_autotune(mppi_batch* B, mppi_request* req, int32_t n, int32_t* gr
     float best = INFINITY;
     int bg = saveG, bt = saveT;
     const int groups[] = {1, 2, 4, 8, 16, 32, -2, -4, -8};
-    const int sizes[] = {64, 128, 256, MAX_ROLLOUT_THREADS};
+    const int sizes[] = {64, 128, 256, BATCH_MAX_THREADS};
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0), "cudaEventCreate");
     BCK(cudaEventCreate(&e1), "cudaEventCreate");
@@ -840,7 +840,7 @@ int mppi_batch_set_launch(mppi_batch* B, int32_t group, int32_t block) {
 #define CASE(gv, g, time) known |= group == gv;
     MPPI_BATCH_GROUPS(CASE)
 #undef CASE
-    if (!known || block < 32 || block > MAX_ROLLOUT_THREADS || block % 32 != 0 || block / lanes_of(group) < 16)
+    if (!known || block < 32 || block > BATCH_MAX_THREADS || block % 32 != 0 || block / lanes_of(group) < 16)
         return bfail(B, MPPI_ERR_ARG, "group must be 1..32 or -2, -4, -8; block a multiple of 32 up to 448 with "
                                       "at least 16 samples per block");
     for (auto& p : B->pipes)

@@ -6,9 +6,14 @@
 
 namespace mppi {
 
-// Largest block of the single-plan rollout kernel: it is compiled for two such blocks per
-// SM (at most 72 registers a thread), so one wave holds 896 lanes per SM.
-constexpr int MAX_ROLLOUT_THREADS = 448;
+// Largest block of the single-plan rollout kernel: it is compiled for 896 lanes per SM (at
+// most 72 registers a thread), as one block of 896 or several smaller ones.  One block per SM
+// matters: two co-resident blocks of one wave do not progress alike (the second ran ~16 %
+// slower), and the second then finished alone at half occupancy.
+constexpr int MAX_ROLLOUT_THREADS = 896;
+
+// Largest block of the batched planner's rollout kernel (two per SM).
+constexpr int BATCH_MAX_THREADS = 448;
 
 // Per-context device record: iteration counter, status and the reduction results.
 struct __align__(16) DevState {
@@ -115,9 +120,11 @@ __host__ __device__ inline size_t block_extra_bytes(const SceneLayout& L) {
 }
 
 // Per-thread slots after the block's extras: the compensated steering angle of the
-// steering-rate model (float2 per thread, MAX_ROLLOUT_THREADS threads at most), kept out of
-// the registers of the other model.
-__host__ __device__ inline size_t steer_slots_bytes() { return (size_t)8 * MAX_ROLLOUT_THREADS; }
+// steering-rate model (float2 per thread of the block), kept out of the registers of the
+// other model; none for the 4-state model.
+__host__ __device__ inline size_t steer_slots_bytes(int threads, bool model1) {
+    return model1 ? (size_t)8 * threads : 0;
+}
 
 // Capacity of the deferred bfloat16 rounding list (pairs beyond it are decided in place).
 constexpr unsigned NOISE_FIX_CAP = 1u << 16;
@@ -160,7 +167,9 @@ cudaError_t launch_rollout(const PlanConst& pc, const SceneLayout& L, const Plan
 cudaError_t launch_rollout_stats(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int noise_bf16,
                                  cudaStream_t st);
 
-size_t rollout_smem_bytes(const SceneLayout& L);
+// Dynamic shared memory of a rollout block: the staged blob, the extras the block builds and
+// the steering slots (threads of the block; model1: the steering-rate model).
+size_t rollout_smem_bytes(const SceneLayout& L, int threads, bool model1);
 
 // Resident rollout blocks per SM for a launch shape (0 if it cannot launch).
 // ext: the steering-rate model or the cost-to-go form is on (PlanConst model / cost_to_go)

@@ -44,8 +44,8 @@ SceneLayout make_layout(int T, int n_ref, int n_circ) {
 }
 
 // the staged blob and what each block builds after it (block_extra_bytes)
-size_t rollout_smem_bytes(const SceneLayout& L) {
-    return (size_t)L.bytes + block_extra_bytes(L) + steer_slots_bytes();
+size_t rollout_smem_bytes(const SceneLayout& L, int threads, bool model1) {
+    return (size_t)L.bytes + block_extra_bytes(L) + steer_slots_bytes(threads, model1);
 }
 
 // A launch chained to the previous kernel on the stream (programmatic stream serialisation,
@@ -178,7 +178,7 @@ __global__ void philox_kernel(uint2 key, const uint4* ctr, uint4* out, int n) {
 }
 
 template <int G, bool TIME, bool BF16, bool STATS, bool EXT>
-__global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 2) rollout_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
+__global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 1) rollout_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
                                                         const typename NoiseT<BF16>::type* __restrict__ z) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long bar;
@@ -309,18 +309,32 @@ static cudaError_t launch_wsum(const PlanConst& pc, const SceneLayout& L, const 
         default: return cudaErrorInvalidValue;
     }
 }
+// Opt an instantiation of the rollout kernel in to the device's whole shared memory per block,
+// once: every launch and occupancy query then passes its own size (which depends on the block
+// for the steering-rate model), and none lowers the limit under another.
+template <int G, bool TIME, bool BF16, bool STATS, bool EXT>
+static cudaError_t allow_rollout_smem() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, rollout_kernel<G, TIME, BF16, STATS, EXT>);
+    // the dynamic part may take what the kernel's static shared memory leaves
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(rollout_kernel<G, TIME, BF16, STATS, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
+    done = e == cudaSuccess;
+    return e;
+}
+
 template <int G, bool TIME, bool BF16, bool STATS, bool EXT>
 static cudaError_t launch_rollout_t(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int threads,
                                     cudaStream_t st) {
-    const size_t smem = rollout_smem_bytes(L);
-    static int configured_smem = -1;
-    if (configured_smem < (int)smem) {
-        cudaError_t e = cudaFuncSetAttribute(rollout_kernel<G, TIME, BF16, STATS, EXT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(smem < 48 * 1024 ? 48 * 1024 : smem));
-        if (e != cudaSuccess) return e;
-        configured_smem = (int)(smem < 48 * 1024 ? 48 * 1024 : smem);
-    }
+    const size_t smem = rollout_smem_bytes(L, threads, pc.model == 1);
+    cudaError_t e = allow_rollout_smem<G, TIME, BF16, STATS, EXT>();
+    if (e != cudaSuccess) return e;
     const long long total = (long long)pc.K * G;
     const int blocks = (int)((total + threads - 1) / threads);
     return launch_chained(rollout_kernel<G, TIME, BF16, STATS, EXT>, dim3(blocks), dim3(threads), smem, st, pc, L, b,
@@ -347,9 +361,7 @@ static cudaError_t launch_rollout_b(const PlanConst& pc, const SceneLayout& L, c
 template <int G, bool TIME, bool BF16, bool EXT>
 static int max_blocks_t(int threads, size_t smem) {
     int n = 0;
-    if (cudaFuncSetAttribute(rollout_kernel<G, TIME, BF16, false, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(smem < 48 * 1024 ? 48 * 1024 : smem)) != cudaSuccess)
-        return 0;
+    if (allow_rollout_smem<G, TIME, BF16, false, EXT>() != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_kernel<G, TIME, BF16, false, EXT>, threads, smem) !=
         cudaSuccess)
         return 0;

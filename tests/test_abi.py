@@ -67,7 +67,7 @@ def test_status_strings():
 
 @pytest.mark.parametrize("bad", [dict(K=0), dict(T=0), dict(T=5000), dict(dt=0.0), dict(lam=-1.0),
                                  dict(n_ego=9), dict(sigma=[-0.1, 0.1]), dict(group=3), dict(group=-3), dict(group=-32),
-                                 dict(block=100), dict(block=480), dict(block=1024)])
+                                 dict(block=100), dict(block=928), dict(block=1024)])
 def test_invalid_params_are_rejected_before_any_cuda_call(bad):
     from paper_2308_01654_gb300 import scenarios
     p = scenarios.default_params(64, 10, 0.05)
