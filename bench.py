@@ -8,10 +8,17 @@ weights, weighted update, Savitzky-Golay smoothing, x* rollout, warm start.
 
 Metric: rollout-steps/s (K*T per iteration / iteration time), higher is better.
   value     device time with inputs resident in HBM (CUDA events on the planner's
-            stream, L2 flushed between steps by writing a 256 MB buffer)
-  e2e       the same metric through mppi_plan() with host buffers: input H2D and
-            output D2H copies inside the timed region
-  roofline  the rollout kernel (the dominant kernel) against the FP32-pipe peak
+            stream, L2 flushed between steps by writing a 256 MB buffer); the planner
+            records two more events around the rollout kernel in each timed step,
+            which end the chaining of its launch with the neighbouring kernels
+            (a few microseconds per step)
+  e2e       the same metric through mppi_plan() with host buffers: the input H2D
+            copy and the outputs (written by the last kernel into pinned host memory)
+            inside the timed region
+  roofline  the rollout kernel (the dominant kernel) against the FP32-pipe peak,
+            its duration from those two events
+  kernel_ms per-kernel times from three untimed steps with an event at every kernel
+            boundary
   cpu_baseline  the FP64 oracle on the host cores over a bounded sample
 N > 1 (torchrun): every rank runs an independent planner on its own GPU (weak
 scaling, no collective on the data path); value = all ranks' rollout-steps / the
