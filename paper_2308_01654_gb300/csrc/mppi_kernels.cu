@@ -10,6 +10,8 @@
 //   finalize  u + du, clamp, Savitzky-Golay (Eq. (19)), clamp, x* by prefix scans, warm start
 #include <math.h>
 
+#include <atomic>
+
 #include "mppi_device.cuh"
 #include "mppi_internal.h"
 #include "mppi_iter.cuh"
@@ -314,8 +316,8 @@ static cudaError_t launch_wsum(const PlanConst& pc, const SceneLayout& L, const 
 // for the steering-rate model), and none lowers the limit under another.
 template <int G, bool TIME, bool BF16, bool STATS, bool EXT>
 static cudaError_t allow_rollout_smem() {
-    static bool done = false;
-    if (done) return cudaSuccess;
+    static std::atomic<bool> done{false};   // contexts may be driven from several host threads
+    if (done.load(std::memory_order_acquire)) return cudaSuccess;
     int dev = 0, optin = 0;
     cudaFuncAttributes fa{};
     cudaError_t e = cudaGetDevice(&dev);
@@ -325,7 +327,7 @@ static cudaError_t allow_rollout_smem() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(rollout_kernel<G, TIME, BF16, STATS, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  optin - (int)fa.sharedSizeBytes);
-    done = e == cudaSuccess;
+    if (e == cudaSuccess) done.store(true, std::memory_order_release);
     return e;
 }
 
