@@ -9,6 +9,8 @@ import os
 import re
 import subprocess
 
+import numpy as np
+
 import pytest
 
 import paper_2308_01654_gb300 as mp
@@ -88,3 +90,18 @@ def test_no_cpu_fallback_without_a_gpu():
     with pytest.raises(mp.MppiError) as e:
         mp.Planner(scenarios.default_params(64, 10, 0.05))
     assert e.value.status == -3
+
+
+def test_array_addresses_passed_to_the_library():
+    """The binding passes arrays as void* addresses taken through the buffer protocol (read-only
+    and empty arrays through ndarray.ctypes): the address must be the array's data pointer."""
+    a = np.arange(12, dtype=np.float64).reshape(6, 2)
+    ro = np.arange(5, dtype=np.float64)
+    ro.setflags(write=False)
+    for arr in (a, ro, np.empty((0, 5)), np.zeros(7, dtype=np.float32), np.zeros(3, dtype=np.uint32), a[2:]):
+        assert mp._dp(arr) == arr.ctypes.data
+    assert mp._dp(None) is None
+    # the request record's pointer fields take the same addresses
+    r = mp.MppiRequest()
+    r.x0, r.ref_xy = mp._dp(a), mp._dp(ro)
+    assert r.x0 == a.ctypes.data and r.ref_xy == ro.ctypes.data
