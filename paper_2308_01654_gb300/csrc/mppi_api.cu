@@ -202,8 +202,8 @@ PlanConst make_const_shared(const mppi_params& p) { return make_const(p); }
 
 static void free_all(mppi_ctx* c) {
     PlanBuffers& b = c->b;
-    void* dev[] = {b.state, b.scene, b.table, b.z, b.S, b.w, b.eta_part, b.kmin_part, b.du_part, b.du, b.tt_count, b.U, b.stats, b.fix_count, b.fix_list, b.ctg_prefix, b.wt,
-                   b.eta_t, c->d_in, c->d_out};
+    void* dev[] = {b.state, b.scene, b.table, b.z, b.S, b.w, b.eta_part, b.kmin_part, b.du_part, b.du,
+                   b.tt_count, b.U, b.stats, b.fix_count, b.fix_list, b.ctg_prefix, b.wt, b.eta_t, c->d_in, c->d_out};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_in) cudaFreeHost(c->h_in);
