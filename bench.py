@@ -19,7 +19,16 @@ Metric: rollout-steps/s (K*T per iteration / iteration time), higher is better.
             its duration from those two events
   kernel_ms per-kernel times from three untimed steps with an event at every kernel
             boundary
-  cpu_baseline  the FP64 oracle on the host cores over a bounded sample
+  cpu_baseline  the FP64 oracle on the host cores over a bounded sample (all cores, and a
+            single-thread row), with the host CPU model
+  error_vs_oracle  the CUDA path against that oracle run on the same K-sample: every
+            sample cost, the argmin, u* and x*
+  bf16_noise  the same workload with bfloat16-stored noise (device-timed), with its
+            error against the oracle on the same codes and on the unrounded noise
+  systems   the batched form (256 uneven plans per submission against the plain
+            per-plan loop) and the serving form (512 sessions, Poisson arrivals at
+            2000 and 8000 plans/s, p50/p99 latency against the plain FIFO loop), in
+            shortened runs; --no-systems skips these and bf16_noise
 N > 1 (torchrun): every rank runs an independent planner on its own GPU (weak
 scaling, no collective on the data path); value = all ranks' rollout-steps / the
 slowest rank's time.
@@ -262,7 +271,7 @@ def oracle_sample(prob, seconds: float):
     return k
 
 
-def time_oracle(prob, k_sample: int):
+def time_oracle(prob, k_sample: int, want_result: bool = False):
     import oracle
     q = prob.copy()
     q.params["K"] = k_sample
@@ -270,7 +279,70 @@ def time_oracle(prob, k_sample: int):
     r = oracle.plan(q)
     el = time.perf_counter() - t
     assert r.rc == 0
-    return el
+    return (el, r) if want_result else el
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the CPU-baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline_record(prob, seconds: float):
+    """The oracle as it stands on the host cores: one full FP64 iteration on a K-sample of the
+    workload with every core (OpenMP over samples), and a smaller one on a single thread.
+    Returns (record, oracle result of the all-cores run) - the result doubles as the reference
+    of the error-vs-oracle check."""
+    import oracle
+    T = prob.T
+    k_s = oracle_sample(prob, seconds)
+    el, r = time_oracle(prob, k_s, want_result=True)
+    cores = oracle.num_threads()
+    rec = {"value": k_s * T / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"one full FP64 iteration at K={k_s} of the same workload (T={T}), {el:.1f} s",
+           "cpu_model": cpu_model()}
+    k_1 = max(16, int(k_s / max(cores, 1) * 0.5))
+    oracle.set_num_threads(1)
+    try:
+        el1 = time_oracle(prob, k_1)
+    finally:
+        oracle.set_num_threads(cores)
+    rec["single_thread"] = {"value": k_1 * T / el1, "unit": UNIT, "cores": 1,
+                            "sample": f"one full FP64 iteration at K={k_1}, {el1:.1f} s"}
+    return rec, r, k_s
+
+
+def error_vs_oracle(mp, prob, k: int, orc, local: int, params=None) -> dict:
+    """The CUDA path against the FP64 oracle on the same workload cut to K = k samples (the noise
+    of sample j does not depend on K): every sample cost, the argmin, u* and x* of one iteration
+    from a zero warm start."""
+    import numpy as np
+    p = dict(prob.params if params is None else params, K=int(k))
+    with mp.Planner(p, device=local) as pl:
+        u, x, info = pl.plan(prob.x0, prob.ref, prob.circles, prob.centres)
+        S = pl.get_costs()
+    rel = np.abs(S - orc.S) / np.maximum(np.abs(orc.S), 1.0)
+    order = np.argsort(orc.S, kind="stable")
+    s1 = orc.S[order[0]]
+    near = set(np.nonzero(orc.S - s1 <= 1e-4 * max(abs(s1), 1.0))[0].tolist())
+    return {"samples": int(k), "max_rel_S": float(rel.max()), "median_rel_S": float(np.median(rel)),
+            "argmin_ok": bool(info["argmin"] in near), "max_abs_du_star": float(np.abs(u - orc.u_star).max()),
+            "max_abs_dx_star": float(np.abs(x - orc.x_star).max()),
+            "tolerance": {"S_rel": 1e-4, "u_abs": 1e-4, "x_abs": 1e-4}}
 
 
 # ------------------------------------------------------------------------ the GPU arm
@@ -414,34 +486,101 @@ def run_gpu(args, world, rank, local):
         "kernel_ms": kmean, "kernel_ms_note": "untimed steps with an event at every kernel boundary (unchained)",
         "clocks": clocks,
     }
+    pl.close()
     if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.quick):
-        import oracle
-        k_s = oracle_sample(prob, args.cpu_seconds)
-        el = time_oracle(prob, k_s)
-        out["cpu_baseline"] = {"value": k_s * T / el, "unit": UNIT, "cores": oracle.num_threads(),
-                               "kind": "oracle",
-                               "sample": f"one full FP64 iteration at K={k_s} of the same workload (T={T}), "
-                                         f"{el:.1f} s"}
+        rec, orc, k_s = cpu_baseline_record(prob, args.cpu_seconds)
+        out["cpu_baseline"] = rec
+        out["error_vs_oracle"] = error_vs_oracle(mp, prob, k_s, orc, local)
+    if args.workload == "roofline" and not (args.quick or args.no_systems):
+        # the other forms the metric names, shortened so the default run stays within minutes
+        out["bf16_noise"] = bf16_report(args, world, rank, local)
+        out["systems"] = {
+            "batched": batched_report(args, world, rank, local, steps=5),
+            "serving": serving_report(args, world, rank, local, rate=args.rate, warm=1.0, meas=3.0),
+            "serving_saturated": serving_report(args, world, rank, local, rate=4.0 * args.rate, warm=1.0,
+                                                meas=2.0),
+            "note": ("at the 2000 plans/s offered load both the server and the plain loop keep up, so "
+                     "plans/s match and the server's gain is latency; the plans/s advantage appears above "
+                     "the plain loop's saturation point (serving_saturated)"),
+        }
     if rank == 0:
         print(json.dumps(out), flush=True)
-    pl.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def bf16_report(args, world, rank, local, steps: int = 10) -> dict:
+    """The roofline workload with the noise stored as bfloat16 (the precision form): device-timed
+    rollout-steps/s, and its error against the FP64 oracle on a K-sample, both on the same bf16
+    codes (the same method) and against the unrounded FP64 noise."""
+    import torch
+
+    import paper_2308_01654_gb300 as mp
+    from paper_2308_01654_gb300 import scenarios
+    dev = torch.device("cuda", local)
+    prob = scenarios.roofline(bf16=True)
+    prob.params["session"] = rank_session(rank)
+    K, T = prob.K, prob.T
+    stream = torch.cuda.Stream(device=dev)
+    with mp.Planner(prob.params, device=local, stream=stream.cuda_stream) as pl:
+        group, block = pl.autotune(prob.x0, prob.ref, prob.circles, prob.centres, cache_path=args.tune_cache)
+        x0 = torch.tensor(prob.x0, dtype=torch.float64, device=dev)
+        ref = torch.tensor(prob.ref, dtype=torch.float64, device=dev)
+        circ = torch.tensor(prob.circles, dtype=torch.float64, device=dev)
+        u_out = torch.empty((T, 2), dtype=torch.float64, device=dev)
+        x_out = torch.empty((T + 1, 4), dtype=torch.float64, device=dev)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(max(3, args.warmup)):
+                flush.zero_()
+                pl.plan_device(x0, ref, circ, None, u_out, x_out)
+            pl.sync()
+            ms = []
+            for _ in range(steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pl.plan_device(x0, ref, circ, None, u_out, x_out)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        pl.sync()
+    (m,) = max_over_ranks([statistics.mean(ms)], world, dev)
+    rec = {"value": weak_value(K * T, world, m * 1e-3), "unit": UNIT, "ms_per_step": m, "steps": steps,
+           "noise_bytes_per_rollout_step": 4, "rollout_launch": launch_desc(group, block)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        k = 2048
+        q = prob.copy()
+        q.params["K"] = k
+        rec["error_vs_oracle_same_codes"] = error_vs_oracle(mp, prob, k, oracle.plan(q), local)
+        rec["error_vs_oracle_unrounded"] = error_vs_oracle(
+            mp, prob, k, oracle.plan(q, params=dict(q.params, noise_bf16=0)), local)
+    return rec
 
 
 # ------------------------------------------------------------------------ batched uneven plans
 
 def run_batched(args, world, rank, local):
     """256 uneven plans per submission through mppi_batch_plan, against the plain per-plan loop."""
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    out = batched_report(args, world, rank, local, steps=args.steps, full_line=True)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def batched_report(args, world, rank, local, steps: int, full_line: bool = False) -> dict:
     import numpy as np
     import torch
 
     import paper_2308_01654_gb300 as mp
     from paper_2308_01654_gb300 import scenarios
-
-    torch.cuda.set_device(local)
-    if world > 1:
-        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     probs = scenarios.batched(seed=0, n=args.batch_size)
     for p in probs:
         p.params["session"] = rank_session(rank, int(p.params["session"]))
@@ -467,11 +606,11 @@ def run_batched(args, world, rank, local):
     barrier()
     lat = []
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         a = time.perf_counter()
         bp.plan(plans, reqs)
         lat.append(time.perf_counter() - a)
-    t_batch = (time.perf_counter() - t0) / args.steps
+    t_batch = (time.perf_counter() - t0) / steps
     barrier()
     bad = sum(p.info.n_finite == 0 for p in plans)
     bp.close()
@@ -482,7 +621,7 @@ def run_batched(args, world, rank, local):
         pl.plan(p.x0, p.ref, p.circles, p.centres)
     barrier()
     t0 = time.perf_counter()
-    reps = max(1, min(args.steps, 3))
+    reps = max(1, min(steps, 3))
     for _ in range(reps):
         for pl, p in zip(ctxs, probs):
             pl.plan(p.x0, p.ref, p.circles, p.centres)
@@ -490,22 +629,25 @@ def run_batched(args, world, rank, local):
     for pl in ctxs:
         pl.close()
     t_batch, t_plain = max_over_ranks([t_batch, t_plain], world, "cuda")
-    out = {"metric": f"plans/s ({n} uneven plans per submission, batched)", "value": weak_value(n, world, t_batch),
-           "unit": "plans/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32+f64-reduce", "data": "synthetic (uneven plans: K in 2^10..2^14, T 30..150, 0..32 obstacles)",
-           "config": {"workload": f"batched: {n} plans, sum K = {sum_k}, sum K*T = {sum_kt}",
-                      "rollout_launch": launch_desc(group, block),
-                      "timing": "wall clock of mppi_batch_plan (host packing, H2D, graph, D2H, unpacking)"},
+    rec = {"value": weak_value(n, world, t_batch), "unit": "plans/s", "steps": steps,
+           "workload": f"batched: {n} uneven plans per submission (K 2^10..2^14, T 30..150, 0..32 obstacles), "
+                       f"sum K = {sum_k}, sum K*T = {sum_kt}",
+           "rollout_launch": launch_desc(group, block),
+           "timing": "wall clock of mppi_batch_plan (host packing, H2D, graph, D2H, unpacking)",
            "rollout_steps_per_s": world * sum_kt / t_batch,
            "submission_ms": {"p50": float(np.percentile(lat, 50)) * 1e3, "p99": float(np.percentile(lat, 99)) * 1e3},
            "plain_per_plan_loop": {"value": world * n / t_plain, "unit": "plans/s", "ms_per_pass": t_plain * 1e3,
                                    "rollout_steps_per_s": world * sum_kt / t_plain},
            "speedup_vs_plain": t_plain / t_batch, "plans_without_finite_cost": int(bad)}
-    if rank == 0:
-        print(json.dumps(out), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    if not full_line:
+        return rec
+    return {"metric": f"plans/s ({n} uneven plans per submission, batched)", "value": rec["value"],
+            "unit": "plans/s", "n_gpus": world, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64-reduce", "data": "synthetic (uneven plans: K in 2^10..2^14, T 30..150, 0..32 obstacles)",
+            "config": {"workload": rec["workload"], "rollout_launch": rec["rollout_launch"], "timing": rec["timing"]},
+            **{k: rec[k] for k in ("rollout_steps_per_s", "submission_ms", "plain_per_plan_loop", "speedup_vs_plain",
+                                   "plans_without_finite_cost")}}
 
 
 # ------------------------------------------------------------------------ closed loop
@@ -603,24 +745,38 @@ def serving_trace(sessions, rate: float, seconds: float, seed: int = 5, variants
 
 def run_serving(args, world, rank, local):
     """Continuous batching of 512 sessions at a Poisson 2000 plans/s against the plain FIFO loop."""
+    import torch
+    torch.cuda.set_device(local)
+    dist_init(world, local)
+    rec = serving_report(args, world, rank, local, rate=args.rate, warm=args.serve_warmup_s, meas=args.serve_seconds)
+    out = {"metric": f"served plans/s ({args.sessions} sessions, Poisson {args.rate:.0f} plans/s offered)",
+           "value": rec["value"], "unit": "plans/s", "n_gpus": world, "steps": rec["requests"], "warmup": 0,
+           "ms_per_step": rec["latency_ms"]["p50"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64-reduce", "data": "synthetic sessions (K 2^10..2^14, T 30..150, 0..32 obstacles)",
+           "config": {"workload": rec["workload"], "pipelines": args.pipelines, "max_wait_us": args.max_wait_us},
+           **{k: rec[k] for k in ("latency_ms", "server", "plain_per_plan_loop")}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    dist_done(world)
+
+
+def serving_report(args, world, rank, local, rate: float, warm: float, meas: float) -> dict:
+    """One Poisson trace at `rate` plans/s through the server and through the plain FIFO loop
+    (one context per session, requests one at a time in arrival order).  Latency = completion -
+    arrival; plans/s = completions inside the measured window.  Every request must complete."""
     import queue as queue_mod
-    import threading
 
     import numpy as np
-    import torch
 
     import paper_2308_01654_gb300 as mp
     from paper_2308_01654_gb300 import scenarios
 
-    torch.cuda.set_device(local)
-    dist_init(world, local)
     sessions = scenarios.serving_sessions(seed=0, n=args.sessions)
     for p in sessions:
         p.params["shift"] = 1
         p.params["session"] = rank_session(rank, int(p.params["session"]))
     cparams = [mp.make_params(p.params) for p in sessions]
-    warm, meas = args.serve_warmup_s, args.serve_seconds
-    trace = serving_trace(sessions, args.rate, warm + meas)
+    trace = serving_trace(sessions, rate, warm + meas)
     max_t = max(p.T for p in sessions)
     max_ref = max(p.ref.shape[0] for p in sessions)
     max_circ = max(max(p.circles.shape[0] for p in sessions), 1)
@@ -640,22 +796,27 @@ def run_serving(args, world, rank, local):
     # tune for the micro-batches the trace produces: a few plans of median size
     by_size = sorted(range(len(sessions)), key=lambda i: sessions[i].K * sessions[i].T)
     mid = by_size[len(by_size) // 2]
-    tune_n = max(1, min(8, int(round(args.rate * 1e-3))))        # ~ plans arriving per millisecond
+    tune_n = max(1, min(8, int(round(rate * 1e-3))))             # ~ plans arriving per millisecond
     group, block = srv.autotune(cparams[mid], sessions[mid].x0, sessions[mid].ref, sessions[mid].circles, tune_n)
-    ids, lat, arr_t, done_t = {}, {}, {}, {}
+    ids = {}                     # request id -> trace index (written after enqueue returns)
+    got = {}                     # request id -> (latency_us, completion time, status), in any order
+    n_enq = [0]
     t0 = [0.0]
     stop = threading.Event()
 
     def collector():
-        while not stop.is_set() or len(done_t) < len(trace):
+        deadline = None
+        while True:
             for r in srv.poll(1024, wait_ms=20):
-                j = ids.get(r["request_id"])
-                if j is None:
-                    continue
-                lat[j] = r["latency_us"]
-                done_t[j] = time.perf_counter() - t0[0]
-            if stop.is_set() and len(done_t) >= len(ids):
-                break
+                # a result may come back before its enqueue has returned and its id is registered:
+                # keep it by id and match it to the trace afterwards
+                got[r["request_id"]] = (r["latency_us"], time.perf_counter() - t0[0], r["status"])
+            if stop.is_set():
+                if len(got) >= n_enq[0]:
+                    return
+                deadline = deadline or time.perf_counter() + 60.0
+                if time.perf_counter() > deadline:
+                    return
 
     th = threading.Thread(target=collector, daemon=True)
     t0[0] = time.perf_counter()
@@ -667,15 +828,20 @@ def run_serving(args, world, rank, local):
         p = sessions[s]
         rid = srv.enqueue(cparams[s], s, p.x0, p.ref, circ if circ.shape[0] else None)
         ids[rid] = j
-        arr_t[j] = t
+        n_enq[0] += 1
     stop.set()
-    th.join(timeout=60)
+    th.join(timeout=90)
     st = srv.pending()
     srv.close()
-    order = sorted(lat)
-    served = summarise([lat[j] for j in order], [arr_t[j] for j in order], [done_t[j] for j in order], "server")
+    lost = [rid for rid in ids if rid not in got]
+    failed = sum(1 for rid in ids if rid in got and got[rid][2] != 0)
+    if lost or failed:
+        raise RuntimeError(f"serving: {len(lost)} of {len(ids)} requests never completed, {failed} failed")
+    order = sorted(ids, key=lambda rid: ids[rid])
+    served = summarise([got[r][0] for r in order], [trace[ids[r]][0] for r in order], [got[r][1] for r in order],
+                       "server")
     served.update(batches=st["batches"], plans=st["plans"], mean_batch=st["plans"] / max(st["batches"], 1),
-                  rollout_launch=launch_desc(group, block))
+                  lost=len(lost), failed=failed, rollout_launch=launch_desc(group, block))
 
     # --- plain loop: one context per session, one request at a time in arrival order
     ctxs = [mp.Planner(p.params, device=local, max_ref=max_ref, max_circ=max_circ) for p in sessions]
@@ -711,19 +877,13 @@ def run_serving(args, world, rank, local):
     plain = summarise(plat, parr, pdone, "plain FIFO mppi_plan loop")
     mean_kt = float(np.mean([sessions[s].K * sessions[s].T for _, s, _ in trace]))
     # every rank serves its own sessions: plans/s add up, latency is the worst rank's
-    (total,) = sum_over_ranks([served["plans_per_s"]], world, "cuda")
+    (total, plain_total) = sum_over_ranks([served["plans_per_s"], plain["plans_per_s"]], world, "cuda")
     p50_all, p99_all = max_over_ranks([served["p50_ms"], served["p99_ms"]], world, "cuda")
-    out = {"metric": f"served plans/s ({len(sessions)} sessions, Poisson {args.rate:.0f} plans/s offered)",
-           "value": total, "unit": "plans/s", "n_gpus": world, "steps": len(trace), "warmup": 0,
-           "ms_per_step": p50_all, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32+f64-reduce", "data": "synthetic sessions (K 2^10..2^14, T 30..150, 0..32 obstacles)",
-           "config": {"workload": f"serving: {warm:.0f} s warm-up + {meas:.0f} s measured, mean K*T {mean_kt:.0f}",
-                      "pipelines": args.pipelines, "max_wait_us": args.max_wait_us},
-           "latency_ms": {"p50": p50_all, "p99": p99_all, "max": served["max_ms"]},
-           "server": served, "plain_per_plan_loop": plain}
-    if rank == 0:
-        print(json.dumps(out), flush=True)
-    dist_done(world)
+    return {"value": total, "unit": "plans/s", "offered_plans_per_s": rate * world, "requests": len(trace),
+            "workload": f"serving: {len(sessions)} sessions, Poisson {rate:.0f} plans/s, {warm:.0f} s warm-up + "
+                        f"{meas:.0f} s measured, mean K*T {mean_kt:.0f}",
+            "latency_ms": {"p50": p50_all, "p99": p99_all, "max": served["max_ms"]},
+            "server": served, "plain_per_plan_loop": dict(plain, plans_per_s_all_ranks=plain_total)}
 
 
 # ------------------------------------------------------------------------ the reference arm (the oracle)
@@ -778,6 +938,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-systems", action="store_true",
+                    help="default workload only: skip the bf16, batched and serving records")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file (read first, appended after tuning)")
     ap.add_argument("--quick", action="store_true",
                     help="device timing only (no e2e, clocks or CPU baseline): the profiling run")

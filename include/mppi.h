@@ -285,6 +285,11 @@ int mppi_batch_set_launch(mppi_batch* batch, int32_t group, int32_t block);
 /* Warm start of one slot: U[T][2] and its iteration index (the Philox counter word 2). */
 int mppi_batch_set_controls(mppi_batch* batch, int32_t slot, const double* U, int32_t T, uint64_t iter);
 int mppi_batch_get_controls(mppi_batch* batch, int32_t slot, double* U, int32_t T, uint64_t* iter);
+/* Parity view (debug): the sample costs S[K] (Eq. (6), binary64) of plan i of the last submission
+   that completed on pipeline `ticket` (the ticket mppi_batch_submit returned).  K must be that plan's
+   K.  MPPI_ERR_CAPACITY while the pipeline has a submission in flight (its costs are being
+   overwritten), MPPI_ERR_ARG for a plan or K the last submission did not have. */
+int mppi_batch_get_costs(mppi_batch* batch, int32_t ticket, int32_t i, double* S, int32_t K);
 const char* mppi_batch_last_error(mppi_batch* batch);
 
 /* ------------------------------------------------------------------------------------
@@ -339,7 +344,9 @@ int mppi_server_enqueue(mppi_server* server, const mppi_params* params, int32_t 
                         const double* centres, uint64_t* request_id);
 
 /* Moves up to max completed results into out[] (waiting up to wait_ms for the first);
-   with u_out / x_out (may be NULL) also their u* [max_T][2] and x* [max_T+1][4] per result. */
+   with u_out / x_out (may be NULL) also their u* [max_T][2] and x* [max_T+1][4] per result.
+   A result whose T exceeds max_T while u_out or x_out is given has status MPPI_ERR_CAPACITY
+   and its rows are not written (its info is). */
 int mppi_server_poll(mppi_server* server, mppi_result* out, int32_t max, double* u_out, double* x_out,
                      int32_t max_T, int32_t wait_ms, int32_t* n_out);
 

@@ -117,6 +117,8 @@ def lib():
                                       C.c_int32, dp, C.c_int32, C.c_int32, dp]
         L.orc_costs_range.restype = C.c_int
         L.orc_num_threads.restype = C.c_int
+        L.orc_set_num_threads.argtypes = [C.c_int]
+        L.orc_set_num_threads.restype = None
         _lib = L
     return _lib
 
@@ -341,6 +343,11 @@ def costs_range(prob, k0: int, count: int, U=None, iter_: int = 0) -> np.ndarray
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's sample loops (timing only; results do not depend on it)."""
+    lib().orc_set_num_threads(int(n))
 
 
 INF = math.inf

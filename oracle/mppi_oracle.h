@@ -134,6 +134,7 @@ int orc_costs_range(const orc_params* p, uint32_t iter, const double x0[4], cons
                     const double* centres, int32_t k0, int32_t count, double* S_out);
 
 int orc_num_threads(void);
+void orc_set_num_threads(int n);
 
 #ifdef __cplusplus
 }

@@ -100,6 +100,7 @@ SIGNATURES = {
     "mppi_batch_set_launch": (C.c_int, [_VP, C.c_int32, C.c_int32]),
     "mppi_batch_set_controls": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, C.c_uint64]),
     "mppi_batch_get_controls": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, C.POINTER(C.c_uint64)]),
+    "mppi_batch_get_costs": (C.c_int, [_VP, C.c_int32, C.c_int32, _VP, C.c_int32]),
     "mppi_batch_last_error": (C.c_char_p, [_VP]),
     "mppi_server_create": (C.c_int, [_VP, C.POINTER(_VP)]),
     "mppi_server_destroy": (C.c_int, [_VP]),
@@ -449,6 +450,12 @@ class BatchPlanner:
         reqs = self.requests(plans) if reqs is None else reqs
         self._check(lib().mppi_batch_plan(self._h, C.cast(reqs, _VP), len(reqs)), self._h)
         return reqs
+
+    def get_costs(self, ticket: int, i: int, K: int) -> np.ndarray:
+        """Sample costs of plan i of the last submission completed on pipeline `ticket`."""
+        S = np.empty(int(K))
+        self._check(lib().mppi_batch_get_costs(self._h, int(ticket), int(i), _dp(S), int(K)), self._h)
+        return S
 
     def autotune(self, plans):
         reqs = self.requests(plans)

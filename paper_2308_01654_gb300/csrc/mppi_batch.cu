@@ -360,6 +360,8 @@ struct Pipeline {
     size_t stage_used = 0, out_used = 0;
     std::vector<mppi_request*> pending;
     std::vector<long long> out_offsets;
+    std::vector<long long> s_offsets;   // per plan of the last submission: offset of its costs in S
+    std::vector<int> s_counts;          // and its K (kept after the wait for mppi_batch_get_costs)
     bool busy = false;
     BatchArgs args{};
 };
@@ -557,6 +559,8 @@ static int build_submission(mppi_batch* B, Pipeline& p, mppi_request* req, int n
     long long noise = 0, wsum = 0, n_tiles = 0;
     const int spt = B->threads / lanes_of(B->G);   // samples per rollout tile
     p.out_offsets.assign((size_t)n, 0);
+    p.s_offsets.assign((size_t)n, 0);
+    p.s_counts.assign((size_t)n, 0);
     std::vector<std::pair<double, int>> cost((size_t)n);
     for (int i = 0; i < n; ++i) {
         mppi_request& r = req[i];
@@ -603,6 +607,8 @@ static int build_submission(mppi_batch* B, Pipeline& p, mppi_request* req, int n
         noise += (long long)K * ((T + 1) / 2);
         wsum += (long long)((T + WS_TT - 1) / WS_TT) * d.n_kt;
         p.out_offsets[(size_t)i] = out_off;
+        p.s_offsets[(size_t)i] = s_off;
+        p.s_counts[(size_t)i] = K;
         z_off += (long long)K * T;
         s_off += K;
         scene_off += (long long)up((size_t)d.L.bytes);
@@ -872,6 +878,18 @@ int mppi_batch_get_controls(mppi_batch* B, int32_t slot, double* U, int32_t T, u
     unsigned long long it = 0;
     BCK(cudaMemcpy(&it, &B->slots[slot].iter, sizeof(it), cudaMemcpyDeviceToHost), "iter copy");
     if (iter) *iter = it;
+    return MPPI_OK;
+}
+
+int mppi_batch_get_costs(mppi_batch* B, int32_t ticket, int32_t i, double* S, int32_t K) {
+    if (!B || !S || ticket < 0 || ticket >= (int)B->pipes.size()) return bfail(B, MPPI_ERR_ARG, "bad argument");
+    std::lock_guard<std::mutex> lock(B->mu);
+    Pipeline& p = B->pipes[(size_t)ticket];
+    if (p.busy) return bfail(B, MPPI_ERR_CAPACITY, "the pipeline has a submission in flight");
+    if (i < 0 || i >= (int)p.s_counts.size() || K != p.s_counts[(size_t)i])
+        return bfail(B, MPPI_ERR_ARG, "no such plan in the pipeline's last submission, or K differs");
+    BCK(cudaSetDevice(B->device), "cudaSetDevice");
+    BCK(cudaMemcpy(S, p.S + p.s_offsets[(size_t)i], sizeof(double) * (size_t)K, cudaMemcpyDeviceToHost), "costs copy");
     return MPPI_OK;
 }
 

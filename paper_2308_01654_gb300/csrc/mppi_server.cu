@@ -115,8 +115,10 @@ static void scheduler_loop(mppi_server* S) {
                 job->reqs.push_back(std::move(*it));
                 it = S->queue.erase(it);
             } else {
-                // a request of a busy session keeps its place; later sessions may go ahead
-                if (!session_free) in_batch[(size_t)r.session] = 1;
+                // a request left in the queue (its session busy, or too large for what is free
+                // now) keeps its place and holds back every later request of its session, so
+                // that a session's requests run in arrival order; other sessions may go ahead
+                in_batch[(size_t)r.session] = 1;
                 ++it;
             }
         }
@@ -300,9 +302,13 @@ int mppi_server_poll(mppi_server* S, mppi_result* out, int32_t max, double* u_ou
         o.latency_us = std::chrono::duration<double, std::micro>(r->t_done - r->t_arrive).count();
         o.queue_us = std::chrono::duration<double, std::micro>(r->t_submit - r->t_arrive).count();
         o.info = r->info;
-        if (u_out && r->params.T <= max_T) memcpy(u_out + (size_t)n * max_T * 2, r->u.data(), r->u.size() * sizeof(double));
-        if (x_out && r->params.T <= max_T)
-            memcpy(x_out + (size_t)n * (max_T + 1) * 4, r->x.data(), r->x.size() * sizeof(double));
+        if ((u_out || x_out) && r->params.T > max_T) {
+            // the caller's rows are too short for this result's u* and x*: not copied, and said so
+            o.status = MPPI_ERR_CAPACITY;
+        } else {
+            if (u_out) memcpy(u_out + (size_t)n * max_T * 2, r->u.data(), r->u.size() * sizeof(double));
+            if (x_out) memcpy(x_out + (size_t)n * (max_T + 1) * 4, r->x.data(), r->x.size() * sizeof(double));
+        }
         ++n;
     }
     *n_out = n;

@@ -11,7 +11,7 @@ import pytest
 import oracle
 import paper_2308_01654_gb300 as mp
 from paper_2308_01654_gb300 import scenarios as sc
-from parity import U_ABS_TOL, X_ABS_TOL, argmin_ok
+from parity import argmin_ok, assert_costs, assert_update
 
 pytestmark = pytest.mark.gpu
 
@@ -30,10 +30,33 @@ def mixed_problems(n=12, seed=3):
     return probs
 
 
-def batch_for(probs, pipelines=2, bf16=0):
+def batch_for(probs, pipelines=2, bf16=0, max_T=128):
     return mp.BatchPlanner(max_slots=64, max_batch=64, max_samples=sum(p.K for p in probs) + 8,
-                           max_rollout_steps=sum(p.K * p.T for p in probs) + 8, max_T=128, max_ref=1024,
+                           max_rollout_steps=sum(p.K * p.T for p in probs) + 8, max_T=max_T, max_ref=1024,
                            max_circ=128, noise_bf16=bf16, pipelines=pipelines)
+
+
+def c4_sized_problems(seed=41):
+    """Plans at the sizes of the batched workload: K up to 2^14, T up to 150, up to 32 obstacles."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shapes = [(16384, 150), (8192, 121), (1024, 30), (4096, 77), (2048, 143)]
+    probs = []
+    for i, (K, T) in enumerate(shapes):
+        p = sc.uneven_instance(rng, i, seed=seed)
+        p.params.update(K=K, T=T, session=200 + i)
+        probs.append(p)
+    probs[1].centres = sc.predicted_centres(probs[1].circles, probs[1].T, probs[1].params["dt"])
+    return probs
+
+
+def oracle_check(p, bpl, S):
+    """A batched plan against the FP64 oracle: every sample cost, the argmin, u* and x*."""
+    orc = oracle.plan(p)
+    rep = assert_costs(S, orc.S, orc.margin)
+    assert argmin_ok(bpl.info.argmin, orc.S), (bpl.info.argmin, orc.info.argmin)
+    assert bpl.info.n_finite == orc.info.n_finite
+    assert_update(bpl.u, bpl.x, orc)
+    return rep
 
 
 def plans_of(probs, slots=None):
@@ -118,13 +141,54 @@ def test_batch_matches_the_oracle():
     probs = mixed_problems(n=6)
     with batch_for(probs) as bp:
         plans = plans_of(probs)
-        bp.plan(plans)
-    for p, bpl in zip(probs, plans):
-        orc = oracle.plan(p)
-        assert argmin_ok(bpl.info.argmin, orc.S)
-        if bpl.info.argmin == orc.info.argmin:
-            np.testing.assert_allclose(bpl.u, orc.u_star, rtol=0, atol=U_ABS_TOL)
-            np.testing.assert_allclose(bpl.x, orc.x_star, rtol=0, atol=X_ABS_TOL)
+        reqs = bp.requests(plans)        # kept alive: wait() writes each request's status
+        t = bp.submit(reqs)
+        bp.wait(t)
+        S = [bp.get_costs(t, i, p.K) for i, p in enumerate(probs)]
+    for p, bpl, s in zip(probs, plans, S):
+        oracle_check(p, bpl, s)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("bf16", [0, 1])
+def test_batch_matches_the_oracle_at_batched_workload_sizes(bf16):
+    """K up to 16384 and T up to 150 in one submission, noise in binary32 or bfloat16.  The bf16
+    form is compared with the oracle on the same bf16-rounded noise (the same method), and its
+    error against the unrounded FP64 method is reported."""
+    probs = c4_sized_problems()
+    for p in probs:
+        p.params["noise_bf16"] = bf16
+    with batch_for(probs, bf16=bf16, max_T=160) as bp:
+        plans = plans_of(probs)
+        reqs = bp.requests(plans)        # kept alive: wait() writes each request's status
+        t = bp.submit(reqs)
+        bp.wait(t)
+        S = [bp.get_costs(t, i, p.K) for i, p in enumerate(probs)]
+    for p, bpl, s in zip(probs, plans, S):
+        rep = oracle_check(p, bpl, s)
+        line = f"K={p.K} T={p.T} n_circ={p.circles.shape[0]}: max rel S err {rep['max_rel_all']:.2e}"
+        if bf16:
+            full = oracle.plan(p, params=dict(p.params, noise_bf16=0))
+            rel = np.abs(s - full.S) / np.maximum(np.abs(full.S), 1.0)
+            line += (f"; vs the unrounded FP64 method: max rel S err {rel.max():.2e}, "
+                     f"|du*| {np.abs(bpl.u - full.u_star).max():.2e}")
+        print(line)
+
+
+def test_batch_costs_view_errors():
+    probs = mixed_problems(n=2)
+    with batch_for(probs) as bp:
+        plans = plans_of(probs)
+        reqs = bp.requests(plans)        # kept alive: wait() writes each request's status
+        t = bp.submit(reqs)
+        with pytest.raises(mp.MppiError) as e:           # still in flight
+            bp.get_costs(t, 0, probs[0].K)
+        assert e.value.status == -6
+        bp.wait(t)
+        for i, K in ((0, probs[0].K + 1), (2, probs[0].K), (-1, probs[0].K)):
+            with pytest.raises(mp.MppiError) as e:
+                bp.get_costs(t, i, K)
+            assert e.value.status == -1
 
 
 def test_warm_starts_persist_in_the_slots():

@@ -13,7 +13,7 @@ import pytest
 import oracle
 import paper_2308_01654_gb300 as mp
 from paper_2308_01654_gb300 import scenarios as sc
-from parity import U_ABS_TOL, X_ABS_TOL, argmin_ok, assert_costs
+from parity import U_ABS_TOL, argmin_ok, assert_costs, assert_update
 
 pytestmark = pytest.mark.gpu
 
@@ -32,14 +32,13 @@ def run_gpu(prob, U=None, iters=1, params=None):
     return outs, z, Ud, it
 
 
-def check_iteration(prob, gpu_out, orc, max_excused=0.02):
+def check_iteration(prob, gpu_out, orc, max_excused_fail=0.0):
+    """Every sample cost, the argmin, and u* and x* whatever the argmin."""
     u, x, info, S = gpu_out
-    rep = assert_costs(S, orc.S, orc.margin, max_excused)
+    rep = assert_costs(S, orc.S, orc.margin, max_excused_fail)
     assert argmin_ok(info["argmin"], orc.S), (info["argmin"], orc.info.argmin)
     assert info["n_finite"] == orc.info.n_finite
-    if info["argmin"] == orc.info.argmin:
-        np.testing.assert_allclose(u, orc.u_star, rtol=0, atol=U_ABS_TOL)
-        np.testing.assert_allclose(x, orc.x_star, rtol=0, atol=X_ABS_TOL)
+    assert_update(u, x, orc)
     return rep
 
 

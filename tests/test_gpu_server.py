@@ -7,8 +7,10 @@ device-resident warm start, and a plan's arithmetic does not depend on its batch
 import numpy as np
 import pytest
 
+import oracle
 import paper_2308_01654_gb300 as mp
 from paper_2308_01654_gb300 import scenarios as sc
+from parity import S_REL_TOL, argmin_ok, assert_update
 
 pytestmark = pytest.mark.gpu
 
@@ -125,3 +127,88 @@ def test_request_above_capacity_is_refused():
         with pytest.raises(mp.MppiError) as e:
             srv.enqueue(params[0], 5, probs[0].x0, probs[0].ref, None)      # session out of range
         assert e.value.status == -1
+
+
+def test_served_results_match_the_oracle():
+    """Each served result against the FP64 oracle (Eq. (11) and Algorithm 1 per request) on the
+    same inputs, warm start and iteration counter.  Three rounds of one request per session, mixed
+    into micro-batches by the server; before each round every session's device warm start is set
+    to the oracle's (teacher forcing), so each result is compared on identical inputs."""
+    probs = sessions(n=6, seed=11)
+    params = [mp.make_params(p.params) for p in probs]
+    rng = np.random.default_rng(3)
+    U = [np.zeros((p.T, 2)) for p in probs]
+    with server_for(probs) as srv:
+        for rnd in range(3):
+            for s, p in enumerate(probs):
+                srv.set_controls(s, U[s], rnd)
+            reqs = []
+            for s, p in enumerate(probs):
+                circ = p.circles.copy()
+                if circ.shape[0]:
+                    circ[:, :2] += rng.normal(scale=0.3, size=(circ.shape[0], 2))
+                reqs.append((s, np.ascontiguousarray(circ)))
+            res = run(srv, probs, reqs, params, alone=False)
+            for (s, circ), r in zip(reqs, res):
+                q = probs[s].copy()
+                q.circles = circ
+                orc = oracle.plan(q, U=U[s], iter_=rnd)
+                assert r["status"] == 0 and r["info"]["iter"] == rnd
+                assert argmin_ok(r["info"]["argmin"], orc.S), (r["info"]["argmin"], orc.info.argmin)
+                assert r["info"]["n_finite"] == orc.info.n_finite
+                assert abs(r["info"]["s_min"] - orc.info.s_min) <= S_REL_TOL * max(abs(orc.info.s_min), 1.0)
+                assert_update(r["u"], r["x"], orc)
+                U[s] = orc.U
+
+
+def test_a_session_keeps_its_order_when_its_older_request_does_not_fit():
+    """Session 0 queues a large request and then a small one while another session's large
+    request holds most of the HBM budget: the small one fits and the large one does not, yet the
+    small one must not overtake it (its warm start is the large one's output)."""
+    probs = sessions(n=2)
+    params = {}
+    for name, K, T in (("big", 65536, 48), ("small", 512, 8)):
+        q = dict(probs[0].params, K=K, T=T)
+        params[name] = mp.make_params(q)
+    scene = 200_000                                   # generous bound on a scene and its centre table
+    big = 65536 * 48 * 8 + 65536 * 12 + scene
+    small = 512 * 8 * 8 + 512 * 12 + scene
+    budget = big + small + scene                      # room for one large and one small request
+    p0, p1 = probs[0], probs[1]
+    with server_for(probs, hbm_budget_bytes=budget, max_samples=200_000, max_rollout_steps=8_000_000) as srv:
+        srv.enqueue(params["big"], 1, p1.x0, p1.ref, None)               # holds the budget for a while
+        r_big = srv.enqueue(params["big"], 0, p0.x0, p0.ref, None)
+        r_small = srv.enqueue(params["small"], 0, p0.x0, p0.ref, None)
+        got = []
+        while len(got) < 3:
+            got += srv.poll(8, wait_ms=1000)
+    by_id = {r["request_id"]: (i, r) for i, r in enumerate(got)}
+    i_big, rb = by_id[r_big]
+    i_small, rs = by_id[r_small]
+    assert rb["status"] == 0 and rs["status"] == 0
+    assert rb["info"]["iter"] == 0 and rs["info"]["iter"] == 1       # session 0's counter: arrival order
+    assert i_big < i_small                                            # completed first
+
+
+def test_poll_reports_rows_too_short_for_a_result():
+    probs = sessions(n=1)
+    p = probs[0]
+    params = mp.make_params(p.params)
+    with server_for(probs) as srv:
+        srv.enqueue(params, 0, p.x0, p.ref, None)
+        out = (mp.MppiResult * 4)()
+        n = mp.C.c_int32()
+        short = max(1, p.T - 1)
+        U = np.zeros((4, short, 2))
+        X = np.zeros((4, short + 1, 4))
+        got = 0
+        for _ in range(50):
+            rc = mp.lib().mppi_server_poll(srv._h, mp.C.cast(out, mp._VP), 4, mp._dp(U), mp._dp(X), short, 200,
+                                           mp.C.byref(n))
+            assert rc == 0
+            if n.value:
+                got = n.value
+                break
+        assert got == 1
+        assert out[0].status == -6 and out[0].T == p.T
+        assert np.all(U == 0.0) and np.all(X == 0.0)
