@@ -326,7 +326,7 @@ def cpu_baseline_record(prob, seconds: float):
     return rec, r, k_s
 
 
-def error_vs_oracle(mp, prob, k: int, orc, local: int, params=None) -> dict:
+def error_vs_oracle(mp, prob, k: int, orc, local: int, params=None, gated: bool = True) -> dict:
     """The CUDA path against the FP64 oracle on the same workload cut to K = k samples (the noise
     of sample j does not depend on K): every sample cost, the argmin, u* and x* of one iteration
     from a zero warm start."""
@@ -342,7 +342,8 @@ def error_vs_oracle(mp, prob, k: int, orc, local: int, params=None) -> dict:
     return {"samples": int(k), "max_rel_S": float(rel.max()), "median_rel_S": float(np.median(rel)),
             "argmin_ok": bool(info["argmin"] in near), "max_abs_du_star": float(np.abs(u - orc.u_star).max()),
             "max_abs_dx_star": float(np.abs(x - orc.x_star).max()),
-            "tolerance": {"S_rel": 1e-4, "u_abs": 1e-4, "x_abs": 1e-4}}
+            **({"tolerance": {"S_rel": 1e-4, "u_abs": 1e-4, "x_abs": 1e-4}} if gated else
+               {"note": "the error of storing the noise as bfloat16 itself (not a parity check)"})}
 
 
 # ------------------------------------------------------------------------ the GPU arm
@@ -556,7 +557,7 @@ def bf16_report(args, world, rank, local, steps: int = 10) -> dict:
         q.params["K"] = k
         rec["error_vs_oracle_same_codes"] = error_vs_oracle(mp, prob, k, oracle.plan(q), local)
         rec["error_vs_oracle_unrounded"] = error_vs_oracle(
-            mp, prob, k, oracle.plan(q, params=dict(q.params, noise_bf16=0)), local)
+            mp, prob, k, oracle.plan(q, params=dict(q.params, noise_bf16=0)), local, gated=False)
     return rec
 
 

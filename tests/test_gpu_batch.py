@@ -176,7 +176,7 @@ def test_batch_matches_the_oracle_at_batched_workload_sizes(bf16):
 
 
 def test_batch_costs_view_errors():
-    probs = mixed_problems(n=2)
+    probs = mixed_problems(n=3)[:2]
     with batch_for(probs) as bp:
         plans = plans_of(probs)
         reqs = bp.requests(plans)        # kept alive: wait() writes each request's status
