@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 2) batch_rollout_kernel(Bat
     __shared__ PlanConst s_pc;
     __shared__ SceneLayout s_L;
     __shared__ float4 s_x0;
-    __shared__ int s_tile, s_plan, s_moving, s_jb0;
+    __shared__ int s_tile, s_plan, s_moving, s_multi, s_jb0;
     if (threadIdx.x == 0) {
         bulk_init(&bar);
         s_plan = -1;
@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 2) batch_rollout_kernel(Bat
                 const DevState* st = a.slots + d.slot;
                 s_x0 = st->x0f;
                 s_moving = st->moving;
+                s_multi = st->multi_head;
                 s_jb0 = (int)(st->jkey & 0xffffffffu);
                 s_plan = td.x;
                 bulk_issue(smem, a.scene + d.scene_off, d.L.bytes, &bar);
@@ -185,12 +186,13 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 2) batch_rollout_kernel(Bat
             __syncthreads();
             if (!__syncthreads_and(bulk_wait(&bar, phase, &a.hdr->flags))) return;
             phase ^= 1u;
-            build_boxes(smem, s_L, a.table + a.inst[s_plan].table_off, s_pc.has_table != 0);
+            build_boxes(smem, s_L);
         }
         const BatchInst& d = a.inst[td.x];
         const int k = td.y + (int)threadIdx.x / G;   // G lanes per sample
         rollout_sample<G, TIME, BF16, false, false>(s_pc, s_L, smem, reinterpret_cast<const NT*>(a.z) + d.z_off,
-                                       a.table + d.table_off, s_x0, 0.0f, s_moving != 0, s_jb0, k, a.S + d.s_off,
+                                       a.table + d.table_off, s_x0, 0.0f, s_moving != 0, s_multi != 0, s_jb0, k,
+                                       a.S + d.s_off,
                                        nullptr);
         __syncthreads();
     }

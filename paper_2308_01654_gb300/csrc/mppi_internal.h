@@ -31,7 +31,8 @@ struct __align__(16) DevState {
     unsigned long long iter_used;  // iteration index of the last finished iteration
     int32_t moving;              // some obstacle circle has a nonzero velocity
     float delta0f;               // steering angle of x0 (model 1)
-    int32_t pad_[2];
+    int32_t multi_head;          // the reference polyline has segments of more than one heading
+    int32_t pad_;
 };
 
 // Byte offsets of the arrays in the scene blob that the rollout kernel stages into
@@ -44,12 +45,13 @@ struct SceneLayout {
     int off_seg;     // float4 [n_seg]   (ex, ey, ex/|e|^2, ey/|e|^2)
     int off_head;    // float  [n_seg]   heading of each segment
     int off_l1;      // float4 [n_l1]    level-1 chunk boxes
+    // the circles are stored sorted by their key s = p . d (p: the first centre, d: the lane direction)
     int off_circ;    // float4 [n_circ]  (x, y, r, (d_safe_0 + r + r_ego)^2 when d_safe is constant)
     int off_vel;     // float2 [n_circ]  velocities
     int off_disp;    // float  [n_circ]  bound on the distance a centre moves in one step
     int off_proj;    // float4           (dx, dy, 0, 0): unit direction of the lane (first to last vertex)
-    int off_order;   // int    [n_circ]  circles sorted by their key s = p . d (p: centre at step 0),
-    int off_skey;    // float  [n_circ]  and the sorted keys: space only, filled in each block's copy
+    int off_order;   // int    [n_circ]  input index of each sorted circle (its column of the centre table)
+    int off_skey;    // float  [n_circ]  the sorted keys
     int bytes;       // total, a multiple of 16
 };
 
@@ -111,12 +113,11 @@ struct PlanBuffers {
 
 // Shared memory each rollout block builds after the staged blob: the level-2 boxes, the
 // prefix and suffix boxes of the chunk sequence, and the circle index (a float4 of scalars
-// and CIRC_BUCKETS + 1 bucket starts into the sorted circles, then the unsorted keys).
+// and CIRC_BUCKETS + 1 bucket starts into the sorted circles).
 constexpr int CIRC_BUCKETS = 64;
 
 __host__ __device__ inline size_t block_extra_bytes(const SceneLayout& L) {
-    return (size_t)16 * (L.n_l2 + 2 * (L.n_l1 + 1)) + 16 + (size_t)4 * ((CIRC_BUCKETS + 1 + 3) & ~3) +
-           (size_t)4 * ((L.n_circ + 3) & ~3);   // unsorted keys while the block sorts
+    return (size_t)16 * (L.n_l2 + 2 * (L.n_l1 + 1)) + 16 + (size_t)4 * ((CIRC_BUCKETS + 1 + 3) & ~3);
 }
 
 // Per-thread slots after the block's extras: the compensated steering angle of the

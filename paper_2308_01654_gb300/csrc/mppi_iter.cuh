@@ -36,6 +36,36 @@ __device__ __forceinline__ float seg_heading(const double* ref, int i) {
     return atan2f((float)hy, (float)hx);
 }
 
+// Unit lane direction (first to last vertex), formed in binary64 and rounded: the axis the
+// circles are sorted on.
+__device__ __forceinline__ float2 lane_direction(const double* ref, int n_ref) {
+    const double ex = ref[2 * (n_ref - 1)] - ref[0], ey = ref[2 * (n_ref - 1) + 1] - ref[1];
+    const double el = sqrt(ex * ex + ey * ey);
+    const bool ok = el > 0.0 && isfinite(el);
+    return make_float2(ok ? (float)(ex / el) : 1.0f, ok ? (float)(ey / el) : 0.0f);
+}
+
+// Sort key of circle j: its first centre (the first row of the centre table when one is given,
+// else the given centre) in the local frame, projected on the lane direction; non-finite keys
+// sort last.
+__device__ __forceinline__ float circle_key(const PlanInputs& in, int j, double ox, double oy, float2 pj) {
+    const double* c = in.centres ? in.centres + 2 * j : in.circ + 5 * j;
+    const float px = (float)(c[0] - ox), py = (float)(c[1] - oy);
+    const float key = fmaf(px, pj.x, py * pj.y);
+    return isfinite(key) ? key : INFINITY;
+}
+
+// Position of circle k in the sorted order (key, then index): one permutation of the circles.
+__device__ __forceinline__ int circle_rank(const PlanInputs& in, int k, float kk, double ox, double oy, float2 pj,
+                                           int j0, int dj) {
+    int rank = 0;
+    for (int j = j0; j < in.n_circ; j += dj) {
+        const float sj = circle_key(in, j, ox, oy, pj);
+        rank += (sj < kk || (sj == kk && j < k)) ? 1 : 0;
+    }
+    return rank;
+}
+
 // The preparation in independent phases: 0 controls and x0, 1 vertices, 2 segments and the
 // segment nearest x0, 3 level-1 boxes, 4 circles and the lane direction, 5 the per-step
 // centre table, 6 the largest step of each tabulated centre.  phase < 0 runs them all in
@@ -82,10 +112,13 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
         // closest segment (or vertex) to x0 itself, the rollouts' first warm start: a packed
         // (distance bits, index) minimum, reduced in the warp before one atomic per warp
         unsigned long long best = ~0ull;
+        const float h0 = seg_heading(in.ref, 0);
+        bool multi = false;
         for (int i = tid; i < L.n_seg; i += nth) {
             const float4 s = seg_record(in.ref, i, ox, oy);
             seg[i] = s;
             head[i] = seg_heading(in.ref, i);
+            multi |= head[i] != h0;
             const float2 a = local_vertex(in.ref, i, ox, oy);
             const float d2 = pc.ref_mode == 0 ? seg_dist2(0.0f, 0.0f, a, s) : fmaf(a.x, a.x, a.y * a.y);
             const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)i;
@@ -97,6 +130,8 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
             best = other < best ? other : best;
         }
         if (lane == 0 && best != ~0ull) atomicMin(&b.state->jkey, best);
+        // one heading throughout: no two segments can be in the binary64 near-tie of the search
+        if (__any_sync(0xffffffffu, multi) && lane == 0) atomicOr(&b.state->multi_head, 1);
     }
     if (all || phase == 3) {
         // level-1 boxes: one thread per chunk (its REF_L1 + 1 vertex loads are independent)
@@ -115,28 +150,30 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
         }
     }
     if (all || phase == 4) {
+        // the circles are stored sorted by their key along the lane direction (circle_rank), with
+        // the original index of each sorted position (for the centre table) and the sorted keys
+        const float2 pj = lane_direction(in.ref, L.n_ref);
+        int* order = reinterpret_cast<int*>(sc + L.off_order);
+        float* skey = reinterpret_cast<float*>(sc + L.off_skey);
         for (int k = tid; k < L.n_circ; k += nth) {
             const double* c = in.circ + 5 * k;
             for (int j = 0; j < 5; ++j) bad |= !isfinite(c[j]);
+            const float kk = circle_key(in, k, ox, oy, pj);
+            const int pos = circle_rank(in, k, kk, ox, oy, pj, 0, 1);
             const float r = (float)c[2];
             // band limit (m + r + r_ego)^2 for the constant-d_safe, equal-ego-radius case
             const float m = pc.collision_only ? fmaxf(pc.d_safe_0, 0.0f) : pc.d_safe_0;
             const float lim = m + r + pc.ego_rad[0];
-            circ[k] = make_float4((float)(c[0] - ox), (float)(c[1] - oy), r, lim > 0.0f ? lim * lim : -1.0f);
-            vel[k] = make_float2((float)c[3], (float)c[4]);
+            circ[pos] = make_float4((float)(c[0] - ox), (float)(c[1] - oy), r, lim > 0.0f ? lim * lim : -1.0f);
+            vel[pos] = make_float2((float)c[3], (float)c[4]);
+            order[pos] = k;
+            skey[pos] = kk;
             if (c[3] != 0.0 || c[4] != 0.0) atomicOr(&b.state->moving, 1);
             // bound on the step of a constant-velocity centre, |v| dt with 0.1 % and 1e-5 m to spare
             // (binary32 square root: its error is far inside that margin)
-            if (!in.centres) disp[k] = sqrtf((float)(c[3] * c[3] + c[4] * c[4])) * pc.dt * 1.001f + 1e-5f;
+            if (!in.centres) disp[pos] = sqrtf((float)(c[3] * c[3] + c[4] * c[4])) * pc.dt * 1.001f + 1e-5f;
         }
-        // unit lane direction (first to last vertex): the axis the rollout blocks sort the circles on
-        if (tid == 0) {
-            const double ex = in.ref[2 * (L.n_ref - 1)] - in.ref[0], ey = in.ref[2 * (L.n_ref - 1) + 1] - in.ref[1];
-            const double el = sqrt(ex * ex + ey * ey);
-            const bool ok = el > 0.0 && isfinite(el);
-            *reinterpret_cast<float4*>(sc + L.off_proj) =
-                make_float4(ok ? (float)(ex / el) : 1.0f, ok ? (float)(ey / el) : 0.0f, 0.0f, 0.0f);
-        }
+        if (tid == 0) *reinterpret_cast<float4*>(sc + L.off_proj) = make_float4(pj.x, pj.y, 0.0f, 0.0f);
     }
     if (in.centres && (all || phase == 5)) {
         for (int i = tid; i < L.T * L.n_circ; i += nth) {
@@ -159,7 +196,11 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
             }
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if (lane == 0) disp[k] = isfinite(m) ? (float)(m * 1.001) + 1e-5f : INFINITY;
+            // the circle's sorted position (its place in phase 4's order), counted by the warp
+            const float2 pj = lane_direction(in.ref, L.n_ref);
+            const int pos = __reduce_add_sync(
+                0xffffffffu, (unsigned)circle_rank(in, k, circle_key(in, k, ox, oy, pj), ox, oy, pj, lane, 32));
+            if (lane == 0) disp[pos] = isfinite(m) ? (float)(m * 1.001) + 1e-5f : INFINITY;
         }
     }
     if (bad) atomicOr(&b.state->flags, FLAG_NONFINITE_INPUT);
@@ -326,11 +367,11 @@ __device__ __forceinline__ RefBoxes ref_boxes(const unsigned char* smem, const S
     return r;
 }
 
-// The circle index built after the boxes: circles sorted by their key along the lane
-// direction, CIRC_BUCKETS buckets of equal key width over the finite keys, and the
-// scalars the broad phase needs to bound where a circle can be at step t.
+// The circle index: the circles are stored sorted by their key along the lane direction; the
+// block adds CIRC_BUCKETS buckets of equal key width over the finite keys and the scalars the
+// broad phase needs to bound where a circle can be at step t.
 struct CircleIndex {
-    const int* order;       // [n_circ] circle of each sorted position
+    const int* order;       // [n_circ] input index of each sorted circle (its centre-table column)
     const int* start;       // [CIRC_BUCKETS + 1] first sorted position of each bucket
     float smin, inv_w;      // bucket b holds the keys from smin + b / inv_w (inv_w = 0: one range)
     float dmax, rmax;       // largest step bound and radius over the circles
@@ -372,8 +413,7 @@ __device__ __forceinline__ float4 box_union(float4 a, float4 b) {
     return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
 }
 
-__device__ __forceinline__ void build_boxes(unsigned char* smem, const SceneLayout& L, const float2* table,
-                                            bool has_table) {
+__device__ __forceinline__ void build_boxes(unsigned char* smem, const SceneLayout& L) {
     const RefBoxes r = ref_boxes(smem, L);
     float4* l2 = const_cast<float4*>(r.l2);
     float4* pre = const_cast<float4*>(r.pre);
@@ -417,39 +457,19 @@ __device__ __forceinline__ void build_boxes(unsigned char* smem, const SceneLayo
             else suf[L.n_l1] = empty;
         }
     }
-    // circle index.  Keys: the step-0 centre (first table row, or the given centre) projected
-    // on the lane direction, non-finite keys last; the rank of each circle (key, then index)
-    // places it, so the sorted order is one permutation.
+    // circle index.  Scene preparation stored the circles sorted by their key (the first centre
+    // projected on the lane direction, non-finite keys last) with the sorted keys; the block adds
+    // the bucket starts over the keys and the largest step bound and radius.
     __shared__ unsigned s_dmax, s_rmax;
     __shared__ int s_nfin;
     if (threadIdx.x == 0) {
         s_dmax = 0u;
         s_rmax = 0u;
     }
+    __syncthreads();
     const float4* circ = reinterpret_cast<const float4*>(smem + L.off_circ);
     const float* disp = reinterpret_cast<const float*>(smem + L.off_disp);
-    const float4 pj = *reinterpret_cast<const float4*>(smem + L.off_proj);
-    float* keyt = reinterpret_cast<float*>(const_cast<unsigned char*>(circle_index_base(smem, L)) + 16 +
-                                           4 * ((CIRC_BUCKETS + 1 + 3) & ~3));
-    for (int k = threadIdx.x; k < L.n_circ; k += blockDim.x) {
-        const float2 p = has_table ? table[k] : make_float2(circ[k].x, circ[k].y);
-        const float key = fmaf(p.x, pj.x, p.y * pj.y);
-        keyt[k] = isfinite(key) ? key : INFINITY;
-    }
-    __syncthreads();
-    int* order = reinterpret_cast<int*>(smem + L.off_order);
-    float* skey = reinterpret_cast<float*>(smem + L.off_skey);
-    for (int k = threadIdx.x; k < L.n_circ; k += blockDim.x) {
-        const float sk = keyt[k];
-        int rank = 0;
-        for (int j = 0; j < L.n_circ; ++j) {
-            const float sj = keyt[j];
-            rank += (sj < sk || (sj == sk && j < k)) ? 1 : 0;
-        }
-        order[rank] = k;
-        skey[rank] = sk;
-    }
-    __syncthreads();
+    const float* skey = reinterpret_cast<const float*>(smem + L.off_skey);
     for (int k = threadIdx.x; k < L.n_circ; k += blockDim.x) {
         atomicMax(&s_dmax, __float_as_uint(fmaxf(disp[k], 0.0f)));     // non-negative: bits order as values
         atomicMax(&s_rmax, __float_as_uint(fmaxf(circ[k].z, 0.0f)));
@@ -492,9 +512,10 @@ __device__ __forceinline__ void search_range(float px, float py, const float2* v
 }
 
 // Closest point of the polyline (ties -> lowest segment).  The chunk of the predicted
-// segment jh is scanned first, then each neighbouring chunk whose box lies within the best
-// distance; one prefix box and one suffix box bound everything farther, and a range whose
-// box passes is searched under its level-2 and chunk boxes.  A box is skipped only when its
+// segment jh is scanned first; one box of all the chunks before it and one of all the chunks
+// after it bound the rest.  Only on a side whose box passes is the neighbouring chunk tested
+// (and scanned if its box passes), then the box of the chunks beyond it, and a range whose box
+// passes is searched under its level-2 and chunk boxes.  A box is skipped only when its
 // lower bound exceeds the best distance (with a relative slack far above binary32
 // rounding), so no segment that can be the closest is missed and the result does not
 // depend on jh.  Two segments that share a vertex can be closer than binary32 resolves
@@ -504,40 +525,49 @@ __device__ __forceinline__ void search_range(float px, float py, const float2* v
 template <int G, bool STATS>
 __device__ __forceinline__ void nearest_segment(float px, float py, const float2* vert, const float4* seg,
                                                 const float* head, const RefBoxes& rb, int n_seg, int n_l1,
-                                                int lane_g, unsigned mask, int jh, int& jb, float& best2,
-                                                Counters& cnt) {
+                                                int lane_g, unsigned mask, int jh, bool refine, int& jb,
+                                                float& best2, Counters& cnt) {
     constexpr float SLACK = 1.0f + 1.0f / 1024.0f;
     const int cw = jh / REF_L1;
     unsigned long long best = ~0ull;
     scan_chunk<G, STATS>(px, py, vert, seg, cw, n_seg, lane_g, best, cnt);
     best = group_min_key<G>(best, mask);
-#pragma unroll
-    for (int d = -1; d <= 1; d += 2) {
-        const int c = cw + d;
-        if (c >= 0 && c < n_l1) {
-            if (STATS) cnt.l1++;
-            if (box_dist2(px, py, rb.l1[c]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK) {
-                scan_chunk<G, STATS>(px, py, vert, seg, c, n_seg, lane_g, best, cnt);
-                best = group_min_key<G>(best, mask);
-            }
+    // one box bounds every chunk before cw and one every chunk after it: when neither can hold
+    // a closer segment, the common case, the search ends here
+    const float lim0 = __uint_as_float((unsigned)(best >> 32)) * SLACK;
+    const bool left = cw >= 1 && box_dist2(px, py, rb.pre[cw]) <= lim0;
+    const bool right = cw + 1 < n_l1 && box_dist2(px, py, rb.suf[cw + 1]) <= lim0;
+    if (STATS) cnt.l2 += (cw >= 1 ? 1 : 0) + (cw + 1 < n_l1 ? 1 : 0);
+    if (left) {
+        if (STATS) cnt.l1++;
+        if (box_dist2(px, py, rb.l1[cw - 1]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK) {
+            scan_chunk<G, STATS>(px, py, vert, seg, cw - 1, n_seg, lane_g, best, cnt);
+            best = group_min_key<G>(best, mask);
+        }
+        if (cw >= 2) {
+            if (STATS) cnt.l2++;
+            if (box_dist2(px, py, rb.pre[cw - 1]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK)
+                search_range<G, STATS>(px, py, vert, seg, rb, n_seg, 0, cw - 1, lane_g, mask, best, cnt);
         }
     }
-    if (cw >= 2) {
-        if (STATS) cnt.l2++;
-        if (box_dist2(px, py, rb.pre[cw - 1]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK)
-            search_range<G, STATS>(px, py, vert, seg, rb, n_seg, 0, cw - 1, lane_g, mask, best, cnt);
-    }
-    if (cw + 2 < n_l1) {
-        if (STATS) cnt.l2++;
-        if (box_dist2(px, py, rb.suf[cw + 2]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK)
-            search_range<G, STATS>(px, py, vert, seg, rb, n_seg, cw + 2, n_l1, lane_g, mask, best, cnt);
+    if (right) {
+        if (STATS) cnt.l1++;
+        if (box_dist2(px, py, rb.l1[cw + 1]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK) {
+            scan_chunk<G, STATS>(px, py, vert, seg, cw + 1, n_seg, lane_g, best, cnt);
+            best = group_min_key<G>(best, mask);
+        }
+        if (cw + 2 < n_l1) {
+            if (STATS) cnt.l2++;
+            if (box_dist2(px, py, rb.suf[cw + 2]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK)
+                search_range<G, STATS>(px, py, vert, seg, rb, n_seg, cw + 2, n_l1, lane_g, mask, best, cnt);
+        }
     }
     float b2 = __uint_as_float((unsigned)(best >> 32));
     int bi = (int)(best & 0xffffffffu);
     const int b0 = bi;
-    const float hb = head[b0];
+    const float hb = refine ? head[b0] : 0.0f;
 #pragma unroll
-    for (int dlt = -1; dlt <= 1; dlt += 2) {
+    for (int dlt = -1; refine && dlt <= 1; dlt += 2) {
         const int j = b0 + dlt;
         if (j < 0 || j >= n_seg || head[j] == hb) continue;
         const float dj = seg_dist2(px, py, vert[j], seg[j]);
@@ -606,13 +636,14 @@ __device__ __forceinline__ void kahan_add(float& hi, float& lo, float inc) {
     hi = t;
 }
 
-// Centre of circle kc at rollout step t (state x_{t+1}).
-__device__ __forceinline__ float2 circle_centre(const float4* circ, const float2* vel, const float2* table, int n_circ,
-                                                int t, int kc, float st, bool has_table, bool moving) {
-    if (has_table) return table[(size_t)t * n_circ + kc];
-    const float4 c = circ[kc];
+// Centre at rollout step t (state x_{t+1}) of the circle c at sorted position pos: from the
+// centre table (column order[pos]), or moved at constant velocity from the given centre.
+__device__ __forceinline__ float2 circle_centre(const float4& c, const float2* vel, const int* order,
+                                                const float2* table, int n_circ, int t, int pos, float st,
+                                                bool has_table, bool moving) {
+    if (has_table) return table[(size_t)t * n_circ + order[pos]];
     if (!moving) return make_float2(c.x, c.y);
-    const float2 vv = vel[kc];
+    const float2 vv = vel[pos];
     return make_float2(fmaf(vv.x, st, c.x), fmaf(vv.y, st, c.y));
 }
 
@@ -681,11 +712,11 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const unsigne
         const int pos = base + lane;
         bool hit = false;
         if (pos < hi) {
-            const int kc = ci.order[pos];
             if (STATS) cnt.circ++;
-            const float2 cc = circle_centre(circ, vel, table, n_circ, tb0, kc, st0, has_table, moving);
-            const float lim = (mmax + circ[kc].z + pc.ego_rmax) * 1.0001f + 1e-4f;
-            const float ext = tb1 != tb0 && (has_table || moving) ? disp[kc] * (float)(tb1 - tb0) : 0.0f;
+            const float4 c = circ[pos];
+            const float2 cc = circle_centre(c, vel, ci.order, table, n_circ, tb0, pos, st0, has_table, moving);
+            const float lim = (mmax + c.z + pc.ego_rmax) * 1.0001f + 1e-4f;
+            const float ext = tb1 != tb0 && (has_table || moving) ? disp[pos] * (float)(tb1 - tb0) : 0.0f;
             const float dx = fmaxf(fmaxf(bx0 - cc.x, cc.x - bx1), 0.0f);
             const float dy = fmaxf(fmaxf(by0 - cc.y, cc.y - by1), 0.0f);
             hit = lim > 0.0f && fmaf(dx, dx, dy * dy) <= (lim + ext) * (lim + ext);
@@ -694,41 +725,46 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const unsigne
         for (int j = 0; m; ++j) {
             const int bit = __ffs(m) - 1;
             m &= m - 1;
-            if ((j & (G - 1)) != lane_g) continue;
+            if (G > 1 && (j & (G - 1)) != lane_g) continue;
             if (STATS) cnt.cand++;
-            const int kc2 = ci.order[base + bit];
-            const float4 c = circ[kc2];
-            const float2 cc = circle_centre(circ, vel, table, n_circ, t, kc2, st, has_table, moving);
+            const int pos2 = base + bit;
+            const float4 c = circ[pos2];
+            const float2 cc = circle_centre(c, vel, ci.order, table, n_circ, t, pos2, st, has_table, moving);
+            // the circle centre in the ego frame, along the heading (al) and across it (pr): the
+            // squared distance to the ego circle at offset o along the heading is (al - o)^2 + pr^2
+            const float wx = cc.x - nx, wy = cc.y - ny;
+            const float al = fmaf(wx, cnth, wy * snth);
+            const float pr = fmaf(wx, snth, -(wy * cnth));
+            const float p2 = pr * pr;
             if (dconst) {
                 // equal ego radii: the closest ego circle gives the pair minimum (sqrt and the
-                // subtraction are monotone), one square root per circle
-                float d2m = INFINITY;
+                // subtraction are monotone), one square root per circle; the minimum over the
+                // in-band circles is taken without a branch
+                float d2m;
                 if (pc.n_ego == 3) {        // the paper's ego model: three circles, no bound checks
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        const float dx = fmaf(pc.ego_off[e], cnth, nx) - cc.x, dy = fmaf(pc.ego_off[e], snth, ny) - cc.y;
-                        d2m = fminf(d2m, fmaf(dx, dx, dy * dy));
-                    }
+                    const float e0 = al - pc.ego_off[0], e1 = al - pc.ego_off[1], e2 = al - pc.ego_off[2];
+                    d2m = fminf(fminf(fmaf(e0, e0, p2), fmaf(e1, e1, p2)), fmaf(e2, e2, p2));
                 } else {
+                    d2m = INFINITY;
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         if (e >= pc.n_ego) break;
-                        const float dx = fmaf(pc.ego_off[e], cnth, nx) - cc.x, dy = fmaf(pc.ego_off[e], snth, ny) - cc.y;
-                        d2m = fminf(d2m, fmaf(dx, dx, dy * dy));
+                        const float de = al - pc.ego_off[e];
+                        d2m = fminf(d2m, fmaf(de, de, p2));
                     }
                 }
-                if (d2m <= c.w) {
-                    if (STATS) cnt.pair++;
-                    dobj = fminf(dobj, dist_of(d2m) - (c.z + pc.ego_rad[0]));
-                }
+                const bool in_band = d2m <= c.w;
+                if (STATS && in_band) cnt.pair++;
+                const float dd = dist_of(d2m) - (c.z + pc.ego_rad[0]);
+                dobj = in_band ? fminf(dobj, dd) : dobj;
             } else {
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     if (e >= pc.n_ego) break;
                     const float R = c.z + pc.ego_rad[e];
                     const float lim = mband + R;
-                    const float dx = fmaf(pc.ego_off[e], cnth, nx) - cc.x, dy = fmaf(pc.ego_off[e], snth, ny) - cc.y;
-                    const float d2 = fmaf(dx, dx, dy * dy);
+                    const float de = al - pc.ego_off[e];
+                    const float d2 = fmaf(de, de, p2);
                     if (lim > 0.0f && d2 <= lim * lim) {
                         if (STATS) cnt.pair++;
                         dobj = fminf(dobj, dist_of(d2) - R);
@@ -842,15 +878,15 @@ __device__ __forceinline__ StepIn dyn_step(const PlanConst& pc, const float4 ct,
 template <int G, bool STATS>
 __device__ __forceinline__ float state_cost(const PlanConst& pc, const SceneLayout& L, const Scene& sc,
                                             const float2* table, const StepIn& s, int t, int tb0, int tb1,
-                                            bool has_table, bool moving, bool dconst, int lane, int lane_g,
-                                            unsigned mask, int& jb, int& jbp, Counters& cnt) {
+                                            bool has_table, bool moving, bool multi_head, bool dconst, int lane,
+                                            int lane_g, unsigned mask, int& jb, int& jbp, Counters& cnt) {
     float d2r;
     if (pc.ref_mode == 0) {
         // search hint: the last closest segment moved on by its last change
         const int jh = min(max(2 * jb - jbp, 0), L.n_seg - 1);
         jbp = jb;
         nearest_segment<G, STATS>(s.nx, s.ny, sc.vert, sc.seg, sc.head, ref_boxes(sc.base, L), L.n_seg, L.n_l1,
-                                  lane_g, mask, jh, jb, d2r, cnt);
+                                  lane_g, mask, jh, multi_head, jb, d2r, cnt);
     } else {
         nearest_vertex<G>(s.nx, s.ny, sc.vert, sc.l1, ref_boxes(sc.base, L).l2, L.n_ref, L.n_l1, L.n_l2, lane_g, mask,
                           jb, d2r);
@@ -910,8 +946,9 @@ __device__ __forceinline__ float state_cost(const PlanConst& pc, const SceneLayo
 template <int G, bool TIME, bool BF16, bool STATS, bool EXT>
 __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneLayout& L, const unsigned char* smem,
                                                const typename NoiseT<BF16>::type* __restrict__ z,
-                                               const float2* table, float4 x0, float d0, bool moving, int jb0,
-                                               int k, double* S_out, unsigned long long* stats,
+                                               const float2* table, float4 x0, float d0, bool moving,
+                                               bool multi_head, int jb0, int k, double* S_out,
+                                               unsigned long long* stats,
                                                float* prefix = nullptr) {
     const Scene sc = scene_of(L, smem);
     const int lane = threadIdx.x & 31;
@@ -940,8 +977,8 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
         for (int t = 0; t < T; ++t) {
             const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
             const StepIn s = dyn_step<BF16, EXT>(pc, sc.ctl[t], sc.c0[t], zz, tp, r, steer_slot(smem, L));
-            const float qx = state_cost<G, STATS>(pc, L, sc, table, s, t, t, t, has_table, moving, dconst, lane,
-                                                  lane_g, mask, jb, jbp, cnt);
+            const float qx = state_cost<G, STATS>(pc, L, sc, table, s, t, t, t, has_table, moving, multi_head,
+                                                  dconst, lane, lane_g, mask, jb, jbp, cnt);
             if (EXT && prefix && lane_g == 0 && k < K) prefix[(size_t)t * K + k] = s_hi - s_c;   // cost of steps < t
             kahan_add(s_hi, s_c, qx + s.qu);    // Eq. (6)
             q_last = qx;
@@ -954,8 +991,78 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
             const int my = min(lane_g, nv - 1);
             const int tm = t0 + my;
             StepIn e;
-            if constexpr (G <= 2) {
-                // two lanes: integrating both steps in each lane is cheaper than the shuffles
+            if constexpr (G == 2 && !EXT) {
+                // two lanes, plain form: lane p perturbs the controls of step t0 + p and takes their
+                // tangent; yaw and speed advance through both steps in both lanes from the shuffled
+                // controls; lane p takes the sine and cosine of the yaw after its own step, and the
+                // positions advance through both steps from the shuffled directions.  The same
+                // operations as one lane per sample (dyn_step), so the same bits, with one tangent
+                // and one sine/cosine per step instead of two.
+                const float4 ct = sc.ctl[tm];
+                const Perturbed pe = perturb(ct.x, ct.y, NoiseT<BF16>::load(z + (size_t)tm * K + kk), pc.sig_a,
+                                             pc.sig_d, pc.amin, pc.amax, pc.dmin, pc.dmax);
+                const float tn_own = tanf(pe.vd);
+                // step t0 (lane 0's controls)
+                const float va0 = __shfl_sync(mask, pe.va, 0, 2), tn0 = __shfl_sync(mask, tn_own, 0, 2);
+                const float vt0 = r.v - r.v_c;
+                float acc = va0;
+                if (pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt0) / pc.dt), pc.amin);
+                kahan_add(r.th, r.th_c, __fmul_rn(__fmul_rn(vt0, tn0), pc.dt_over_L));
+                kahan_add(r.v, r.v_c, __fmul_rn(acc, pc.dt));
+                float th_own = r.th, thc_own = r.th_c, v_own = r.v, vc_own = r.v_c;
+                // step t0 + 1 (lane 1's controls), when there is one
+                const float va1 = __shfl_sync(mask, pe.va, 1, 2), tn1 = __shfl_sync(mask, tn_own, 1, 2);
+                const float vt1 = r.v - r.v_c;
+                if (nv == 2) {
+                    acc = va1;
+                    if (pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt1) / pc.dt), pc.amin);
+                    kahan_add(r.th, r.th_c, __fmul_rn(__fmul_rn(vt1, tn1), pc.dt_over_L));
+                    kahan_add(r.v, r.v_c, __fmul_rn(acc, pc.dt));
+                    if (my == 1) {
+                        th_own = r.th;
+                        thc_own = r.th_c;
+                        v_own = r.v;
+                        vc_own = r.v_c;
+                    }
+                }
+                sincosf(th_own, &e.snth, &e.cnth);
+                // positions: step t0 moves along the carried direction, step t0 + 1 along lane 0's
+                const float cn0 = __shfl_sync(mask, e.cnth, 0, 2), sn0 = __shfl_sync(mask, e.snth, 0, 2);
+                kahan_add(r.px, r.px_c, __fmul_rn(__fmul_rn(vt0, r.cth), pc.dt));
+                kahan_add(r.py, r.py_c, __fmul_rn(__fmul_rn(vt0, r.sth), pc.dt));
+                float tx = (r.px - tp.x) - r.px_c, ty = (r.py - tp.y) - r.py_c;
+                float tdn = fmaf(tx, tx, ty * ty);
+                e.nx = r.px;
+                e.ny = r.py;
+                e.px_c = r.px_c;
+                e.py_c = r.py_c;
+                e.c_target = tdn > r.tdp ? 1.0f : 0.0f;
+                r.tdp = tdn;
+                if (nv == 2) {
+                    kahan_add(r.px, r.px_c, __fmul_rn(__fmul_rn(vt1, cn0), pc.dt));
+                    kahan_add(r.py, r.py_c, __fmul_rn(__fmul_rn(vt1, sn0), pc.dt));
+                    tx = (r.px - tp.x) - r.px_c;
+                    ty = (r.py - tp.y) - r.py_c;
+                    tdn = fmaf(tx, tx, ty * ty);
+                    if (my == 1) {
+                        e.nx = r.px;
+                        e.ny = r.py;
+                        e.px_c = r.px_c;
+                        e.py_c = r.py_c;
+                        e.c_target = tdn > r.tdp ? 1.0f : 0.0f;
+                    }
+                    r.tdp = tdn;
+                }
+                r.cth = __shfl_sync(mask, e.cnth, nv - 1, 2);
+                r.sth = __shfl_sync(mask, e.snth, nv - 1, 2);
+                e.th = th_own;
+                e.th_c = thc_own;
+                e.dv = (v_own - pc.v_ref) - vc_own;
+                e.ds = fmaf(pc.d_safe_c, v_own - vc_own, pc.d_safe_0);
+                e.qu = fmaf(ct.z, pe.ea, fmaf(ct.w, pe.ed, sc.c0[tm]));
+            } else if constexpr (G <= 2) {
+                // two lanes with the steering-rate model or the cost-to-go form: both lanes
+                // integrate both steps
 #pragma unroll 1
                 for (int j = 0; j < nv; ++j) {
                     const int t = t0 + j;
@@ -1036,8 +1143,8 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
             e.qu = fmaf(ct.z, pe.ea, fmaf(ct.w, pe.ed, sc.c0[tm]));
             }
             const int tb1 = min(t0 + G - 1, T - 1);
-            const float qx = state_cost<1, STATS>(pc, L, sc, table, e, tm, t0, tb1, has_table, moving, dconst,
-                                                  lane, 0, mask, jb, jbp, cnt);
+            const float qx = state_cost<1, STATS>(pc, L, sc, table, e, tm, t0, tb1, has_table, moving, multi_head,
+                                                  dconst, lane, 0, mask, jb, jbp, cnt);
             const float c = qx + e.qu;
             float pre_own = 0.0f;
 #pragma unroll
@@ -1458,6 +1565,7 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
             st->status = s_status;
             st->flags = 0;
             st->moving = 0;
+            st->multi_head = 0;
             st->jkey = ~0ull;
             copy_state(st, in.state_out);
         }
@@ -1557,6 +1665,7 @@ __device__ __forceinline__ void finalize_block(const PlanConst& pc, const PlanBu
         st->iter += 1ull;
         st->flags = 0;
         st->moving = 0;
+        st->multi_head = 0;
         st->jkey = ~0ull;
         copy_state(st, in.state_out);
     }

@@ -187,10 +187,11 @@ __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 1) rollout_kernel(PlanCon
     pdl_wait();
     const bool staged = __syncthreads_and(stage_to_smem(smem, b.scene, L.bytes, &bar, &b.state->flags));
     if (staged) {
-        build_boxes(smem, L, b.table, pc.has_table != 0);
+        build_boxes(smem, L);
         const int k = (blockIdx.x * blockDim.x + threadIdx.x) / G;
         rollout_sample<G, TIME, BF16, STATS, EXT>(pc, L, smem, z, b.table, b.state->x0f, b.state->delta0f,
-                                             b.state->moving != 0, (int)(b.state->jkey & 0xffffffffu), k, b.S,
+                                             b.state->moving != 0, b.state->multi_head != 0,
+                                             (int)(b.state->jkey & 0xffffffffu), k, b.S,
                                              b.stats, pc.cost_to_go ? b.ctg_prefix : nullptr);
     }
     pdl_trigger();   // after the block's samples: the rollout may run in several waves
@@ -421,6 +422,7 @@ cudaError_t launch_prep_noise(const PlanConst& pc, const SceneLayout& L, const P
 __global__ void reset_state_kernel(DevState* st) {
     st->flags = 0;
     st->moving = 0;
+    st->multi_head = 0;
     st->jkey = ~0ull;
 }
 

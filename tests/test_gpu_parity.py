@@ -361,9 +361,10 @@ def test_rollout_stats_are_consistent_and_leave_state():
         U, it = pl.get_controls()
         np.testing.assert_array_equal(U, U0)
         assert it == 3
-        # straight lane: the neighbours of the scanned chunk and one prefix and one suffix box
-        # (fewer at the ends of the lane); the fallback ranges never open
-        assert 1.0 <= st["range_boxes"] <= 2.0 and 1.0 <= st["chunk_boxes"] <= 2.0
+        # straight lane: one box of the chunks before the scanned chunk and one of those after it
+        # (fewer at the ends of the lane); a side whose box passes adds its neighbour chunk box
+        # and the box beyond it; the fallback ranges never open
+        assert 1.0 <= st["range_boxes"] <= 4.0 and 0.0 <= st["chunk_boxes"] <= 2.0
         assert 1 <= st["segments"] <= prob.ref.shape[0]
         # the broad phase tests one circle per lane per 32 circles of the indexed range, at most
         # every circle; on this lane of 200 m the range around a warp is a few circles
