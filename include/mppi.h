@@ -171,6 +171,37 @@ int mppi_plan_device(mppi_ctx* ctx, const double* d_x0, const double* d_ref_xy, 
                      const double* d_circ, int32_t n_circ, const double* d_centres,
                      double* d_u_out, double* d_x_out, mppi_info* info);
 
+/* ------------------------------------------------------------------------------------
+   K-partitioned iteration (the multi-GPU form of one iteration).  Both sums of the update,
+   Eq. (11), run over the samples, so K splits into slices, one per context (normally one per
+   GPU), with two exchanges between them:
+     1. mppi_slice_costs on every slice: noise, rollouts and costs of the slice's samples and
+        the slice's lowest cost; the caller takes the minimum over the slices (ties: the lowest
+        global index) and the sum of the finite counts;
+     2. mppi_slice_sums on every slice with that global minimum: the slice's softmin normaliser
+        eta = sum_k exp(-(S_k - S_min) / lambda) and its weighted noise sums
+        du[t][c] = sum_k w_k eps'_{t,k,c} (binary64, not divided by eta); the caller adds them
+        up over the slices;
+     3. mppi_slice_finalize on every slice with the totals: u += du / eta, clamp, Savitzky-Golay
+        (Eq. (19)), x* and the warm start, the same on every slice.
+   A context holds the K = params->K samples k_offset .. k_offset + K - 1 of the whole plan: the
+   Philox counter takes the global index, so the noise, the costs and the result do not depend
+   on how the samples are split.  The sums match the unsplit iteration to the rounding of
+   binary64 additions when every slice but the last holds a multiple of 2048 samples (the
+   weighted sums' binary32 partials then group the same samples), otherwise to that of the
+   binary32 partials.  The slices must share every parameter but K and the iteration counter
+   (mppi_set_controls).  The cost-to-go form is refused (MPPI_ERR_ARG).  Errors: as for
+   mppi_plan; a stage out of order is MPPI_ERR_ARG. */
+int mppi_slice_costs(mppi_ctx* ctx, int64_t k_offset, const double* x0, const double* ref_xy, int32_t n_ref,
+                     const mppi_circle* circ, int32_t n_circ, const double* centres, double* s_min, int32_t* argmin,
+                     int32_t* n_finite);
+/* s_min: the global minimum; eta and du[T][2]: this slice's sums (host outputs). */
+int mppi_slice_sums(mppi_ctx* ctx, double s_min, double* eta, double* du);
+/* eta, du[T][2], n_finite: the totals over all slices; s_min and argmin (global index) are
+   reported in info.  u_out[T][2] and x_out[T+1][nx] as for mppi_plan. */
+int mppi_slice_finalize(mppi_ctx* ctx, double eta, const double* du, int32_t n_finite, double s_min, int32_t argmin,
+                        double* u_out, double* x_out, mppi_info* info);
+
 /* Autotuner: times the rollout kernel for every lanes-per-sample group (1..32, -2..-16) and
    block size (64, 128, 256, and sizes that spread the lanes evenly over the SMs with
    1 to 4 resident blocks each, up to 896 threads) on the given inputs (host arrays, as for mppi_plan) and
@@ -200,6 +231,17 @@ int mppi_rollout_stats(mppi_ctx* ctx, const double* x0, const double* ref_xy, in
 
 /* Waits for the context's queued work and returns the status of the last iteration. */
 int mppi_sync(mppi_ctx* ctx, mppi_info* info);
+
+/* Debug (failure-path testing without a device fault; no counterpart in the paper): the next
+   iteration of the context writes these status flags into its device record between the
+   rollout and the update, as a kernel that detected the condition would.  MPPI_FLAG_TIMEOUT
+   makes that iteration end with MPPI_ERR_TIMEOUT (as when a bounded device wait runs out) and
+   MPPI_FLAG_NONFINITE_INPUT with MPPI_ERR_ARG; either way the warm start and the iteration
+   counter are left as they were and the context stays usable.  One-shot; the iteration runs
+   uncaptured.  MPPI_ERR_ARG for other bits. */
+#define MPPI_FLAG_NONFINITE_INPUT 1
+#define MPPI_FLAG_TIMEOUT 2
+int mppi_debug_inject_flags(mppi_ctx* ctx, int32_t flags);
 
 /* Warm start I/O (checkpoint / resume): U[T][2] host doubles and the iteration index. */
 int mppi_set_controls(mppi_ctx* ctx, const double* U, uint64_t iter);

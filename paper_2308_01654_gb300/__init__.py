@@ -31,6 +31,9 @@ MAX_T = 1024
 MAX_REF = 4096
 MAX_CIRC = 1024
 
+FLAG_NONFINITE_INPUT = 1
+FLAG_TIMEOUT = 2
+
 STATUS = {0: "MPPI_OK", -1: "MPPI_ERR_ARG", -2: "MPPI_ERR_OOM", -3: "MPPI_ERR_CUDA", -4: "MPPI_ERR_NUMERIC",
           -5: "MPPI_ERR_TIMEOUT", -6: "MPPI_ERR_CAPACITY"}
 
@@ -89,6 +92,12 @@ SIGNATURES = {
     "mppi_set_profiling": (C.c_int, [_VP, C.c_int32]),
     "mppi_kernel_times": (C.c_int, [_VP, _VP, C.c_int32]),
     "mppi_argmin_noalloc": (C.c_int, [_VP, C.c_int32, _VP, _VP, _VP, _VP]),
+    "mppi_debug_inject_flags": (C.c_int, [_VP, C.c_int32]),
+    "mppi_slice_costs": (C.c_int, [_VP, C.c_int64, _VP, _VP, C.c_int32, _VP, C.c_int32, _VP, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "mppi_slice_sums": (C.c_int, [_VP, C.c_double, C.POINTER(C.c_double), _VP]),
+    "mppi_slice_finalize": (C.c_int, [_VP, C.c_double, _VP, C.c_int32, C.c_double, C.c_int32, _VP, _VP,
+                                      C.POINTER(MppiInfo)]),
     "mppi_batch_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_int32,
                                     C.c_int32, C.c_int32, C.c_int, C.POINTER(_VP)]),
     "mppi_batch_destroy": (C.c_int, [_VP]),
@@ -306,6 +315,43 @@ class Planner:
         z = np.empty((self.T, self.K, 2), dtype=np.float32)
         _check(lib().mppi_get_noise(self._h, _dp(z)), self._h)
         return z
+
+    def debug_inject_flags(self, flags: int):
+        """Debug: the next iteration raises these device status flags between its rollout and
+        its update (FLAG_TIMEOUT = 2, FLAG_NONFINITE_INPUT = 1)."""
+        _check(lib().mppi_debug_inject_flags(self._h, int(flags)), self._h)
+
+    # K-partitioned iteration (this context holds samples k_offset .. k_offset + K - 1) -----
+    def slice_costs(self, k_offset: int, x0, ref, circles=None, centres=None):
+        """Noise, rollouts and costs of this slice; returns (s_min, global argmin, n_finite)."""
+        x0 = _f64(x0)
+        ref = _f64(ref).reshape(-1, 2)
+        circ = _f64(np.zeros((0, 5)) if circles is None else circles).reshape(-1, 5)
+        cen = None if centres is None else _f64(centres)
+        s, a, n = C.c_double(), C.c_int32(), C.c_int32()
+        rc = lib().mppi_slice_costs(self._h, int(k_offset), _dp(x0), _dp(ref), ref.shape[0],
+                                    _dp(circ) if circ.shape[0] else None, circ.shape[0], _dp(cen), C.byref(s),
+                                    C.byref(a), C.byref(n))
+        _check(rc, self._h)
+        return s.value, a.value, n.value
+
+    def slice_sums(self, s_min: float):
+        """The slice's softmin normaliser and weighted noise sums against the global minimum."""
+        eta = C.c_double()
+        du = np.empty((self.T, 2))
+        _check(lib().mppi_slice_sums(self._h, float(s_min), C.byref(eta), _dp(du)), self._h)
+        return eta.value, du
+
+    def slice_finalize(self, eta: float, du, n_finite: int, s_min: float, argmin: int):
+        """The update from the totals over all slices; returns (u*, x*, info) like plan()."""
+        du = _f64(du).reshape(self.T, 2)
+        u = np.empty((self.T, 2))
+        x = np.empty((self.T + 1, self.nx))
+        info = MppiInfo()
+        rc = lib().mppi_slice_finalize(self._h, float(eta), _dp(du), int(n_finite), float(s_min), int(argmin),
+                                       _dp(u), _dp(x), C.byref(info))
+        _check(rc, self._h)
+        return u, x, info.as_dict()
 
 
 KERNELS = ("prep", "noise", "rollout", "argmin", "weights", "wsum", "finalize")

@@ -6,6 +6,7 @@
 
 #include <new>
 #include <string>
+#include <vector>
 
 #include "mppi.h"
 #include "mppi_device.cuh"
@@ -40,6 +41,12 @@ struct mppi_ctx {
     long long graph_key = -1, seen_key = -1;
     size_t graph_n_in = 0;
     cudaEvent_t ev[N_KERNELS + 1] = {};
+    // K-partitioned iteration: the inputs staged by mppi_slice_costs and the stage reached
+    // (0 none, 1 costs done, 2 sums done)
+    PlanInputs slice_in{};
+    int slice_stage = 0;
+    // debug: status flags the next iteration raises between its rollout and its update
+    int inject_flags = 0;
     std::string err;
 };
 
@@ -398,8 +405,11 @@ static int enqueue(mppi_ctx* c, const PlanInputs& in, int has_table) {
     const SceneLayout L = make_layout(c->p.T, in.n_ref, in.n_circ);
     PlanConst pc = c->pc;
     pc.has_table = has_table;
+    // an armed injection is copied from pageable memory (staged before the call returns)
+    const int inject = c->inject_flags;
+    c->inject_flags = 0;
     CK(launch_iteration(pc, L, c->b, in, c->group, c->threads, c->p.noise_bf16, c->stream,
-                        c->profiling ? c->ev : nullptr, c->profiling),
+                        c->profiling ? c->ev : nullptr, c->profiling, inject ? &inject : nullptr),
        "kernel launch");
     return MPPI_OK;
 }
@@ -488,7 +498,8 @@ int mppi_plan(mppi_ctx* c, const double* x0, const double* ref_xy, int32_t n_ref
     in.u_out = c->h_out_dev;
     in.x_out = c->h_out_dev + 2 * (size_t)T;
     in.state_out = c->h_state_dev;
-    if (c->profiling) {
+    if (c->profiling || c->inject_flags) {
+        // traced or injected iterations run uncaptured
         CK(cudaMemcpyAsync(c->d_in, c->h_in, n_in * sizeof(double), cudaMemcpyHostToDevice, c->stream), "input copy");
         rc = enqueue(c, in, in.centres ? 1 : 0);
         if (rc != MPPI_OK) return rc;
@@ -551,6 +562,109 @@ int mppi_plan_device(mppi_ctx* c, const double* d_x0, const double* d_ref_xy, in
     rc = enqueue(c, in, d_centres ? 1 : 0);
     if (rc != MPPI_OK) return rc;
     if (info) return wait_status(c, info);
+    return MPPI_OK;
+}
+
+int mppi_debug_inject_flags(mppi_ctx* c, int32_t flags) {
+    if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
+    if (flags & ~(FLAG_NONFINITE_INPUT | FLAG_TIMEOUT)) return fail(c, MPPI_ERR_ARG, "unknown flag bits");
+    c->inject_flags = flags;
+    return MPPI_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// K-partitioned iteration (one slice of the samples per context; see include/mppi.h)
+// ------------------------------------------------------------------------------------
+int mppi_slice_costs(mppi_ctx* c, int64_t k_offset, const double* x0, const double* ref_xy, int32_t n_ref,
+                     const mppi_circle* circ, int32_t n_circ, const double* centres, double* s_min, int32_t* argmin,
+                     int32_t* n_finite) {
+    if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
+    if (!s_min || !argmin || !n_finite) return fail(c, MPPI_ERR_ARG, "NULL output argument");
+    if (c->p.cost_to_go) return fail(c, MPPI_ERR_ARG, "the K-partitioned iteration runs the whole-cost weights");
+    if (k_offset < 0 || k_offset + (int64_t)c->p.K > (int64_t)INT32_MAX)
+        return fail(c, MPPI_ERR_ARG, "k_offset must be >= 0 and the global sample indices below 2^31");
+    c->slice_stage = 0;
+    PlanInputs in;
+    int rc = stage_host_inputs(c, x0, ref_xy, n_ref, circ, n_circ, centres, in);
+    if (rc != MPPI_OK) return rc;
+    const SceneLayout L = make_layout(c->p.T, in.n_ref, in.n_circ);
+    PlanConst pc = c->pc;
+    pc.has_table = in.centres ? 1 : 0;
+    pc.k_offset = (uint32_t)k_offset;
+    CK(launch_slice_costs(pc, L, c->b, in, c->group, c->threads, c->p.noise_bf16, c->stream), "kernel launch");
+    CK(cudaMemcpyAsync(c->h_state, c->b.state, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "state copy");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    const DevState& s = *c->h_state;
+    if (s.flags & FLAG_NONFINITE_INPUT) rc = fail(c, MPPI_ERR_ARG, "non-finite input detected on the device");
+    else if (s.flags & FLAG_TIMEOUT) rc = fail(c, MPPI_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (rc != MPPI_OK) {
+        CK(launch_reset_state(c->b.state, c->stream), "state reset");
+        CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+        return rc;
+    }
+    *s_min = s.n_finite > 0 ? s.s_min : INFINITY;
+    *argmin = s.n_finite > 0 ? (int32_t)(s.argmin + k_offset) : -1;
+    *n_finite = s.n_finite;
+    c->slice_in = in;
+    c->slice_stage = 1;
+    return MPPI_OK;
+}
+
+int mppi_slice_sums(mppi_ctx* c, double s_min, double* eta, double* du) {
+    if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
+    if (!eta || !du) return fail(c, MPPI_ERR_ARG, "NULL output argument");
+    if (c->slice_stage != 1) return fail(c, MPPI_ERR_ARG, "mppi_slice_costs must come first");
+    if (isnan(s_min)) return fail(c, MPPI_ERR_ARG, "s_min is NaN");
+    const int T = c->p.T;
+    const SceneLayout L = make_layout(T, c->slice_in.n_ref, c->slice_in.n_circ);
+    CK(cudaMemcpyAsync(&c->b.state->s_min, &s_min, sizeof(double), cudaMemcpyHostToDevice, c->stream), "s_min copy");
+    CK(launch_slice_sums(c->pc, L, c->b, c->p.noise_bf16, c->stream), "kernel launch");
+    CK(cudaMemcpyAsync(c->h_out, c->b.du, sizeof(double) * 2 * (size_t)T, cudaMemcpyDeviceToHost, c->stream),
+       "sums copy");
+    std::vector<double> parts((size_t)c->b.n_wblk);
+    CK(cudaMemcpyAsync(parts.data(), c->b.eta_part, sizeof(double) * parts.size(), cudaMemcpyDeviceToHost, c->stream),
+       "eta copy");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    double e = 0.0;
+    for (double v : parts) e += v;      // block order
+    *eta = e;
+    memcpy(du, c->h_out, sizeof(double) * 2 * (size_t)T);
+    c->slice_stage = 2;
+    return MPPI_OK;
+}
+
+int mppi_slice_finalize(mppi_ctx* c, double eta, const double* du, int32_t n_finite, double s_min, int32_t argmin,
+                        double* u_out, double* x_out, mppi_info* info) {
+    if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
+    if (!du || !u_out || !x_out) return fail(c, MPPI_ERR_ARG, "NULL array argument");
+    if (c->slice_stage != 2) return fail(c, MPPI_ERR_ARG, "mppi_slice_sums must come first");
+    const int T = c->p.T;
+    if (!finite_all(du, 2 * (size_t)T) || isnan(eta) || n_finite < 0)
+        return fail(c, MPPI_ERR_ARG, "non-finite sums or a negative count");
+    // the exchanged totals take the place of this slice's own: du, eta (first partial, the
+    // others zero), the finite count and the global minimum
+    memcpy(c->h_out, du, sizeof(double) * 2 * (size_t)T);
+    CK(cudaMemcpyAsync(c->b.du, c->h_out, sizeof(double) * 2 * (size_t)T, cudaMemcpyHostToDevice, c->stream),
+       "sums copy");
+    CK(cudaMemsetAsync(c->b.eta_part, 0, sizeof(double) * (size_t)c->b.n_wblk, c->stream), "eta reset");
+    CK(cudaMemcpyAsync(c->b.eta_part, &eta, sizeof(double), cudaMemcpyHostToDevice, c->stream), "eta copy");
+    CK(cudaMemcpyAsync(&c->b.state->n_finite, &n_finite, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream),
+       "count copy");
+    CK(cudaMemcpyAsync(&c->b.state->s_min, &s_min, sizeof(double), cudaMemcpyHostToDevice, c->stream), "s_min copy");
+    CK(cudaMemcpyAsync(&c->b.state->argmin, &argmin, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream),
+       "argmin copy");
+    PlanInputs in = c->slice_in;
+    in.u_out = c->d_out;
+    in.x_out = c->d_out + 2 * (size_t)T;
+    in.state_out = nullptr;
+    CK(launch_slice_finalize(c->pc, c->b, in, c->stream), "kernel launch");
+    CK(cudaMemcpyAsync(c->h_out, c->d_out, sizeof(double) * c->out_elems, cudaMemcpyDeviceToHost, c->stream),
+       "output copy");
+    c->slice_stage = 0;
+    const int rc = wait_status(c, info);
+    if (rc != MPPI_OK) return rc;
+    memcpy(u_out, c->h_out, 2 * (size_t)T * sizeof(double));
+    memcpy(x_out, c->h_out + 2 * (size_t)T, (size_t)c->nx * (size_t)(T + 1) * sizeof(double));
     return MPPI_OK;
 }
 

@@ -84,6 +84,7 @@ struct PlanConst {
     double inv_dt_d;         // 1 / dt
     double dt_over_wb_d;     // dt / wheelbase
     float inv_lam_f;         // 1 / lambda
+    uint32_t k_offset;       // global index of sample 0 (a K-slice of a partitioned plan; else 0)
 };
 
 SceneLayout make_layout(int T, int n_ref, int n_circ);
@@ -147,9 +148,21 @@ struct PlanInputs {
 // fix-up, the argmin stage empty since the rollout kernel ends with the argmin), 2 only ev[2]
 // and ev[3] around the rollout (the rest stays chained).
 constexpr int N_KERNELS = 7;   // prep, noise, rollout, argmin, weights, wsum, finalize
+// inject: status flags written into the device record between the rollout and the weights
+// (debug: the failure path without a fault; 0 = none; the source must outlive the launch).
 cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
                              const PlanInputs& in, int group, int threads, int noise_bf16, cudaStream_t st,
-                             cudaEvent_t* ev = nullptr, int ev_mode = 1);
+                             cudaEvent_t* ev = nullptr, int ev_mode = 1, const int* inject = nullptr);
+
+// The iteration split at the two exchanges of a K-partitioned plan (each context holds the
+// slice of samples k_offset .. k_offset + K - 1): costs (prep, noise, rollout with the slice's
+// S_min and argmin), sums (softmin weights against the global S_min and the weighted noise
+// sums), finalize (update, smoothing, x*, warm start from the summed eta and du).
+cudaError_t launch_slice_costs(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
+                               const PlanInputs& in, int group, int threads, int noise_bf16, cudaStream_t st);
+cudaError_t launch_slice_sums(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int noise_bf16,
+                              cudaStream_t st);
+cudaError_t launch_slice_finalize(const PlanConst& pc, const PlanBuffers& b, const PlanInputs& in, cudaStream_t st);
 
 // prep + noise only (no change to the warm start or the iteration counter) and the
 // reset of the fields prep accumulates into; used by the autotuner.

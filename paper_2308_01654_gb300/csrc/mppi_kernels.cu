@@ -79,7 +79,9 @@ __device__ __forceinline__ void noise_pair(const PlanConst& pc, const DevState* 
                                            unsigned* fix_count, uint2* fix_list, int k, int j) {
     if (k >= pc.K) return;
     const uint32_t it = (uint32_t)st->iter;
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)k, it, pc.session), make_uint2(pc.key0, pc.key1));
+    // the counter takes the sample's global index (k_offset: first sample of a K-slice)
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)k + pc.k_offset, it, pc.session),
+                                  make_uint2(pc.key0, pc.key1));
     const size_t K = (size_t)pc.K;
     const bool two = 2 * j + 1 < pc.T;
     const unsigned long long keep = l2_keep_policy();
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(32) noise_fix_kernel(PlanConst pc, const DevSt
     const size_t K = (size_t)pc.K;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint2 jk = fix_list[i];
-        const uint4 w = philox4x32_10(make_uint4(jk.x, jk.y, it, pc.session), make_uint2(pc.key0, pc.key1));
+        const uint4 w = philox4x32_10(make_uint4(jk.x, jk.y + pc.k_offset, it, pc.session), make_uint2(pc.key0, pc.key1));
         z[(size_t)(2 * jk.x) * K + jk.y] = make_noise<true>(uniform24(w.x), uniform24(w.y));
         if (2 * (int)jk.x + 1 < pc.T)
             z[(size_t)(2 * jk.x + 1) * K + jk.y] = make_noise<true>(uniform24(w.z), uniform24(w.w));
@@ -433,7 +435,7 @@ cudaError_t launch_reset_state(DevState* st, cudaStream_t s) {
 
 cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
                              const PlanInputs& in, int group, int threads, int noise_bf16, cudaStream_t st,
-                             cudaEvent_t* ev, int ev_mode) {
+                             cudaEvent_t* ev, int ev_mode, const int* inject) {
     // ev_mode 1: an event before the first kernel and after each (every boundary timed, none
     // chained); 2: only the two around the rollout (ev[2], ev[3]), the other kernels stay chained
     cudaError_t e;
@@ -456,6 +458,8 @@ cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const Pl
     if ((e = mark()) != cudaSuccess) return e;
     // argmin: folded into the rollout kernel (its last block); the stage keeps its event
     if ((e = mark()) != cudaSuccess) return e;
+    if (inject && (e = cudaMemcpyAsync(&b.state->flags, inject, sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return e;
     if (pc.cost_to_go)
         e = launch_chained(ctg_weights_kernel, dim3(pc.T), dim3(256), 0, st, pc.K, pc.inv_lam_f, b);
     else
@@ -478,6 +482,27 @@ cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const Pl
     if ((e = launch_chained(finalize_kernel, dim3(1), dim3(((pc.T + 31) / 32) * 32), 0, st, pc, b, in)) != cudaSuccess)
         return e;
     return mark();
+}
+
+cudaError_t launch_slice_costs(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b,
+                               const PlanInputs& in, int group, int threads, int noise_bf16, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = launch_prep_noise_k(pc, L, b, in, noise_bf16, st)) != cudaSuccess) return e;
+    if (noise_bf16 && (e = launch_noise_fix(pc, b, st)) != cudaSuccess) return e;
+    return launch_rollout(pc, L, b, group, threads, noise_bf16, st);
+}
+
+cudaError_t launch_slice_sums(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int noise_bf16,
+                              cudaStream_t st) {
+    cudaError_t e = launch_chained(weights_kernel, dim3(b.n_wblk), dim3(256), 0, st, pc.K, pc.inv_lam_f, b);
+    if (e != cudaSuccess) return e;
+    const dim3 grid(b.n_kt, b.n_tt);
+    if (noise_bf16) return launch_wsum<true, false>(pc, L, b, reinterpret_cast<const __nv_bfloat162*>(b.z), grid, st);
+    return launch_wsum<false, false>(pc, L, b, reinterpret_cast<const float2*>(b.z), grid, st);
+}
+
+cudaError_t launch_slice_finalize(const PlanConst& pc, const PlanBuffers& b, const PlanInputs& in, cudaStream_t st) {
+    return launch_chained(finalize_kernel, dim3(1), dim3(((pc.T + 31) / 32) * 32), 0, st, pc, b, in);
 }
 
 cudaError_t launch_philox(uint2 key, const uint4* ctr, uint4* out, int n, cudaStream_t st) {

@@ -480,3 +480,46 @@ def test_cost_to_go_reading_changes_the_update():
     b, _, _, _ = run_gpu(prob, params=dict(prob.params, cost_to_go=1))
     np.testing.assert_array_equal(a[0][3], b[0][3])                   # same sample costs
     assert np.abs(a[0][0] - b[0][0]).max() > 1e-6                     # different update
+
+
+# ----------------------------------------------------------------------------- failure path
+
+@pytest.mark.parametrize("flag,status", [(mp.FLAG_TIMEOUT, -5), (mp.FLAG_NONFINITE_INPUT, -1)])
+@pytest.mark.parametrize("entry", ["host", "device"])
+def test_injected_device_flag_ends_the_iteration_and_keeps_the_state(flag, status, entry):
+    """The status a kernel raises when a bounded wait runs out (or it sees non-finite input),
+    written into the device record between the rollout and the update from the host: the
+    iteration ends with that status, the warm start and the iteration counter stay, and the next
+    iteration runs normally.  No kernel faults or waits on anything."""
+    torch = pytest.importorskip("torch")
+    prob = sc.single_plan()
+    prob.params.update(K=512, T=20)
+    U0 = np.random.default_rng(4).normal(size=(20, 2)) * [0.2, 0.02]
+    with mp.Planner(prob.params, stream=torch.cuda.current_stream().cuda_stream) as pl:
+        for rep in range(2):                         # also after the host-buffer graph is captured
+            pl.set_controls(U0, 3)
+            pl.plan(prob.x0, prob.ref, prob.circles)
+            pl.plan(prob.x0, prob.ref, prob.circles)
+        pl.set_controls(U0, 3)
+        pl.debug_inject_flags(flag)
+        with pytest.raises(mp.MppiError) as e:
+            if entry == "host":
+                pl.plan(prob.x0, prob.ref, prob.circles)
+            else:
+                dev = torch.device("cuda:0")
+                t = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+                u = torch.empty((20, 2), dtype=torch.float64, device=dev)
+                x = torch.empty((21, 4), dtype=torch.float64, device=dev)
+                pl.plan_device(t(prob.x0), t(prob.ref), t(prob.circles), None, u, x, wait=True)
+        assert e.value.status == status
+        U, it = pl.get_controls()
+        np.testing.assert_array_equal(U, U0)
+        assert it == 3
+        u, x, info = pl.plan(prob.x0, prob.ref, prob.circles)     # the context stays usable
+        assert info["iter"] == 3
+        orc = oracle.plan(prob, U=U0, iter_=3)
+        check_iteration(prob, (u, x, info, pl.get_costs()), orc)
+    with mp.Planner(prob.params) as pl:
+        with pytest.raises(mp.MppiError) as e:
+            pl.debug_inject_flags(8)
+        assert e.value.status == -1
