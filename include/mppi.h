@@ -243,6 +243,17 @@ int mppi_sync(mppi_ctx* ctx, mppi_info* info);
 #define MPPI_FLAG_TIMEOUT 2
 int mppi_debug_inject_flags(mppi_ctx* ctx, int32_t flags);
 
+/* Debug (no counterpart in the paper): the library built with -DMPPI_CHECKS (libmppi_checks.so)
+   tests every index the rollout kernels read from the staged scene, the circle index, the
+   controls and the centre table against its array's length, and the block's dynamic shared
+   memory against the scene it stages; a violation is counted and the read moved to index 0, so
+   nothing traps.  *enabled = 1 in that build (0 otherwise, where the checks are compiled out);
+   *hits = the violations counted since the last call (then reset; 0 in the normal build).
+   mppi_debug_check_selftest runs, on `device`, one kernel with two out-of-range indices and
+   reports the count it leaves (2 in the checks build, 0 otherwise). */
+int mppi_debug_check_hits(int32_t* enabled, uint64_t* hits);
+int mppi_debug_check_selftest(int device, uint64_t* hits);
+
 /* Warm start I/O (checkpoint / resume): U[T][2] host doubles and the iteration index. */
 int mppi_set_controls(mppi_ctx* ctx, const double* U, uint64_t iter);
 int mppi_get_controls(mppi_ctx* ctx, double* U, uint64_t* iter);
@@ -359,6 +370,8 @@ typedef struct {
     int32_t device;
     int64_t hbm_budget_bytes;   /* admission limit on the footprint of all requests in flight */
     double max_wait_us;         /* a batch may wait this long to grow while others run (0: never waits) */
+    double watchdog_ms;         /* host-side watchdog: a micro-batch still running this long after its
+                                   submission is abandoned (0: off; see mppi_server_set_watchdog) */
 } mppi_server_config;
 
 typedef struct {
@@ -398,6 +411,23 @@ int mppi_server_pending(mppi_server* server, int32_t* queued, int32_t* in_flight
 
 /* Warm start of an idle session (checkpoint / resume). */
 int mppi_server_set_controls(mppi_server* server, int32_t session, const double* U, int32_t T, uint64_t iter);
+
+/* Host-side watchdog (no counterpart in the paper): a micro-batch still running watchdog_ms
+   after its submission is abandoned.  Its requests complete at once with MPPI_ERR_TIMEOUT
+   (latency stamped then, u* and x* not given); the device work cannot be stopped, so their
+   sessions, HBM budget and pipeline stay taken until it has ended, when its results are dropped
+   (the sessions' warm starts are what that work left).  0 turns the watchdog off.
+   mppi_server_timeouts gives the number of requests completed that way so far. */
+int mppi_server_set_watchdog(mppi_server* server, double watchdog_ms);
+int mppi_server_timeouts(mppi_server* server, uint64_t* n);
+
+/* Session table to and from a file (checkpoint / resume of every session's warm start and
+   iteration counter; no counterpart in the paper): the server must be idle (no request queued
+   or in flight), else MPPI_ERR_CAPACITY.  The file holds "MPPISNAP", version 1, max_sessions,
+   max_T, then per session its counter and U[max_T][2] in this host's byte order; restore
+   refuses (MPPI_ERR_ARG) a file of another size or version, or a truncated one. */
+int mppi_server_snapshot(mppi_server* server, const char* path);
+int mppi_server_restore(mppi_server* server, const char* path);
 const char* mppi_server_last_error(mppi_server* server);
 
 /* Allocation-free lowest-cost search.  The paper has no counterpart: this is a

@@ -93,6 +93,8 @@ SIGNATURES = {
     "mppi_kernel_times": (C.c_int, [_VP, _VP, C.c_int32]),
     "mppi_argmin_noalloc": (C.c_int, [_VP, C.c_int32, _VP, _VP, _VP, _VP]),
     "mppi_debug_inject_flags": (C.c_int, [_VP, C.c_int32]),
+    "mppi_debug_check_hits": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]),
+    "mppi_debug_check_selftest": (C.c_int, [C.c_int, C.POINTER(C.c_uint64)]),
     "mppi_slice_costs": (C.c_int, [_VP, C.c_int64, _VP, _VP, C.c_int32, _VP, C.c_int32, _VP, C.POINTER(C.c_double),
                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "mppi_slice_sums": (C.c_int, [_VP, C.c_double, C.POINTER(C.c_double), _VP]),
@@ -121,6 +123,10 @@ SIGNATURES = {
     "mppi_server_pending": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_uint64),
                                       C.POINTER(C.c_uint64)]),
     "mppi_server_set_controls": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, C.c_uint64]),
+    "mppi_server_set_watchdog": (C.c_int, [_VP, C.c_double]),
+    "mppi_server_timeouts": (C.c_int, [_VP, C.POINTER(C.c_uint64)]),
+    "mppi_server_snapshot": (C.c_int, [_VP, C.c_char_p]),
+    "mppi_server_restore": (C.c_int, [_VP, C.c_char_p]),
     "mppi_server_last_error": (C.c_char_p, [_VP]),
     "mppi_status_string": (C.c_char_p, [C.c_int]),
     "mppi_last_error": (C.c_char_p, [_VP]),
@@ -131,18 +137,53 @@ def library_path() -> str:
     return _build.LIB
 
 
+def load_library(path: str):
+    """Load a build of the library at `path` with every entry point's signature."""
+    L = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
 def lib():
     """Build (if needed) and load libmppi.so; raises if that is impossible."""
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
-        for name, (res, args) in SIGNATURES.items():
-            f = getattr(L, name)
-            f.restype = res
-            f.argtypes = args
-        _lib = L
+        _lib = load_library(_build.build())
     return _lib
+
+
+class use_library:
+    """Context manager: route the binding to another build of the library (e.g. the
+    bounds-checking debug build, _build.build(checks=True)) and back."""
+
+    def __init__(self, L):
+        self.L = L
+
+    def __enter__(self):
+        global _lib
+        self.old = _lib
+        _lib = self.L
+        return self.L
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.old
+
+
+def check_hits():
+    """(enabled, violations since the last call) of the bounds-checking debug build."""
+    en, hits = C.c_int32(), C.c_uint64()
+    _check(lib().mppi_debug_check_hits(C.byref(en), C.byref(hits)))
+    return bool(en.value), int(hits.value)
+
+
+def check_selftest(device: int = 0) -> int:
+    hits = C.c_uint64()
+    _check(lib().mppi_debug_check_selftest(int(device), C.byref(hits)))
+    return int(hits.value)
 
 
 def _check(rc: int, ctx=None):
@@ -528,7 +569,7 @@ class MppiServerConfig(C.Structure):
     _fields_ = [("max_sessions", C.c_int32), ("max_batch", C.c_int32), ("max_samples", C.c_int64),
                 ("max_rollout_steps", C.c_int64), ("max_T", C.c_int32), ("max_ref", C.c_int32),
                 ("max_circ", C.c_int32), ("pipelines", C.c_int32), ("noise_bf16", C.c_int32), ("device", C.c_int32),
-                ("hbm_budget_bytes", C.c_int64), ("max_wait_us", C.c_double)]
+                ("hbm_budget_bytes", C.c_int64), ("max_wait_us", C.c_double), ("watchdog_ms", C.c_double)]
 
 
 class MppiResult(C.Structure):
@@ -541,9 +582,10 @@ class Server:
 
     def __init__(self, max_sessions: int, max_batch: int, max_samples: int, max_rollout_steps: int, max_T: int,
                  max_ref: int, max_circ: int, pipelines: int = 3, hbm_budget_bytes: int = 8 << 30,
-                 noise_bf16: int = 0, max_wait_us: float = 0.0, device: int = 0):
+                 noise_bf16: int = 0, max_wait_us: float = 0.0, device: int = 0, watchdog_ms: float = 0.0):
         self.cfg = MppiServerConfig(max_sessions, max_batch, max_samples, max_rollout_steps, max_T, max_ref,
-                                    max_circ, pipelines, noise_bf16, device, hbm_budget_bytes, max_wait_us)
+                                    max_circ, pipelines, noise_bf16, device, hbm_budget_bytes, max_wait_us,
+                                    watchdog_ms)
         self.max_T = max_T
         h = _VP()
         self._check(lib().mppi_server_create(C.byref(self.cfg), C.byref(h)), None)
@@ -618,3 +660,20 @@ class Server:
     def set_controls(self, session: int, U, iter_: int = 0):
         U = _f64(U).reshape(-1, 2)
         self._check(lib().mppi_server_set_controls(self._h, session, _dp(U), U.shape[0], int(iter_)), self._h)
+
+    def set_watchdog(self, watchdog_ms: float):
+        """Abandon micro-batches still running watchdog_ms after submission (0: off)."""
+        self._check(lib().mppi_server_set_watchdog(self._h, float(watchdog_ms)), self._h)
+
+    def timeouts(self) -> int:
+        n = C.c_uint64()
+        self._check(lib().mppi_server_timeouts(self._h, C.byref(n)), self._h)
+        return n.value
+
+    def snapshot(self, path: str):
+        """Write every session's warm start and iteration counter to a file (idle server)."""
+        self._check(lib().mppi_server_snapshot(self._h, os.fsencode(path)), self._h)
+
+    def restore(self, path: str):
+        """Read a session table written by snapshot() into this (idle, same-sized) server."""
+        self._check(lib().mppi_server_restore(self._h, os.fsencode(path)), self._h)

@@ -565,6 +565,38 @@ int mppi_plan_device(mppi_ctx* c, const double* d_x0, const double* d_ref_xy, in
     return MPPI_OK;
 }
 
+int mppi_debug_check_hits(int32_t* enabled, uint64_t* hits) {
+    if (!enabled || !hits) return fail(nullptr, MPPI_ERR_ARG, "NULL argument");
+#ifdef MPPI_CHECKS
+    *enabled = 1;
+#else
+    *enabled = 0;
+#endif
+    unsigned long long a = 0, b = 0;
+    cudaError_t e = take_check_hits_kernels(&a);
+    if (e == cudaSuccess) e = take_check_hits_batch(&b);
+    if (e != cudaSuccess) return fail(nullptr, MPPI_ERR_CUDA, std::string("check counters: ") + cudaGetErrorString(e));
+    *hits = a + b;
+    return MPPI_OK;
+}
+
+int mppi_debug_check_selftest(int device, uint64_t* hits) {
+    if (!hits) return fail(nullptr, MPPI_ERR_ARG, "NULL argument");
+    cudaError_t e = cudaSetDevice(device);
+    int* d = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&d, 5 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(d, 0, 5 * sizeof(int));
+    unsigned long long before = 0, after = 0;
+    if (e == cudaSuccess) e = take_check_hits_kernels(&before);
+    if (e == cudaSuccess) e = run_check_selftest(d, d + 4, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = take_check_hits_kernels(&after);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) return fail(nullptr, MPPI_ERR_CUDA, std::string("check self-test: ") + cudaGetErrorString(e));
+    *hits = after;
+    return MPPI_OK;
+}
+
 int mppi_debug_inject_flags(mppi_ctx* c, int32_t flags) {
     if (!c) return fail(nullptr, MPPI_ERR_ARG, "ctx is NULL");
     if (flags & ~(FLAG_NONFINITE_INPUT | FLAG_TIMEOUT)) return fail(c, MPPI_ERR_ARG, "unknown flag bits");

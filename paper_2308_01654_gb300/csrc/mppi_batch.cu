@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 2) batch_rollout_kernel(Bat
             }
             __syncthreads();
             if (!__syncthreads_and(bulk_wait(&bar, phase, &a.hdr->flags))) return;
+            check_smem(s_L, false);
             phase ^= 1u;
             build_boxes(smem, s_L);
         }
@@ -332,6 +333,19 @@ static int batch_max_blocks(int G, int bf16, int threads, size_t smem) {
 }
 
 static int lanes_of(int G) { return G < 0 ? -G : G; }
+
+// Debug build: the index violations this translation unit's kernels counted (then reset).
+cudaError_t take_check_hits_batch(unsigned long long* hits) {
+#ifdef MPPI_CHECKS
+    cudaError_t e = cudaMemcpyFromSymbol(hits, g_check_hits, sizeof(unsigned long long));
+    const unsigned long long zero = 0;
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_check_hits, &zero, sizeof(zero));
+    return e;
+#else
+    *hits = 0;
+    return cudaSuccess;
+#endif
+}
 
 }  // namespace mppi
 
@@ -765,6 +779,23 @@ int mppi_batch_wait(mppi_batch* B, int32_t ticket) {
     if (worst != MPPI_OK) return bfail(B, worst, "some plans of the submission failed (see their status)");
     return MPPI_OK;
 }
+
+}  // extern "C"
+
+// 1 when the submission on the ticket's pipeline has finished on the device, 0 while it runs,
+// MPPI_ERR_* on a bad ticket or a failed query (the server's watchdog polls it).
+int batch_ticket_done(mppi_batch* B, int32_t ticket) {
+    if (!B || ticket < 0 || ticket >= (int)B->pipes.size()) return MPPI_ERR_ARG;
+    Pipeline& p = B->pipes[(size_t)ticket];
+    if (!p.busy) return MPPI_ERR_ARG;
+    if (cudaSetDevice(B->device) != cudaSuccess) return MPPI_ERR_CUDA;
+    const cudaError_t e = cudaEventQuery(p.done);
+    if (e == cudaSuccess) return 1;
+    if (e == cudaErrorNotReady) return 0;
+    return MPPI_ERR_CUDA;
+}
+
+extern "C" {
 
 int mppi_batch_plan(mppi_batch* B, mppi_request* req, int32_t n) {
     int32_t t = -1;

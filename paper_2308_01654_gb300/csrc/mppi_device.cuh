@@ -26,6 +26,23 @@ constexpr int FLAG_NONFINITE_INPUT = 1;
 constexpr int FLAG_TIMEOUT = 2;
 
 // -----------------------------------------------------------------------------
+// Bounds-checking debug build (compiled with MPPI_CHECKS): IX(i, n) tests an index against
+// the length of the array it reads; one outside [0, n) is counted and replaced by 0, so the
+// access stays inside the array and nothing traps.  The normal build compiles IX to the index.
+// -----------------------------------------------------------------------------
+#ifdef MPPI_CHECKS
+static __device__ unsigned long long g_check_hits;   // one counter per translation unit
+__device__ __forceinline__ int checked_index(long long i, long long n) {
+    if (i >= 0 && i < n) return (int)i;
+    atomicAdd(&g_check_hits, 1ull);
+    return 0;
+}
+#define IX(i, n) ::mppi::checked_index((long long)(i), (long long)(n))
+#else
+#define IX(i, n) (i)
+#endif
+
+// -----------------------------------------------------------------------------
 // Programmatic dependent launch.  The kernels of an iteration after the first are launched
 // with programmatic stream serialisation: a kernel may be scheduled while its predecessor
 // drains, and waits here (griddepcontrol.wait: until the predecessor grid has completed and

@@ -170,6 +170,13 @@ cudaError_t launch_prep_noise(const PlanConst& pc, const SceneLayout& L, const P
                               const PlanInputs& in, int noise_bf16, cudaStream_t st);
 cudaError_t launch_reset_state(DevState* st, cudaStream_t s);
 
+// Bounds-checking debug build (MPPI_CHECKS): the index violations counted by the kernels of
+// each translation unit since the last call (then reset; 0 in the normal build), and a kernel
+// with two out-of-range indices that the checks must count (a4: 4 ints, out: 1 int).
+cudaError_t take_check_hits_kernels(unsigned long long* hits);
+cudaError_t take_check_hits_batch(unsigned long long* hits);
+cudaError_t run_check_selftest(int* a4, int* out, cudaStream_t st);
+
 // Raw Philox words for n counters (device buffers).
 cudaError_t launch_philox(uint2 key, const uint4* ctr, uint4* out, int n, cudaStream_t st);
 

@@ -341,7 +341,7 @@ __device__ __forceinline__ void scan_chunk(float px, float py, const float2* ver
         const int i = i0 + o;
         if (o < REF_L1 && i < n_seg) {
             if (STATS) cnt.seg++;
-            const unsigned long long k = dkey(seg_dist2(px, py, vert[i], seg[i]), i);
+            const unsigned long long k = dkey(seg_dist2(px, py, vert[IX(i, n_seg)], seg[IX(i, n_seg)]), i);
             best = k < best ? k : best;
         }
     }
@@ -498,12 +498,13 @@ __device__ __forceinline__ void search_range(float px, float py, const float2* v
 #pragma unroll 1
     for (int g = lo / REF_L2; g <= (hi - 1) / REF_L2; ++g) {
         if (STATS) cnt.l2++;
-        if (box_dist2(px, py, rb.l2[g]) > __uint_as_float((unsigned)(best >> 32)) * SLACK) continue;
+        if (box_dist2(px, py, rb.l2[IX(g, (hi - 1) / REF_L2 + 1)]) > __uint_as_float((unsigned)(best >> 32)) * SLACK)
+            continue;
         const int c1 = min(hi, (g + 1) * REF_L2);
 #pragma unroll 1
         for (int c = max(lo, g * REF_L2); c < c1; ++c) {
             if (STATS) cnt.l1++;
-            if (box_dist2(px, py, rb.l1[c]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK) {
+            if (box_dist2(px, py, rb.l1[IX(c, hi)]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK) {
                 scan_chunk<G, STATS>(px, py, vert, seg, c, n_seg, lane_g, best, cnt);
                 best = group_min_key<G>(best, mask);
             }
@@ -535,46 +536,46 @@ __device__ __forceinline__ void nearest_segment(float px, float py, const float2
     // one box bounds every chunk before cw and one every chunk after it: when neither can hold
     // a closer segment, the common case, the search ends here
     const float lim0 = __uint_as_float((unsigned)(best >> 32)) * SLACK;
-    const bool left = cw >= 1 && box_dist2(px, py, rb.pre[cw]) <= lim0;
-    const bool right = cw + 1 < n_l1 && box_dist2(px, py, rb.suf[cw + 1]) <= lim0;
+    const bool left = cw >= 1 && box_dist2(px, py, rb.pre[IX(cw, n_l1 + 1)]) <= lim0;
+    const bool right = cw + 1 < n_l1 && box_dist2(px, py, rb.suf[IX(cw + 1, n_l1 + 1)]) <= lim0;
     if (STATS) cnt.l2 += (cw >= 1 ? 1 : 0) + (cw + 1 < n_l1 ? 1 : 0);
     if (left) {
         if (STATS) cnt.l1++;
-        if (box_dist2(px, py, rb.l1[cw - 1]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK) {
+        if (box_dist2(px, py, rb.l1[IX(cw - 1, n_l1)]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK) {
             scan_chunk<G, STATS>(px, py, vert, seg, cw - 1, n_seg, lane_g, best, cnt);
             best = group_min_key<G>(best, mask);
         }
         if (cw >= 2) {
             if (STATS) cnt.l2++;
-            if (box_dist2(px, py, rb.pre[cw - 1]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK)
+            if (box_dist2(px, py, rb.pre[IX(cw - 1, n_l1 + 1)]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK)
                 search_range<G, STATS>(px, py, vert, seg, rb, n_seg, 0, cw - 1, lane_g, mask, best, cnt);
         }
     }
     if (right) {
         if (STATS) cnt.l1++;
-        if (box_dist2(px, py, rb.l1[cw + 1]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK) {
+        if (box_dist2(px, py, rb.l1[IX(cw + 1, n_l1)]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK) {
             scan_chunk<G, STATS>(px, py, vert, seg, cw + 1, n_seg, lane_g, best, cnt);
             best = group_min_key<G>(best, mask);
         }
         if (cw + 2 < n_l1) {
             if (STATS) cnt.l2++;
-            if (box_dist2(px, py, rb.suf[cw + 2]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK)
+            if (box_dist2(px, py, rb.suf[IX(cw + 2, n_l1 + 1)]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK)
                 search_range<G, STATS>(px, py, vert, seg, rb, n_seg, cw + 2, n_l1, lane_g, mask, best, cnt);
         }
     }
     float b2 = __uint_as_float((unsigned)(best >> 32));
     int bi = (int)(best & 0xffffffffu);
     const int b0 = bi;
-    const float hb = refine ? head[b0] : 0.0f;
+    const float hb = refine ? head[IX(b0, n_seg)] : 0.0f;
 #pragma unroll
     for (int dlt = -1; refine && dlt <= 1; dlt += 2) {
         const int j = b0 + dlt;
-        if (j < 0 || j >= n_seg || head[j] == hb) continue;
-        const float dj = seg_dist2(px, py, vert[j], seg[j]);
+        if (j < 0 || j >= n_seg || head[IX(j, n_seg)] == hb) continue;
+        const float dj = seg_dist2(px, py, vert[IX(j, n_seg)], seg[IX(j, n_seg)]);
         if (fabsf(dj - b2) <= 4e-6f * b2 + 1e-20f) {
             if (STATS) cnt.refine++;
-            const double db = seg_dist2_f64(px, py, vert[bi], vert[bi + 1]);
-            const double dd = seg_dist2_f64(px, py, vert[j], vert[j + 1]);
+            const double db = seg_dist2_f64(px, py, vert[IX(bi, n_seg)], vert[IX(bi + 1, n_seg + 1)]);
+            const double dd = seg_dist2_f64(px, py, vert[IX(j, n_seg)], vert[IX(j + 1, n_seg + 1)]);
             if (dd < db || (dd == db && j < bi)) {
                 bi = j;
                 b2 = dj;
@@ -604,17 +605,17 @@ __device__ __forceinline__ void nearest_vertex(float px, float py, const float2*
                                                const float4* l2, int n_ref, int n_l1, int n_l2, int lane_g,
                                                unsigned mask, int& jb, float& best2) {
     constexpr float SLACK = 1.0f + 1.0f / 1024.0f;
-    float dx = px - vert[jb].x, dy = py - vert[jb].y;
+    float dx = px - vert[IX(jb, n_ref)].x, dy = py - vert[IX(jb, n_ref)].y;
     float b2 = fmaf(dx, dx, dy * dy);
     int bi = jb;
     for (int g = 0; g < n_l2; ++g) {
-        if (box_dist2(px, py, l2[g]) > b2 * SLACK) continue;
+        if (box_dist2(px, py, l2[IX(g, n_l2)]) > b2 * SLACK) continue;
         const int c1 = min((g + 1) * REF_L2, n_l1);
         for (int c = g * REF_L2; c < c1; ++c) {
-            if (box_dist2(px, py, l1[c]) > b2 * SLACK) continue;
+            if (box_dist2(px, py, l1[IX(c, n_l1)]) > b2 * SLACK) continue;
             const int i1 = min((c + 1) * REF_L1 + 1, n_ref);
             for (int i = c * REF_L1 + lane_g; i < i1; i += G) {
-                const float ex = px - vert[i].x, ey = py - vert[i].y;
+                const float ex = px - vert[IX(i, n_ref)].x, ey = py - vert[IX(i, n_ref)].y;
                 const float d2 = fmaf(ex, ex, ey * ey);
                 if (d2 < b2 || (d2 == b2 && i < bi)) {
                     b2 = d2;
@@ -641,9 +642,9 @@ __device__ __forceinline__ void kahan_add(float& hi, float& lo, float inc) {
 __device__ __forceinline__ float2 circle_centre(const float4& c, const float2* vel, const int* order,
                                                 const float2* table, int n_circ, int t, int pos, float st,
                                                 bool has_table, bool moving) {
-    if (has_table) return table[(size_t)t * n_circ + order[pos]];
+    if (has_table) return table[(size_t)t * n_circ + order[IX(pos, n_circ)]];
     if (!moving) return make_float2(c.x, c.y);
-    const float2 vv = vel[pos];
+    const float2 vv = vel[IX(pos, n_circ)];
     return make_float2(fmaf(vv.x, st, c.x), fmaf(vv.y, st, c.y));
 }
 
@@ -703,8 +704,8 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const unsigne
         if (ci.inv_w > 0.0f && isfinite(f0) && isfinite(f1)) {
             const int b0 = f0 < 1.0f ? 0 : (int)fminf(floorf(f0) - 1.0f, (float)CIRC_BUCKETS);
             const int b1 = f1 < -1.0f ? -1 : (int)fminf(floorf(f1) + 1.0f, (float)(CIRC_BUCKETS - 1));
-            lo = ci.start[b0];
-            hi = ci.start[b1 + 1];
+            lo = ci.start[IX(b0, CIRC_BUCKETS + 1)];
+            hi = ci.start[IX(b1 + 1, CIRC_BUCKETS + 1)];
         }
     }
     float dobj = INFINITY;
@@ -713,10 +714,10 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const unsigne
         bool hit = false;
         if (pos < hi) {
             if (STATS) cnt.circ++;
-            const float4 c = circ[pos];
+            const float4 c = circ[IX(pos, n_circ)];
             const float2 cc = circle_centre(c, vel, ci.order, table, n_circ, tb0, pos, st0, has_table, moving);
             const float lim = (mmax + c.z + pc.ego_rmax) * 1.0001f + 1e-4f;
-            const float ext = tb1 != tb0 && (has_table || moving) ? disp[pos] * (float)(tb1 - tb0) : 0.0f;
+            const float ext = tb1 != tb0 && (has_table || moving) ? disp[IX(pos, n_circ)] * (float)(tb1 - tb0) : 0.0f;
             const float dx = fmaxf(fmaxf(bx0 - cc.x, cc.x - bx1), 0.0f);
             const float dy = fmaxf(fmaxf(by0 - cc.y, cc.y - by1), 0.0f);
             hit = lim > 0.0f && fmaf(dx, dx, dy * dy) <= (lim + ext) * (lim + ext);
@@ -728,7 +729,7 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const unsigne
             if (G > 1 && (j & (G - 1)) != lane_g) continue;
             if (STATS) cnt.cand++;
             const int pos2 = base + bit;
-            const float4 c = circ[pos2];
+            const float4 c = circ[IX(pos2, n_circ)];
             const float2 cc = circle_centre(c, vel, ci.order, table, n_circ, t, pos2, st, has_table, moving);
             // the circle centre in the ego frame, along the heading (al) and across it (pr): the
             // squared distance to the ego circle at offset o along the heading is (al - o)^2 + pr^2
@@ -891,17 +892,17 @@ __device__ __forceinline__ float state_cost(const PlanConst& pc, const SceneLayo
         nearest_vertex<G>(s.nx, s.ny, sc.vert, sc.l1, ref_boxes(sc.base, L).l2, L.n_ref, L.n_l1, L.n_l2, lane_g, mask,
                           jb, d2r);
     }
-    const float thr = sc.head[min(jb, L.n_seg - 1)];
+    const float thr = sc.head[IX(min(jb, L.n_seg - 1), L.n_seg)];
     {
         // c_dist on the compensated position: closest point of the winning segment or vertex
-        const float2 a = sc.vert[jb];
+        const float2 a = sc.vert[IX(jb, L.n_ref)];
         float qx = a.x, qy = a.y;
         if (pc.ref_mode == 0) {
-            const float4 sg = sc.seg[jb];
+            const float4 sg = sc.seg[IX(jb, L.n_seg)];
             const float tau = fmaf(s.nx - a.x, sg.z, (s.ny - a.y) * sg.w);
             if (tau >= 1.0f) {
-                qx = sc.vert[jb + 1].x;
-                qy = sc.vert[jb + 1].y;
+                qx = sc.vert[IX(jb + 1, L.n_ref)].x;
+                qy = sc.vert[IX(jb + 1, L.n_ref)].y;
             } else if (tau > 0.0f) {
                 qx = fmaf(tau, sg.x, a.x);
                 qy = fmaf(tau, sg.y, a.y);
@@ -926,6 +927,20 @@ __device__ __forceinline__ float state_cost(const PlanConst& pc, const SceneLayo
     return fmaf(pc.w_dist, d2r,
                 fmaf(pc.w_target, s.c_target,
                      fmaf(pc.w_yaw, dyaw * dyaw, fmaf(pc.w_speed, s.dv * s.dv, pc.w_safe * c_safe))));
+}
+
+// Debug build: the block's dynamic shared memory must hold the staged blob, what the block
+// builds after it and the steering slots; a shortfall is counted (the normal build has no check).
+__device__ __forceinline__ void check_smem(const SceneLayout& L, bool model1) {
+#ifdef MPPI_CHECKS
+    unsigned dyn = 0;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    if (threadIdx.x == 0 && (size_t)L.bytes + block_extra_bytes(L) + steer_slots_bytes(blockDim.x, model1) > dyn)
+        atomicAdd(&g_check_hits, 1ull);
+#else
+    (void)L;
+    (void)model1;
+#endif
 }
 
 // One sample's rollout and cost (Algorithm 1 inner loop), by the G lanes of its group.
@@ -976,7 +991,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
     if constexpr (!TIME) {
         for (int t = 0; t < T; ++t) {
             const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
-            const StepIn s = dyn_step<BF16, EXT>(pc, sc.ctl[t], sc.c0[t], zz, tp, r, steer_slot(smem, L));
+            const StepIn s = dyn_step<BF16, EXT>(pc, sc.ctl[IX(t, T)], sc.c0[IX(t, T)], zz, tp, r, steer_slot(smem, L));
             const float qx = state_cost<G, STATS>(pc, L, sc, table, s, t, t, t, has_table, moving, multi_head,
                                                   dconst, lane, lane_g, mask, jb, jbp, cnt);
             if (EXT && prefix && lane_g == 0 && k < K) prefix[(size_t)t * K + k] = s_hi - s_c;   // cost of steps < t
@@ -998,7 +1013,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
                 // positions advance through both steps from the shuffled directions.  The same
                 // operations as one lane per sample (dyn_step), so the same bits, with one tangent
                 // and one sine/cosine per step instead of two.
-                const float4 ct = sc.ctl[tm];
+                const float4 ct = sc.ctl[IX(tm, T)];
                 const Perturbed pe = perturb(ct.x, ct.y, NoiseT<BF16>::load(z + (size_t)tm * K + kk), pc.sig_a,
                                              pc.sig_d, pc.amin, pc.amax, pc.dmin, pc.dmax);
                 const float tn_own = tanf(pe.vd);
@@ -1059,7 +1074,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
                 e.th_c = thc_own;
                 e.dv = (v_own - pc.v_ref) - vc_own;
                 e.ds = fmaf(pc.d_safe_c, v_own - vc_own, pc.d_safe_0);
-                e.qu = fmaf(ct.z, pe.ea, fmaf(ct.w, pe.ed, sc.c0[tm]));
+                e.qu = fmaf(ct.z, pe.ea, fmaf(ct.w, pe.ed, sc.c0[IX(tm, T)]));
             } else if constexpr (G <= 2) {
                 // two lanes with the steering-rate model or the cost-to-go form: both lanes
                 // integrate both steps
@@ -1067,12 +1082,12 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
                 for (int j = 0; j < nv; ++j) {
                     const int t = t0 + j;
                     const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
-                    const StepIn q = dyn_step<BF16, EXT>(pc, sc.ctl[t], sc.c0[t], zz, tp, r, steer_slot(smem, L));
+                    const StepIn q = dyn_step<BF16, EXT>(pc, sc.ctl[IX(t, T)], sc.c0[IX(t, T)], zz, tp, r, steer_slot(smem, L));
                     if (j == my) e = q;
                 }
             } else {
             // own step: perturbed controls and the steering tangent (independent of the state)
-            const float4 ct = sc.ctl[tm];
+            const float4 ct = sc.ctl[IX(tm, T)];
             const Perturbed pe = perturb(ct.x, ct.y, NoiseT<BF16>::load(z + (size_t)tm * K + kk), pc.sig_a, pc.sig_d,
                                          pc.amin, pc.amax, pc.dmin, pc.dmax);
             float tn_own;
@@ -1140,7 +1155,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
             e.th_c = thc_own;
             e.dv = (v_own - pc.v_ref) - vc_own;
             e.ds = fmaf(pc.d_safe_c, v_own - vc_own, pc.d_safe_0);
-            e.qu = fmaf(ct.z, pe.ea, fmaf(ct.w, pe.ed, sc.c0[tm]));
+            e.qu = fmaf(ct.z, pe.ea, fmaf(ct.w, pe.ed, sc.c0[IX(tm, T)]));
             }
             const int tb1 = min(t0 + G - 1, T - 1);
             const float qx = state_cost<1, STATS>(pc, L, sc, table, e, tm, t0, tb1, has_table, moving, multi_head,

@@ -15,6 +15,7 @@
 #include "mppi_device.cuh"
 #include "mppi_internal.h"
 #include "mppi_iter.cuh"
+#include "mppi_trace.h"
 
 namespace mppi {
 
@@ -187,6 +188,7 @@ __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 1) rollout_kernel(PlanCon
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long bar;
     pdl_wait();
+    check_smem(L, pc.model == 1);
     const bool staged = __syncthreads_and(stage_to_smem(smem, b.scene, L.bytes, &bar, &b.state->flags));
     if (staged) {
         build_boxes(smem, L);
@@ -447,26 +449,40 @@ cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const Pl
         if (ev_mode == 2 && s != 2 && s != 3) return cudaSuccess;
         return cudaEventRecord(ev[s], st);
     };
+    TraceScope iteration("mppi iteration");
     if (ev && ev_mode != 2 && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
     ++stage;
     // prep and noise in one launch (the "prep" stage), the bf16 fix-up chained after it (the "noise" stage)
-    if ((e = launch_prep_noise_k(pc, L, b, in, noise_bf16, st)) != cudaSuccess) return e;
+    {
+        TraceScope r("prep + noise");
+        if ((e = launch_prep_noise_k(pc, L, b, in, noise_bf16, st)) != cudaSuccess) return e;
+    }
     if ((e = mark()) != cudaSuccess) return e;
-    if (noise_bf16 && (e = launch_noise_fix(pc, b, st)) != cudaSuccess) return e;
+    if (noise_bf16) {
+        TraceScope r("bf16 noise fix-up");
+        if ((e = launch_noise_fix(pc, b, st)) != cudaSuccess) return e;
+    }
     if ((e = mark()) != cudaSuccess) return e;
-    if ((e = launch_rollout(pc, L, b, group, threads, noise_bf16, st)) != cudaSuccess) return e;
+    {
+        TraceScope r("rollout + cost + argmin");
+        if ((e = launch_rollout(pc, L, b, group, threads, noise_bf16, st)) != cudaSuccess) return e;
+    }
     if ((e = mark()) != cudaSuccess) return e;
     // argmin: folded into the rollout kernel (its last block); the stage keeps its event
     if ((e = mark()) != cudaSuccess) return e;
     if (inject && (e = cudaMemcpyAsync(&b.state->flags, inject, sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return e;
-    if (pc.cost_to_go)
-        e = launch_chained(ctg_weights_kernel, dim3(pc.T), dim3(256), 0, st, pc.K, pc.inv_lam_f, b);
-    else
-        e = launch_chained(weights_kernel, dim3(b.n_wblk), dim3(256), 0, st, pc.K, pc.inv_lam_f, b);
+    {
+        TraceScope r("softmin weights");
+        if (pc.cost_to_go)
+            e = launch_chained(ctg_weights_kernel, dim3(pc.T), dim3(256), 0, st, pc.K, pc.inv_lam_f, b);
+        else
+            e = launch_chained(weights_kernel, dim3(b.n_wblk), dim3(256), 0, st, pc.K, pc.inv_lam_f, b);
+    }
     if (e != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
     {
+        TraceScope r("weighted noise sums");
         dim3 grid(b.n_kt, b.n_tt);
         const bool ctg = pc.cost_to_go != 0;
         if (noise_bf16) {
@@ -479,8 +495,12 @@ cudaError_t launch_iteration(const PlanConst& pc, const SceneLayout& L, const Pl
         if (e != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
     }
-    if ((e = launch_chained(finalize_kernel, dim3(1), dim3(((pc.T + 31) / 32) * 32), 0, st, pc, b, in)) != cudaSuccess)
-        return e;
+    {
+        TraceScope r("update + smoothing + x*");
+        if ((e = launch_chained(finalize_kernel, dim3(1), dim3(((pc.T + 31) / 32) * 32), 0, st, pc, b, in)) !=
+            cudaSuccess)
+            return e;
+    }
     return mark();
 }
 
@@ -503,6 +523,33 @@ cudaError_t launch_slice_sums(const PlanConst& pc, const SceneLayout& L, const P
 
 cudaError_t launch_slice_finalize(const PlanConst& pc, const PlanBuffers& b, const PlanInputs& in, cudaStream_t st) {
     return launch_chained(finalize_kernel, dim3(1), dim3(((pc.T + 31) / 32) * 32), 0, st, pc, b, in);
+}
+
+// Debug build: the index violations this translation unit's kernels counted (then reset), and a
+// self-test kernel whose two indices are out of range (the check keeps its reads in bounds).
+__global__ void check_selftest_kernel(const int* a, int* out) {
+#ifdef MPPI_CHECKS
+    out[0] = a[IX(-1, 4)] + a[IX(4, 4)];   // both indices are replaced by 0 and counted
+#else
+    out[0] = a[0];                          // the normal build has no checks: no stray index
+#endif
+}
+
+cudaError_t take_check_hits_kernels(unsigned long long* hits) {
+#ifdef MPPI_CHECKS
+    cudaError_t e = cudaMemcpyFromSymbol(hits, g_check_hits, sizeof(unsigned long long));
+    const unsigned long long zero = 0;
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_check_hits, &zero, sizeof(zero));
+    return e;
+#else
+    *hits = 0;
+    return cudaSuccess;
+#endif
+}
+
+cudaError_t run_check_selftest(int* a4, int* out, cudaStream_t st) {
+    check_selftest_kernel<<<1, 1, 0, st>>>(a4, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_philox(uint2 key, const uint4* ctr, uint4* out, int n, cudaStream_t st) {

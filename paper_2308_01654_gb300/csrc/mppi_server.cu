@@ -10,9 +10,11 @@
 // A completion thread waits for the batches in submission order, stamps each request's
 // latency (completion - arrival) and frees its footprint and session; mppi_server_poll
 // hands the results out.
+#include <stdio.h>
 #include <string.h>
 
 #include <atomic>
+#include <cmath>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -25,6 +27,10 @@
 
 #include "mppi.h"
 #include "mppi_internal.h"
+#include "mppi_trace.h"
+
+// the batch engine's completion query (mppi_batch.cu)
+int batch_ticket_done(mppi_batch* B, int32_t ticket);
 
 namespace {
 
@@ -48,6 +54,8 @@ struct InFlight {
     std::vector<std::unique_ptr<Req>> reqs;
     std::vector<mppi_request> creq;
     size_t footprint = 0;
+    Clock::time_point t_submit;
+    nvtxRangeId_t range = 0;       // NVTX range of the micro-batch, submission to completion
 };
 
 }  // namespace
@@ -67,8 +75,9 @@ struct mppi_server {
     uint64_t next_id = 1;
     bool stop = false;
     std::thread sched, compl_;
+    double watchdog_ms = 0.0;      // a micro-batch still running this long after its submission is abandoned
     // statistics
-    uint64_t n_batches = 0, n_plans = 0;
+    uint64_t n_batches = 0, n_plans = 0, n_timeouts = 0;
     std::string err;
 };
 
@@ -152,6 +161,8 @@ static void scheduler_loop(mppi_server* S) {
             q.info = &r.info;
         }
         InFlight* jp = job.get();
+        jp->t_submit = now;
+        jp->range = mppi::trace_start("serve micro-batch");
         S->inflight.push_back(std::move(job));
         lk.unlock();
         int32_t ticket = -1;
@@ -173,8 +184,45 @@ static void completion_loop(mppi_server* S) {
         if (S->stop && S->inflight.empty()) return;
         if (S->inflight.empty()) continue;
         InFlight* jp = S->inflight.front().get();
+        bool abandoned = false;
         if (jp->ticket >= 0) {
+            const double wd = S->watchdog_ms;
             lk.unlock();
+            if (wd > 0.0) {
+                // watchdog: a micro-batch still running wd ms after its submission is abandoned
+                const auto deadline =
+                    jp->t_submit + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double, std::milli>(wd));
+                int d = batch_ticket_done(S->batch, jp->ticket);
+                while (d == 0 && Clock::now() < deadline) {
+                    std::this_thread::sleep_for(std::chrono::microseconds(20));
+                    d = batch_ticket_done(S->batch, jp->ticket);
+                }
+                abandoned = d == 0;
+            }
+            if (abandoned) {
+                // its requests complete now with MPPI_ERR_TIMEOUT (copies: the batch still writes
+                // into the originals); the sessions, the budget and the pipeline stay taken until
+                // the device work has ended, and its results are then dropped
+                lk.lock();
+                const auto now = Clock::now();
+                for (auto& r : jp->reqs) {
+                    auto t = std::make_unique<Req>();
+                    t->id = r->id;
+                    t->session = r->session;
+                    t->params = r->params;
+                    t->u.assign(r->u.size(), 0.0);
+                    t->x.assign(r->x.size(), 0.0);
+                    t->status = MPPI_ERR_TIMEOUT;
+                    t->t_arrive = r->t_arrive;
+                    t->t_submit = r->t_submit;
+                    t->t_done = now;
+                    S->done.push_back(std::move(t));
+                    S->n_plans += 1;
+                    S->n_timeouts += 1;
+                }
+                S->cv_poll.notify_all();
+                lk.unlock();
+            }
             mppi_batch_wait(S->batch, jp->ticket);   // per-plan status is in creq[i].status
             lk.lock();
             for (size_t i = 0; i < jp->reqs.size(); ++i) jp->reqs[i]->status = jp->creq[i].status;
@@ -182,9 +230,11 @@ static void completion_loop(mppi_server* S) {
         const auto now = Clock::now();
         auto job = std::move(S->inflight.front());
         S->inflight.pop_front();
+        mppi::trace_end(job->range);
         for (auto& r : job->reqs) {
-            r->t_done = now;
             S->session_busy[(size_t)r->session] = 0;
+            if (abandoned) continue;
+            r->t_done = now;
             S->done.push_back(std::move(r));
             S->n_plans += 1;
         }
@@ -216,6 +266,7 @@ int mppi_server_create(const mppi_server_config* cfg, mppi_server** out) {
     }
     S->session_busy.assign((size_t)cfg->max_sessions, 0);
     S->budget = (size_t)cfg->hbm_budget_bytes;
+    S->watchdog_ms = cfg->watchdog_ms > 0.0 ? cfg->watchdog_ms : 0.0;
     S->free_pipes = cfg->pipelines;
     S->sched = std::thread(scheduler_loop, S);
     S->compl_ = std::thread(completion_loop, S);
@@ -352,6 +403,76 @@ int mppi_server_destroy(mppi_server* S) {
     if (S->compl_.joinable()) S->compl_.join();
     mppi_batch_destroy(S->batch);
     delete S;
+    return MPPI_OK;
+}
+
+int mppi_server_set_watchdog(mppi_server* S, double watchdog_ms) {
+    if (!S) return sfail(nullptr, MPPI_ERR_ARG, "NULL server");
+    if (std::isnan(watchdog_ms)) return sfail(S, MPPI_ERR_ARG, "watchdog_ms is NaN");
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->watchdog_ms = watchdog_ms > 0.0 ? watchdog_ms : 0.0;
+    return MPPI_OK;
+}
+
+int mppi_server_timeouts(mppi_server* S, uint64_t* n) {
+    if (!S || !n) return sfail(S, MPPI_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    *n = S->n_timeouts;
+    return MPPI_OK;
+}
+
+// Session table file: "MPPISNAP", version 1, max_sessions, max_T, then per session its
+// iteration counter and its warm start U[max_T][2] (little-endian as written by this host).
+static const char kSnapMagic[8] = {'M', 'P', 'P', 'I', 'S', 'N', 'A', 'P'};
+
+int mppi_server_snapshot(mppi_server* S, const char* path) {
+    if (!S || !path) return sfail(S, MPPI_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (!S->inflight.empty() || !S->queue.empty()) return sfail(S, MPPI_ERR_CAPACITY, "snapshot an idle server");
+    FILE* f = fopen(path, "wb");
+    if (!f) return sfail(S, MPPI_ERR_ARG, std::string("cannot write ") + path);
+    const int32_t hdr[3] = {1, S->cfg.max_sessions, S->cfg.max_T};
+    bool ok = fwrite(kSnapMagic, 1, 8, f) == 8 && fwrite(hdr, sizeof(int32_t), 3, f) == 3;
+    std::vector<double> U(2 * (size_t)S->cfg.max_T);
+    for (int s = 0; ok && s < S->cfg.max_sessions; ++s) {
+        uint64_t iter = 0;
+        if (mppi_batch_get_controls(S->batch, s, U.data(), S->cfg.max_T, &iter) != MPPI_OK) {
+            fclose(f);
+            return sfail(S, MPPI_ERR_CUDA, std::string("session read: ") + mppi_batch_last_error(S->batch));
+        }
+        ok = fwrite(&iter, sizeof(iter), 1, f) == 1 && fwrite(U.data(), sizeof(double), U.size(), f) == U.size();
+    }
+    ok = (fclose(f) == 0) && ok;
+    return ok ? MPPI_OK : sfail(S, MPPI_ERR_ARG, std::string("write failed: ") + path);
+}
+
+int mppi_server_restore(mppi_server* S, const char* path) {
+    if (!S || !path) return sfail(S, MPPI_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (!S->inflight.empty() || !S->queue.empty()) return sfail(S, MPPI_ERR_CAPACITY, "restore into an idle server");
+    FILE* f = fopen(path, "rb");
+    if (!f) return sfail(S, MPPI_ERR_ARG, std::string("cannot read ") + path);
+    char magic[8];
+    int32_t hdr[3];
+    if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kSnapMagic, 8) != 0 || fread(hdr, sizeof(int32_t), 3, f) != 3 ||
+        hdr[0] != 1 || hdr[1] != S->cfg.max_sessions || hdr[2] != S->cfg.max_T) {
+        fclose(f);
+        return sfail(S, MPPI_ERR_ARG, "not a session table of this server's size");
+    }
+    std::vector<double> U(2 * (size_t)S->cfg.max_T);
+    for (int s = 0; s < S->cfg.max_sessions; ++s) {
+        uint64_t iter = 0;
+        if (fread(&iter, sizeof(iter), 1, f) != 1 || fread(U.data(), sizeof(double), U.size(), f) != U.size()) {
+            fclose(f);
+            return sfail(S, MPPI_ERR_ARG, "session table truncated");
+        }
+        const int rc = mppi_batch_set_controls(S->batch, s, U.data(), S->cfg.max_T, iter);
+        if (rc != MPPI_OK) {
+            fclose(f);
+            return sfail(S, rc, std::string("session write: ") + mppi_batch_last_error(S->batch));
+        }
+    }
+    fclose(f);
     return MPPI_OK;
 }
 

@@ -212,3 +212,48 @@ def test_poll_reports_rows_too_short_for_a_result():
         assert got == 1
         assert out[0].status == -6 and out[0].T == p.T
         assert np.all(U == 0.0) and np.all(X == 0.0)
+
+
+def test_watchdog_abandons_a_late_micro_batch_and_the_server_recovers():
+    """A host-side watchdog far shorter than any micro-batch: every request completes with
+    MPPI_ERR_TIMEOUT, nothing faults or waits on the device, and with the watchdog off again the
+    server plans normally (its sessions were held until the abandoned work had ended)."""
+    probs = sessions(n=4)
+    params = [mp.make_params(p.params) for p in probs]
+    reqs = [(s, probs[s].circles) for s in range(4)]
+    with server_for(probs, watchdog_ms=1e-3) as srv:
+        res = run(srv, probs, reqs, params, alone=False)
+        assert all(r["status"] == -5 for r in res)
+        assert srv.timeouts() == len(reqs)
+        srv.set_watchdog(0.0)
+        res2 = run(srv, probs, reqs, params, alone=False)
+        assert all(r["status"] == 0 for r in res2)
+        assert srv.timeouts() == len(reqs)
+        st = srv.pending()
+        assert st["queued"] == 0 and st["in_flight"] == 0
+
+
+def test_session_table_snapshot_and_restore(tmp_path):
+    """Every session's warm start and counter written to a file and read into a new server: the
+    next request of each session gives the same result in both servers."""
+    probs = sessions(n=5)
+    params = [mp.make_params(p.params) for p in probs]
+    reqs = [(s, probs[s].circles) for s in range(5)]
+    path = str(tmp_path / "sessions.bin")
+    with server_for(probs) as a:
+        run(a, probs, reqs, params, alone=False)                  # warm starts move on (shift on)
+        run(a, probs, reqs, params, alone=False)
+        a.snapshot(path)
+        nxt_a = run(a, probs, reqs, params, alone=False)
+    with server_for(probs) as b:
+        b.restore(path)
+        nxt_b = run(b, probs, reqs, params, alone=False)
+        with pytest.raises(mp.MppiError) as e:
+            with server_for(probs, max_T=32) as c:               # another size: refused
+                c.restore(path)
+        assert e.value.status == -1
+    for ra, rb in zip(nxt_a, nxt_b):
+        assert ra["status"] == rb["status"] == 0
+        assert ra["info"]["iter"] == rb["info"]["iter"] == 2
+        np.testing.assert_array_equal(ra["u"], rb["u"])
+        np.testing.assert_array_equal(ra["x"], rb["x"])
