@@ -271,6 +271,21 @@ __device__ __forceinline__ bool bulk_wait(unsigned long long* bar, uint32_t pari
             : "memory");
     }
     if (!done && threadIdx.x == 0) atomicOr(flags, FLAG_TIMEOUT);
+    // the block reports the timeout but stays resident for a second bounded wait, so a copy that
+    // is only late can still land before the block exits (a block must not exit while a bulk
+    // copy into its shared memory is in flight); a copy that never completes cannot be told
+    // apart from this on the device, so the block returns after the second limit either way
+    for (int it = 0; it < (1 << 22) && !done; ++it) {
+        uint32_t late = 0;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(late)
+            : "r"(bar_a), "r"(parity)
+            : "memory");
+        if (late) break;
+    }
     return done != 0;
 }
 
