@@ -84,7 +84,8 @@ def executed_ops_per_step(stats) -> float:
 
 
 KERNEL_SOURCES = ("paper_2308_01654_gb300/csrc/mppi_kernels.cu", "paper_2308_01654_gb300/csrc/mppi_device.cuh",
-                  "paper_2308_01654_gb300/csrc/mppi_internal.h", "paper_2308_01654_gb300/csrc/mppi_iter.cuh")
+                  "paper_2308_01654_gb300/csrc/mppi_internal.h", "paper_2308_01654_gb300/csrc/mppi_iter.cuh",
+                  "paper_2308_01654_gb300/csrc/mppi_trace.h")
 TRAFFIC_PROFILE = {"roofline": "profiles/rollout_kernel_roofline_K65536_T200.md"}
 
 
@@ -122,6 +123,20 @@ def profiled_traffic(workload: str):
     """DRAM bytes per rollout launch from the committed ncu summary (same source only)."""
     v = profiled_value(workload, "dram_bytes_per_launch")
     return None if v is None else int(v)
+
+
+def counted_model(workload: str, units: float, ms: float, peak_tops: float):
+    """Arithmetic thread instructions per rollout-step counted by ncu on the current build (from the
+    committed summary), or None when that summary was taken on another build."""
+    ops = profiled_value(workload, "counted_ops_per_rollout_step")
+    fp32 = profiled_value(workload, "fp32_ops_per_rollout_step")
+    inst = profiled_value(workload, "thread_inst_per_rollout_step")
+    if ops is None:
+        return None
+    achieved = ops * units / (ms * 1e-3) / 1e12
+    return {"ops_per_rollout_step": ops, "fp32_ops_per_rollout_step": fp32, "thread_inst_per_rollout_step": inst,
+            "achieved": achieved, "frac": achieved / peak_tops,
+            "classes": "FP32 (FADD, FMUL, FFMA and the other FP32 ops), integer, bit and conversion"}
 
 
 def measured_peaks():
@@ -462,6 +477,10 @@ def run_gpu(args, world, rank, local):
                 # issue slots used by the same launch (ncu smsp__issue_active, committed summary)
                 "issue_active_frac": (lambda v: None if v is None else v / 100.0)(
                     profiled_value(args.workload, "issue_active_pct")),
+                # counted from one ncu capture of the same build (committed summary): the arithmetic
+                # thread instructions per rollout-step (FP32, integer, bit and conversion classes),
+                # and the fraction of the peak they would give at this launch's duration
+                "counted_model": counted_model(args.workload, K * T, ms_roll, peak_tops),
                 "work_per_rollout_step": {k: round(v, 4) for k, v in work.items()},
                 "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {f_max:.0f} MHz (max SM clock)",
                 "kernel_ms": ms_roll,
