@@ -690,7 +690,7 @@ __device__ __forceinline__ float warp_max_f(float v) { return ord_f32(__reduce_m
 // different steps t (all within tb0..tb1, the same for the whole warp): the broad phase
 // then tests each circle's centre at tb0 with the band widened by the farthest it can
 // move in tb1 - tb0 steps.
-template <int G, bool STATS>
+template <int G, bool STATS, bool SIMPLE = false>
 __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const unsigned char* smem, const SceneLayout& L,
                                               const float4* circ, const float2* vel,
                                               const float* disp, const float2* table, int n_circ, int t, int tb0,
@@ -757,7 +757,7 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const unsigne
                 // subtraction are monotone), one square root per circle; the minimum over the
                 // in-band circles is taken without a branch
                 float d2m;
-                if (pc.n_ego == 3) {        // the paper's ego model: three circles, no bound checks
+                if (SIMPLE || pc.n_ego == 3) {        // the paper's ego model: three circles, no bound checks
                     const float e0 = al - pc.ego_off[0], e1 = al - pc.ego_off[1], e2 = al - pc.ego_off[2];
                     d2m = fminf(fminf(fmaf(e0, e0, p2), fmaf(e1, e1, p2)), fmaf(e2, e2, p2));
                 } else {
@@ -844,13 +844,13 @@ struct StepIn {
 // Eq. (5): explicit Euler from x_t to x_{t+1} under the perturbed controls of step t.
 // EXT: compiled with the steering-rate model and the cost-to-go form (otherwise both are
 // compiled out: model 0 and whole-cost weights).
-template <bool BF16, bool EXT>
+template <bool BF16, bool EXT, bool SIMPLE = false>
 __device__ __forceinline__ StepIn dyn_step(const PlanConst& pc, const float4 ct, float c0t, float2 zz, float2 tp,
                                            Roll& r, float2* ds) {
     const Perturbed pe = perturb(ct.x, ct.y, zz, pc.sig_a, pc.sig_d, pc.amin, pc.amax, pc.dmin, pc.dmax);
     const float vt = r.v - r.v_c;
     float acc = pe.va;
-    if (pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt) / pc.dt), pc.amin);
+    if (!SIMPLE && pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt) / pc.dt), pc.amin);
     // model 0: the steering angle is the control; model 1: it is the state, advanced by the
     // steering rate (the second control) after its tangent is taken (right-hand side at x_t)
     float tn;
@@ -891,13 +891,13 @@ __device__ __forceinline__ StepIn dyn_step(const PlanConst& pc, const float4 ct,
 
 // Weighted state cost of Eq. (18) at x_{t+1}: the closest waypoint (Eq. 12, 14, search on
 // the binary32 position from the warm start jb) and the obstacle term (Eq. 16-17).
-template <int G, bool STATS>
+template <int G, bool STATS, bool SIMPLE = false>
 __device__ __forceinline__ float state_cost(const PlanConst& pc, const SceneLayout& L, const Scene& sc,
                                             const float2* table, const StepIn& s, int t, int tb0, int tb1,
                                             bool has_table, bool moving, bool multi_head, bool dconst, int lane,
                                             int lane_g, unsigned mask, int& jb, int& jbp, Counters& cnt) {
     float d2r;
-    if (pc.ref_mode == 0) {
+    if (SIMPLE || pc.ref_mode == 0) {
         // search hint: the last closest segment moved on by its last change
         const int jh = min(max(2 * jb - jbp, 0), L.n_seg - 1);
         jbp = jb;
@@ -912,7 +912,7 @@ __device__ __forceinline__ float state_cost(const PlanConst& pc, const SceneLayo
         // c_dist on the compensated position: closest point of the winning segment or vertex
         const float2 a = sc.vert[IX(jb, L.n_ref)];
         float qx = a.x, qy = a.y;
-        if (pc.ref_mode == 0) {
+        if (SIMPLE || pc.ref_mode == 0) {
             const float4 sg = sc.seg[IX(jb, L.n_seg)];
             const float tau = fmaf(s.nx - a.x, sg.z, (s.ny - a.y) * sg.w);
             if (tau >= 1.0f) {
@@ -929,14 +929,14 @@ __device__ __forceinline__ float state_cost(const PlanConst& pc, const SceneLayo
     const float dyaw = wrap_pi((s.th - thr) - s.th_c);
 
     // Eq. (16)-(17): ego circles against obstacle circles
-    const float mband = pc.collision_only ? fmaxf(s.ds, 0.0f) : s.ds;
+    const float mband = (!SIMPLE && pc.collision_only) ? fmaxf(s.ds, 0.0f) : s.ds;
     float dobj = INFINITY;
     if (L.n_circ > 0)
-        dobj = obstacle_min<G, STATS>(pc, sc.base, L, sc.circ, sc.vel, sc.disp, table, L.n_circ, t, tb0, tb1, has_table, moving, dconst,
+        dobj = obstacle_min<G, STATS, SIMPLE>(pc, sc.base, L, sc.circ, sc.vel, sc.disp, table, L.n_circ, t, tb0, tb1, has_table, moving, dconst,
                                       s.nx, s.ny, s.cnth, s.snth, mband, lane, lane_g, mask, cnt);
     const float gap = s.ds - dobj;
     float c_safe = gap > 0.0f ? gap * gap : 0.0f;
-    if (pc.collision_only && !(dobj <= 0.0f)) c_safe = 0.0f;
+    if (!SIMPLE && pc.collision_only && !(dobj <= 0.0f)) c_safe = 0.0f;
 
     // Eq. (18) weighted state cost
     return fmaf(pc.w_dist, d2r,
@@ -973,7 +973,11 @@ __device__ __forceinline__ void check_smem(const SceneLayout& L, bool model1) {
 // bits).  Lane p evaluates the state cost of its step (the reference search warm-started
 // from its own previous step) and the step costs are added in step order, so S is bit for
 // bit that of G = 1.
-template <int G, bool TIME, bool BF16, bool STATS, bool EXT>
+// SIMPLE: the plan's scene has static circles without a centre table, three ego circles of one
+// radius, a constant safety band, no collision-only switch, no speed cap, the segment form of
+// the closest waypoint and a lane of one heading; those decisions are then compile-time
+// constants (the same arithmetic, so the same bits, with fewer instructions).
+template <int G, bool TIME, bool BF16, bool STATS, bool EXT, bool SIMPLE = false>
 __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneLayout& L, const unsigned char* smem,
                                                const typename NoiseT<BF16>::type* __restrict__ z,
                                                const float2* table, float4 x0, float d0, bool moving,
@@ -986,9 +990,13 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
     const unsigned mask = group_mask<G>();
     const int K = pc.K, T = pc.T;
     const int kk = min(k, K - 1);               // whole groups past K run along (shuffle safety)
-    const bool has_table = pc.has_table != 0;
+    const bool has_table = !SIMPLE && pc.has_table != 0;
     const float2 tp = sc.vert[L.n_ref - 1];     // target point T_P: last vertex
-    const bool dconst = pc.d_safe_c == 0.0f && pc.ego_same_radius;
+    const bool dconst = SIMPLE || (pc.d_safe_c == 0.0f && pc.ego_same_radius);
+    if (SIMPLE) {
+        moving = false;
+        multi_head = false;
+    }
 
     Roll r;
     r.px = x0.x;
@@ -1006,8 +1014,9 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
     if constexpr (!TIME) {
         for (int t = 0; t < T; ++t) {
             const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
-            const StepIn s = dyn_step<BF16, EXT>(pc, sc.ctl[IX(t, T)], sc.c0[IX(t, T)], zz, tp, r, steer_slot(smem, L));
-            const float qx = state_cost<G, STATS>(pc, L, sc, table, s, t, t, t, has_table, moving, multi_head,
+            const StepIn s = dyn_step<BF16, EXT, SIMPLE>(pc, sc.ctl[IX(t, T)], sc.c0[IX(t, T)], zz, tp, r,
+                                                         steer_slot(smem, L));
+            const float qx = state_cost<G, STATS, SIMPLE>(pc, L, sc, table, s, t, t, t, has_table, moving, multi_head,
                                                   dconst, lane, lane_g, mask, jb, jbp, cnt);
             if (EXT && prefix && lane_g == 0 && k < K) prefix[(size_t)t * K + k] = s_hi - s_c;   // cost of steps < t
             kahan_add(s_hi, s_c, qx + s.qu);    // Eq. (6)
@@ -1036,7 +1045,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
                 const float va0 = __shfl_sync(mask, pe.va, 0, 2), tn0 = __shfl_sync(mask, tn_own, 0, 2);
                 const float vt0 = r.v - r.v_c;
                 float acc = va0;
-                if (pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt0) / pc.dt), pc.amin);
+                if (!SIMPLE && pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt0) / pc.dt), pc.amin);
                 kahan_add(r.th, r.th_c, __fmul_rn(__fmul_rn(vt0, tn0), pc.dt_over_L));
                 kahan_add(r.v, r.v_c, __fmul_rn(acc, pc.dt));
                 float th_own = r.th, thc_own = r.th_c, v_own = r.v, vc_own = r.v_c;
@@ -1045,7 +1054,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
                 const float vt1 = r.v - r.v_c;
                 if (nv == 2) {
                     acc = va1;
-                    if (pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt1) / pc.dt), pc.amin);
+                    if (!SIMPLE && pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt1) / pc.dt), pc.amin);
                     kahan_add(r.th, r.th_c, __fmul_rn(__fmul_rn(vt1, tn1), pc.dt_over_L));
                     kahan_add(r.v, r.v_c, __fmul_rn(acc, pc.dt));
                     if (my == 1) {
@@ -1097,7 +1106,8 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
                 for (int j = 0; j < nv; ++j) {
                     const int t = t0 + j;
                     const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
-                    const StepIn q = dyn_step<BF16, EXT>(pc, sc.ctl[IX(t, T)], sc.c0[IX(t, T)], zz, tp, r, steer_slot(smem, L));
+                    const StepIn q = dyn_step<BF16, EXT, SIMPLE>(pc, sc.ctl[IX(t, T)], sc.c0[IX(t, T)], zz, tp, r,
+                                                                 steer_slot(smem, L));
                     if (j == my) e = q;
                 }
             } else {
@@ -1130,7 +1140,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
                 const float tn = __shfl_sync(mask, tn_own, j, G);
                 const float vt = r.v - r.v_c;
                 float acc = va;
-                if (pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt) / pc.dt), pc.amin);
+                if (!SIMPLE && pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt) / pc.dt), pc.amin);
                 kahan_add(r.th, r.th_c, __fmul_rn(__fmul_rn(vt, tn), pc.dt_over_L));
                 kahan_add(r.v, r.v_c, __fmul_rn(acc, pc.dt));
                 if (j == my) {
@@ -1173,7 +1183,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
             e.qu = fmaf(ct.z, pe.ea, fmaf(ct.w, pe.ed, sc.c0[IX(tm, T)]));
             }
             const int tb1 = min(t0 + G - 1, T - 1);
-            const float qx = state_cost<1, STATS>(pc, L, sc, table, e, tm, t0, tb1, has_table, moving, multi_head,
+            const float qx = state_cost<1, STATS, SIMPLE>(pc, L, sc, table, e, tm, t0, tb1, has_table, moving, multi_head,
                                                   dconst, lane, 0, mask, jb, jbp, cnt);
             const float c = qx + e.qu;
             float pre_own = 0.0f;

@@ -182,7 +182,10 @@ __global__ void philox_kernel(uint2 key, const uint4* ctr, uint4* out, int n) {
     if (i < n) out[i] = philox4x32_10(ctr[i], key);
 }
 
-template <int G, bool TIME, bool BF16, bool STATS, bool EXT>
+// SIMPLE: the plan's parameters allow the specialised step (see rollout_sample); the block then
+// takes it when scene preparation found the circles static and the lane of one heading, and the
+// general step otherwise (a block-uniform choice; both give the same bits).
+template <int G, bool TIME, bool BF16, bool STATS, bool EXT, bool SIMPLE = false>
 __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 1) rollout_kernel(PlanConst pc, SceneLayout L, PlanBuffers b,
                                                         const typename NoiseT<BF16>::type* __restrict__ z) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -193,10 +196,15 @@ __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 1) rollout_kernel(PlanCon
     if (staged) {
         build_boxes(smem, L);
         const int k = (blockIdx.x * blockDim.x + threadIdx.x) / G;
-        rollout_sample<G, TIME, BF16, STATS, EXT>(pc, L, smem, z, b.table, b.state->x0f, b.state->delta0f,
-                                             b.state->moving != 0, b.state->multi_head != 0,
-                                             (int)(b.state->jkey & 0xffffffffu), k, b.S,
-                                             b.stats, pc.cost_to_go ? b.ctg_prefix : nullptr);
+        const bool moving = b.state->moving != 0, multi = b.state->multi_head != 0;
+        if (SIMPLE && !moving && !multi)
+            rollout_sample<G, TIME, BF16, STATS, EXT, true>(pc, L, smem, z, b.table, b.state->x0f, b.state->delta0f,
+                                                           false, false, (int)(b.state->jkey & 0xffffffffu), k, b.S,
+                                                           b.stats, nullptr);
+        else
+            rollout_sample<G, TIME, BF16, STATS, EXT>(pc, L, smem, z, b.table, b.state->x0f, b.state->delta0f, moving,
+                                                      multi, (int)(b.state->jkey & 0xffffffffu), k, b.S, b.stats,
+                                                      pc.cost_to_go ? b.ctg_prefix : nullptr);
     }
     pdl_trigger();   // after the block's samples: the rollout may run in several waves
     rollout_argmin_tail(pc.K, b, (int)(blockIdx.x * blockDim.x / G), (int)(blockDim.x / G), staged);
@@ -319,7 +327,7 @@ static cudaError_t launch_wsum(const PlanConst& pc, const SceneLayout& L, const 
 // Opt an instantiation of the rollout kernel in to the device's whole shared memory per block,
 // once: every launch and occupancy query then passes its own size (which depends on the block
 // for the steering-rate model), and none lowers the limit under another.
-template <int G, bool TIME, bool BF16, bool STATS, bool EXT>
+template <int G, bool TIME, bool BF16, bool STATS, bool EXT, bool SIMPLE = false>
 static cudaError_t allow_rollout_smem() {
     static std::atomic<bool> done{false};   // contexts may be driven from several host threads
     if (done.load(std::memory_order_acquire)) return cudaSuccess;
@@ -327,25 +335,25 @@ static cudaError_t allow_rollout_smem() {
     cudaFuncAttributes fa{};
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, rollout_kernel<G, TIME, BF16, STATS, EXT>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, rollout_kernel<G, TIME, BF16, STATS, EXT, SIMPLE>);
     // the dynamic part may take what the kernel's static shared memory leaves
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(rollout_kernel<G, TIME, BF16, STATS, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(rollout_kernel<G, TIME, BF16, STATS, EXT, SIMPLE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  optin - (int)fa.sharedSizeBytes);
     if (e == cudaSuccess) done.store(true, std::memory_order_release);
     return e;
 }
 
-template <int G, bool TIME, bool BF16, bool STATS, bool EXT>
+template <int G, bool TIME, bool BF16, bool STATS, bool EXT, bool SIMPLE = false>
 static cudaError_t launch_rollout_t(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int threads,
                                     cudaStream_t st) {
     const size_t smem = rollout_smem_bytes(L, threads, pc.model == 1);
-    cudaError_t e = allow_rollout_smem<G, TIME, BF16, STATS, EXT>();
+    cudaError_t e = allow_rollout_smem<G, TIME, BF16, STATS, EXT, SIMPLE>();
     if (e != cudaSuccess) return e;
     const long long total = (long long)pc.K * G;
     const int blocks = (int)((total + threads - 1) / threads);
-    return launch_chained(rollout_kernel<G, TIME, BF16, STATS, EXT>, dim3(blocks), dim3(threads), smem, st, pc, L, b,
-                          reinterpret_cast<const typename NoiseT<BF16>::type*>(b.z));
+    return launch_chained(rollout_kernel<G, TIME, BF16, STATS, EXT, SIMPLE>, dim3(blocks), dim3(threads), smem, st, pc,
+                          L, b, reinterpret_cast<const typename NoiseT<BF16>::type*>(b.z));
 }
 
 // The launch shapes: lanes per sample as the group value (g > 0 split the work of each
@@ -353,9 +361,35 @@ static cudaError_t launch_rollout_t(const PlanConst& pc, const SceneLayout& L, c
 #define MPPI_ROLLOUT_GROUPS(X) X(1, 1, false) X(2, 2, false) X(4, 4, false) X(8, 8, false) X(16, 16, false) \
     X(32, 32, false) X(-2, 2, true) X(-4, 4, true) X(-8, 8, true) X(-16, 16, true)
 
+// The lane splits with a specialised instantiation (the ones the autotuner picks; the others run
+// the general kernel).
+#define MPPI_SIMPLE_GROUPS(X) X(1, 1, false) X(2, 2, false) X(4, 4, false) X(-2, 2, true) X(-4, 4, true) X(-8, 8, true)
+
+// The plan's parameters allow the specialised rollout step (rollout_sample's SIMPLE): three ego
+// circles of one radius, a constant safety band, no collision-only switch, no speed cap, the
+// segment form of the closest waypoint, no centre table, the 4-state model with whole-cost weights.
+static bool simple_plan(const PlanConst& pc) {
+    return pc.n_ego == 3 && pc.ego_same_radius && pc.d_safe_c == 0.0f && !pc.collision_only && !pc.vcap &&
+           pc.ref_mode == 0 && !pc.has_table && pc.model == 0 && !pc.cost_to_go;
+}
+
+template <bool BF16>
+static bool launch_rollout_simple(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int group,
+                                  int threads, cudaStream_t st, cudaError_t* e) {
+    switch (group) {
+#define CASE(gv, g, time) \
+    case gv: *e = launch_rollout_t<g, time, BF16, false, false, true>(pc, L, b, threads, st); return true;
+        MPPI_SIMPLE_GROUPS(CASE)
+#undef CASE
+        default: return false;
+    }
+}
+
 template <bool BF16, bool EXT>
 static cudaError_t launch_rollout_b(const PlanConst& pc, const SceneLayout& L, const PlanBuffers& b, int group,
                                     int threads, cudaStream_t st) {
+    cudaError_t es = cudaSuccess;
+    if (!EXT && simple_plan(pc) && launch_rollout_simple<BF16>(pc, L, b, group, threads, st, &es)) return es;
     switch (group) {
 #define CASE(gv, g, time) \
     case gv: return launch_rollout_t<g, time, BF16, false, EXT>(pc, L, b, threads, st);

@@ -523,3 +523,33 @@ def test_injected_device_flag_ends_the_iteration_and_keeps_the_state(flag, statu
         with pytest.raises(mp.MppiError) as e:
             pl.debug_inject_flags(8)
         assert e.value.status == -1
+
+
+# ----------------------------------------------------------------------------- specialised step
+
+@pytest.mark.parametrize("scene", ["straight_static", "moving", "curved"])
+@pytest.mark.parametrize("group", [1, 2, 4, -2, -4, -8, 8])
+def test_specialised_step_gives_the_general_bits(scene, group):
+    """The rollout's specialised step (static circles, three equal ego circles, constant band, no
+    speed cap, one lane heading) against the general step on the same plan: a speed cap of 1e30
+    never binds (the perturbed acceleration is already clamped into the control box) but makes the
+    host launch the general kernel.  Moving circles or a curved lane send the specialised kernel's
+    blocks down the general branch at run time.  The costs and u* are the same bits."""
+    if scene == "curved":
+        prob = sc.closed_loop()
+        prob.params.update(K=3000, T=45)
+        prob.centres = None                      # circles moving by velocity, no table: host-simple
+        prob.circles[:, 3:] = 0.0                # static, but the lane has many headings
+    elif scene == "moving":
+        prob = sc.tiny(K=2500, T=40, n_ref=60, n_obs=3, moving=True)
+        prob.params["d_safe_0"] = 2.0
+    else:
+        prob = sc.roofline()
+        prob.params.update(K=4096, T=60)
+    prob.params["group"] = group
+    a, _, _, _ = run_gpu(prob)
+    b, _, _, _ = run_gpu(prob, params=dict(prob.params, v_max=1e30))
+    np.testing.assert_array_equal(a[0][3], b[0][3])
+    np.testing.assert_array_equal(a[0][0], b[0][0])
+    np.testing.assert_allclose(a[0][1], b[0][1], rtol=0, atol=1e-9)     # x*: the capped speed is a serial sum
+    assert a[0][2]["argmin"] == b[0][2]["argmin"]
