@@ -1049,20 +1049,25 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
                 kahan_add(r.th, r.th_c, __fmul_rn(__fmul_rn(vt0, tn0), pc.dt_over_L));
                 kahan_add(r.v, r.v_c, __fmul_rn(acc, pc.dt));
                 float th_own = r.th, thc_own = r.th_c, v_own = r.v, vc_own = r.v_c;
-                // step t0 + 1 (lane 1's controls), when there is one
+                // step t0 + 1 (lane 1's controls), when there is one: computed on copies and taken
+                // by selects (no branch; the same operations, so the same bits)
+                const bool two = nv == 2, mine = my == 1;
                 const float va1 = __shfl_sync(mask, pe.va, 1, 2), tn1 = __shfl_sync(mask, tn_own, 1, 2);
                 const float vt1 = r.v - r.v_c;
-                if (nv == 2) {
+                {
                     acc = va1;
                     if (!SIMPLE && pc.vcap) acc = fmaxf(fminf(acc, (pc.v_max - vt1) / pc.dt), pc.amin);
-                    kahan_add(r.th, r.th_c, __fmul_rn(__fmul_rn(vt1, tn1), pc.dt_over_L));
-                    kahan_add(r.v, r.v_c, __fmul_rn(acc, pc.dt));
-                    if (my == 1) {
-                        th_own = r.th;
-                        thc_own = r.th_c;
-                        v_own = r.v;
-                        vc_own = r.v_c;
-                    }
+                    float th2 = r.th, thc2 = r.th_c, v2 = r.v, vc2 = r.v_c;
+                    kahan_add(th2, thc2, __fmul_rn(__fmul_rn(vt1, tn1), pc.dt_over_L));
+                    kahan_add(v2, vc2, __fmul_rn(acc, pc.dt));
+                    th_own = mine ? th2 : th_own;
+                    thc_own = mine ? thc2 : thc_own;
+                    v_own = mine ? v2 : v_own;
+                    vc_own = mine ? vc2 : vc_own;
+                    r.th = two ? th2 : r.th;
+                    r.th_c = two ? thc2 : r.th_c;
+                    r.v = two ? v2 : r.v;
+                    r.v_c = two ? vc2 : r.v_c;
                 }
                 sincosf(th_own, &e.snth, &e.cnth);
                 // positions: step t0 moves along the carried direction, step t0 + 1 along lane 0's
@@ -1077,20 +1082,22 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
                 e.py_c = r.py_c;
                 e.c_target = tdn > r.tdp ? 1.0f : 0.0f;
                 r.tdp = tdn;
-                if (nv == 2) {
-                    kahan_add(r.px, r.px_c, __fmul_rn(__fmul_rn(vt1, cn0), pc.dt));
-                    kahan_add(r.py, r.py_c, __fmul_rn(__fmul_rn(vt1, sn0), pc.dt));
-                    tx = (r.px - tp.x) - r.px_c;
-                    ty = (r.py - tp.y) - r.py_c;
-                    tdn = fmaf(tx, tx, ty * ty);
-                    if (my == 1) {
-                        e.nx = r.px;
-                        e.ny = r.py;
-                        e.px_c = r.px_c;
-                        e.py_c = r.py_c;
-                        e.c_target = tdn > r.tdp ? 1.0f : 0.0f;
-                    }
-                    r.tdp = tdn;
+                {
+                    float px2 = r.px, pxc2 = r.px_c, py2 = r.py, pyc2 = r.py_c;
+                    kahan_add(px2, pxc2, __fmul_rn(__fmul_rn(vt1, cn0), pc.dt));
+                    kahan_add(py2, pyc2, __fmul_rn(__fmul_rn(vt1, sn0), pc.dt));
+                    const float tx2 = (px2 - tp.x) - pxc2, ty2 = (py2 - tp.y) - pyc2;
+                    const float tdn2 = fmaf(tx2, tx2, ty2 * ty2);
+                    e.nx = mine ? px2 : e.nx;
+                    e.ny = mine ? py2 : e.ny;
+                    e.px_c = mine ? pxc2 : e.px_c;
+                    e.py_c = mine ? pyc2 : e.py_c;
+                    e.c_target = mine ? (tdn2 > r.tdp ? 1.0f : 0.0f) : e.c_target;
+                    r.px = two ? px2 : r.px;
+                    r.px_c = two ? pxc2 : r.px_c;
+                    r.py = two ? py2 : r.py;
+                    r.py_c = two ? pyc2 : r.py_c;
+                    r.tdp = two ? tdn2 : r.tdp;
                 }
                 r.cth = __shfl_sync(mask, e.cnth, nv - 1, 2);
                 r.sth = __shfl_sync(mask, e.snth, nv - 1, 2);
