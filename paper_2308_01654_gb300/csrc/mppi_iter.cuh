@@ -664,22 +664,25 @@ __device__ __forceinline__ float2 circle_centre(const float4& c, const float2* v
 }
 
 // Distance from a squared distance as d2 * rsqrt(d2) (a few ulp, against the many more
-// instructions of the correctly rounded square root); 0 at 0.  The obstacle term uses it
-// only inside the safety band, where c_safe is continuous in it.
-__device__ __forceinline__ float dist_of(float d2) { return d2 > 0.0f ? d2 * rsqrtf(d2) : 0.0f; }
+// instructions of the correctly rounded square root); the argument of the reciprocal square
+// root is raised to the smallest normal, so 0 gives 0 without a compare and a select (and a
+// subnormal d2 gives at most 1.1e-19 m).  The obstacle term uses it only inside the safety
+// band, where c_safe is continuous in it.
+__device__ __forceinline__ float dist_of(float d2) { return d2 * rsqrtf(fmaxf(d2, 1.17549435e-38f)); }
 
-// Warp min / max of a float with one redux.sync on an order-preserving integer image
-// (non-negative floats keep their bits, negative ones have their magnitude bits flipped).
-__device__ __forceinline__ int f32_ord(float f) {
-    const int i = __float_as_int(f);
-    return i >= 0 ? i : i ^ 0x7fffffff;
+// Warp min / max of a float: one redux.sync on binary32 (a NaN lane is ignored, like fminf and
+// fmaxf; the results only bound the warp's broad phase).
+__device__ __forceinline__ float warp_min_f(float v) {
+    float r;
+    asm("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
 }
 
-__device__ __forceinline__ float ord_f32(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
-
-__device__ __forceinline__ float warp_min_f(float v) { return ord_f32(__reduce_min_sync(0xffffffffu, f32_ord(v))); }
-
-__device__ __forceinline__ float warp_max_f(float v) { return ord_f32(__reduce_max_sync(0xffffffffu, f32_ord(v))); }
+__device__ __forceinline__ float warp_max_f(float v) {
+    float r;
+    asm("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
 
 // d_obj of Eq. (16) restricted to the pairs that can lie inside the safety band (the
 // only pairs that change c_safe), with a warp-wide broad phase: the lanes test the
@@ -1104,7 +1107,8 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
                 e.th = th_own;
                 e.th_c = thc_own;
                 e.dv = (v_own - pc.v_ref) - vc_own;
-                e.ds = fmaf(pc.d_safe_c, v_own - vc_own, pc.d_safe_0);
+                // d_safe of Eq. (17): the specialised step has d_safe_c = 0
+                e.ds = SIMPLE ? pc.d_safe_0 : fmaf(pc.d_safe_c, v_own - vc_own, pc.d_safe_0);
                 e.qu = fmaf(ct.z, pe.ea, fmaf(ct.w, pe.ed, sc.c0[IX(tm, T)]));
             } else if constexpr (G <= 2) {
                 // two lanes with the steering-rate model or the cost-to-go form: both lanes
