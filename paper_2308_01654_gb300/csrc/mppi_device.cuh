@@ -167,6 +167,13 @@ __device__ __forceinline__ void store_keep(__nv_bfloat162* p, __nv_bfloat162 v, 
     asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(bits), "l"(pol) : "memory");
 }
 
+// a noise value already in registers or shared memory, as binary32
+template <bool BF16>
+__device__ __forceinline__ float2 noise_value(typename NoiseT<BF16>::type v) {
+    if constexpr (BF16) return __bfloat1622float2(v);
+    else return v;
+}
+
 // last read of the noise: streaming load
 template <bool BF16>
 __device__ __forceinline__ float2 load_last(const typename NoiseT<BF16>::type* p) {

@@ -1477,10 +1477,15 @@ __device__ __forceinline__ float softmin_weight(double s, double smin, float inv
 // products); the per-warp partials are added in binary64 into du_part[kt][T][2].
 // -----------------------------------------------------------------------------
 
-template <bool BF16, bool CTG = false, int TT = WS_TT>
+// STAGED: z is the tile itself in shared memory (row t - t0 of kt_size samples, landed by
+// the caller's bulk copies; wait_tile(r) waits for row r before its products are taken, so
+// the later rows land while the earlier ones are summed); otherwise z is the noise in global
+// memory.  Both read the same values in the same order: the same bits.
+template <bool BF16, bool CTG = false, int TT = WS_TT, bool STAGED = false, typename Wait = int>
 __device__ __forceinline__ void wsum_tile(const PlanConst& pc, const float4* ctl,
                                           const typename NoiseT<BF16>::type* __restrict__ z, const float* w, int kt,
-                                          int t0, int kt_size, double* du_part, const float* wt = nullptr) {
+                                          int t0, int kt_size, double* du_part, const float* wt = nullptr,
+                                          Wait wait_tile = 0) {
     static_assert(TT >= 1 && TT <= WS_TT, "step tile");
     __shared__ float red[8][TT][2];
     const int K = pc.K, T = pc.T;
@@ -1495,6 +1500,7 @@ __device__ __forceinline__ void wsum_tile(const PlanConst& pc, const float4* ctl
     }
     for (int t = t0; t < t1; ++t) {
         const float4 ct = ctl[t];
+        if constexpr (STAGED) wait_tile(t - t0);
         float aa = 0.0f, ad = 0.0f;
         if (CTG) {                 // cost-to-go form: weights of this step
 #pragma unroll
@@ -1503,7 +1509,11 @@ __device__ __forceinline__ void wsum_tile(const PlanConst& pc, const float4* ctl
 #pragma unroll
         for (int j = 0; j < WS_J; ++j) {
             if (kj[j] < K) {
-                const float2 zz = load_last<BF16>(z + (size_t)t * K + kj[j]);
+                float2 zz;
+                if constexpr (STAGED)
+                    zz = noise_value<BF16>(z[(t - t0) * kt_size + j * blockDim.x + threadIdx.x]);
+                else
+                    zz = load_last<BF16>(z + (size_t)t * K + kj[j]);
                 const Perturbed pe =
                     perturb(ct.x, ct.y, zz, pc.sig_a, pc.sig_d, pc.amin, pc.amax, pc.dmin, pc.dmax);
                 aa = fmaf(wj[j], pe.ea, aa);
