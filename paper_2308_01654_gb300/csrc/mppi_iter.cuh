@@ -1026,6 +1026,9 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
             q_last = qx;
         }
     } else {
+        // the two-lane plain form reads its noise one block of steps ahead (the load's latency
+        // is then spent on the previous block's work)
+        typename NoiseT<BF16>::type zpre = z[(size_t)min(lane_g, min(G, T) - 1) * K + kk];
         for (int t0 = 0; t0 < T; t0 += G) {
             // nv real steps in this block; past the last step a lane re-evaluates step T - 1
             // (the warp stays converged)
@@ -1040,9 +1043,15 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
                 // positions advance through both steps from the shuffled directions.  The same
                 // operations as one lane per sample (dyn_step), so the same bits, with one tangent
                 // and one sine/cosine per step instead of two.
+                const typename NoiseT<BF16>::type zcur = zpre;
+                {
+                    const int tn = t0 + G;      // the next block's own step (T - 1 past the end)
+                    const int tmn = tn < T ? tn + min(lane_g, min(G, T - tn) - 1) : T - 1;
+                    zpre = z[(size_t)tmn * K + kk];
+                }
                 const float4 ct = sc.ctl[IX(tm, T)];
-                const Perturbed pe = perturb(ct.x, ct.y, NoiseT<BF16>::load(z + (size_t)tm * K + kk), pc.sig_a,
-                                             pc.sig_d, pc.amin, pc.amax, pc.dmin, pc.dmax);
+                const Perturbed pe = perturb(ct.x, ct.y, noise_value<BF16>(zcur), pc.sig_a, pc.sig_d, pc.amin,
+                                             pc.amax, pc.dmin, pc.dmax);
                 const float tn_own = tanf(pe.vd);
                 // step t0 (lane 0's controls)
                 const float va0 = __shfl_sync(mask, pe.va, 0, 2), tn0 = __shfl_sync(mask, tn_own, 0, 2);
