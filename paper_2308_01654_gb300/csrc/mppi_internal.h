@@ -113,12 +113,12 @@ struct PlanBuffers {
 };
 
 // Shared memory each rollout block builds after the staged blob: the level-2 boxes, the
-// prefix and suffix boxes of the chunk sequence, and the circle index (a float4 of scalars
-// and CIRC_BUCKETS + 1 bucket starts into the sorted circles).
+// prefix and suffix boxes of the chunk sequence, the circle index (a float4 of scalars and
+// CIRC_BUCKETS + 1 bucket starts into the sorted circles) and a float4 of search scalars.
 constexpr int CIRC_BUCKETS = 64;
 
 __host__ __device__ inline size_t block_extra_bytes(const SceneLayout& L) {
-    return (size_t)16 * (L.n_l2 + 2 * (L.n_l1 + 1)) + 16 + (size_t)4 * ((CIRC_BUCKETS + 1 + 3) & ~3);
+    return (size_t)16 * (L.n_l2 + 2 * (L.n_l1 + 1)) + 32 + (size_t)4 * ((CIRC_BUCKETS + 1 + 3) & ~3);
 }
 
 // Per-thread slots after the block's extras: the compensated steering angle of the

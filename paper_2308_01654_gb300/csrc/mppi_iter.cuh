@@ -403,7 +403,7 @@ __device__ __forceinline__ CircleIndex circle_index(const unsigned char* smem, c
     const float4 pj = *reinterpret_cast<const float4*>(smem + L.off_proj);
     CircleIndex c;
     c.order = reinterpret_cast<const int*>(smem + L.off_order);
-    c.start = reinterpret_cast<const int*>(e + 16);
+    c.start = reinterpret_cast<const int*>(e + 32);
     c.smin = sc.x;
     c.inv_w = sc.y;
     c.dmax = sc.z;
@@ -411,6 +411,12 @@ __device__ __forceinline__ CircleIndex circle_index(const unsigned char* smem, c
     c.dx = pj.x;
     c.dy = pj.y;
     return c;
+}
+
+// The search scalar the block derives from the staged segments: 4 x the longest segment, the
+// length term of the pruning bound (prune_lim).
+__device__ __forceinline__ float search_lfac(const unsigned char* smem, const SceneLayout& L) {
+    return *reinterpret_cast<const float*>(circle_index_base(smem, L) + 16);
 }
 
 // First position in skey[0, n) whose key is >= v (n if none).
@@ -475,11 +481,12 @@ __device__ __forceinline__ void build_boxes(unsigned char* smem, const SceneLayo
     // circle index.  Scene preparation stored the circles sorted by their key (the first centre
     // projected on the lane direction, non-finite keys last) with the sorted keys; the block adds
     // the bucket starts over the keys and the largest step bound and radius.
-    __shared__ unsigned s_dmax, s_rmax;
+    __shared__ unsigned s_dmax, s_rmax, s_lmax;
     __shared__ int s_nfin;
     if (threadIdx.x == 0) {
         s_dmax = 0u;
         s_rmax = 0u;
+        s_lmax = 0u;
     }
     __syncthreads();
     const float4* circ = reinterpret_cast<const float4*>(smem + L.off_circ);
@@ -489,10 +496,22 @@ __device__ __forceinline__ void build_boxes(unsigned char* smem, const SceneLayo
         atomicMax(&s_dmax, __float_as_uint(fmaxf(disp[k], 0.0f)));     // non-negative: bits order as values
         atomicMax(&s_rmax, __float_as_uint(fmaxf(circ[k].z, 0.0f)));
     }
+    {
+        // the longest segment (a NaN length, from non-finite input, gives an infinite bound)
+        const float4* seg = reinterpret_cast<const float4*>(smem + L.off_seg);
+        float lm = 0.0f;
+        for (int i = threadIdx.x; i < L.n_seg; i += blockDim.x) {
+            const float l = sqrtf(fmaf(seg[i].x, seg[i].x, seg[i].y * seg[i].y));
+            lm = l >= lm ? l : (l < lm ? lm : INFINITY);
+        }
+        atomicMax(&s_lmax, __float_as_uint(lm));
+    }
     if (threadIdx.x == 0) s_nfin = lower_bound_f(skey, L.n_circ, INFINITY);
     __syncthreads();
     unsigned char* e = const_cast<unsigned char*>(circle_index_base(smem, L));
-    int* start = reinterpret_cast<int*>(e + 16);
+    int* start = reinterpret_cast<int*>(e + 32);
+    if (threadIdx.x == 0)
+        *reinterpret_cast<float4*>(e + 16) = make_float4(4.0f * __uint_as_float(s_lmax), 0.0f, 0.0f, 0.0f);
     const int nfin = s_nfin;
     const float smin = nfin > 0 ? skey[0] : 0.0f;
     const float bw = nfin > 0 ? (skey[nfin - 1] - smin) / (float)CIRC_BUCKETS : 0.0f;
@@ -504,22 +523,44 @@ __device__ __forceinline__ void build_boxes(unsigned char* smem, const SceneLayo
     __syncthreads();
 }
 
+// Distance from a squared distance as d2 * rsqrt(d2) (a few ulp, against the many more
+// instructions of the correctly rounded square root); the argument of the reciprocal square
+// root is raised to the smallest normal, so 0 gives 0 without a compare and a select (and a
+// subnormal d2 gives at most 1.1e-19 m).  The obstacle term uses it only inside the safety
+// band, where c_safe is continuous in it.
+__device__ __forceinline__ float dist_of(float d2) { return d2 * rsqrtf(fmaxf(d2, 1.17549435e-38f)); }
+
+// The pruning bound of the segment search: a box whose computed squared distance from p exceeds
+// prune_lim(best) holds no segment whose computed squared distance (seg_dist2) is at or below
+// best.  In binary32 the computed distances differ from the exact ones by rounding that scales
+// with the coordinates involved (|p|, the distance itself and the segment length: the rounded
+// segment vector and projection, and an end point that may lie outside its box by a rounding
+// of the vertex coordinates), each term a few 2^-24 times its size; the bound allows 2^-20
+// times their sum (lfac = 4 x the longest segment) on the distance, plus 2^-20 relative.
+__device__ __forceinline__ float prune_lim(float best2, float px, float py, float lfac) {
+    const float d = dist_of(best2);
+    const float e = 0x1p-20f * (fabsf(px) + fabsf(py) + 2.0f * d + lfac);
+    const float r = fmaf(d, 0x1p-20f, d + e);
+    return r * r;
+}
+
+__device__ __forceinline__ float key_dist2(unsigned long long key) { return __uint_as_float((unsigned)(key >> 32)); }
+
 // The chunks lo .. hi-1 under the level-2 boxes (the search's rare fallback).
 template <int G, bool STATS>
 __device__ __forceinline__ void search_range(float px, float py, const float2* vert, const float4* seg,
                                              const RefBoxes& rb, int n_seg, int lo, int hi, int lane_g,
-                                             unsigned mask, unsigned long long& best, Counters& cnt) {
-    constexpr float SLACK = 1.0f + 1.0f / 1024.0f;
+                                             unsigned mask, float lfac, unsigned long long& best, Counters& cnt) {
 #pragma unroll 1
     for (int g = lo / REF_L2; g <= (hi - 1) / REF_L2; ++g) {
         if (STATS) cnt.l2++;
-        if (box_dist2(px, py, rb.l2[IX(g, (hi - 1) / REF_L2 + 1)]) > __uint_as_float((unsigned)(best >> 32)) * SLACK)
+        if (box_dist2(px, py, rb.l2[IX(g, (hi - 1) / REF_L2 + 1)]) > prune_lim(key_dist2(best), px, py, lfac))
             continue;
         const int c1 = min(hi, (g + 1) * REF_L2);
 #pragma unroll 1
         for (int c = max(lo, g * REF_L2); c < c1; ++c) {
             if (STATS) cnt.l1++;
-            if (box_dist2(px, py, rb.l1[IX(c, hi)]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK) {
+            if (box_dist2(px, py, rb.l1[IX(c, hi)]) <= prune_lim(key_dist2(best), px, py, lfac)) {
                 scan_chunk<G, STATS>(px, py, vert, seg, c, n_seg, lane_g, best, cnt);
                 best = group_min_key<G>(best, mask);
             }
@@ -532,8 +573,8 @@ __device__ __forceinline__ void search_range(float px, float py, const float2* v
 // after it bound the rest.  Only on a side whose box passes is the neighbouring chunk tested
 // (and scanned if its box passes), then the box of the chunks beyond it, and a range whose box
 // passes is searched under its level-2 and chunk boxes.  A box is skipped only when its
-// lower bound exceeds the best distance (with a relative slack far above binary32
-// rounding), so no segment that can be the closest is missed and the result does not
+// lower bound exceeds the best distance by more than binary32 rounding can account for
+// (prune_lim), so no segment that can be the closest is missed and the result does not
 // depend on jh.  Two segments that share a vertex can be closer than binary32 resolves
 // (next to the vertex on the outside of a bend their distances differ by a second-order
 // term): the winner's neighbours of another heading are re-ordered against it in binary64
@@ -541,41 +582,40 @@ __device__ __forceinline__ void search_range(float px, float py, const float2* v
 template <int G, bool STATS>
 __device__ __forceinline__ void nearest_segment(float px, float py, const float2* vert, const float4* seg,
                                                 const float* head, const RefBoxes& rb, int n_seg, int n_l1,
-                                                int lane_g, unsigned mask, int jh, bool refine, int& jb,
-                                                float& best2, Counters& cnt) {
-    constexpr float SLACK = 1.0f + 1.0f / 1024.0f;
+                                                int lane_g, unsigned mask, int jh, bool refine, float lfac,
+                                                int& jb, float& best2, Counters& cnt) {
     const int cw = jh / REF_L1;
     unsigned long long best = ~0ull;
     scan_chunk<G, STATS>(px, py, vert, seg, cw, n_seg, lane_g, best, cnt);
     best = group_min_key<G>(best, mask);
     // one box bounds every chunk before cw and one every chunk after it: when neither can hold
     // a closer segment, the common case, the search ends here
-    const float lim0 = __uint_as_float((unsigned)(best >> 32)) * SLACK;
+    const float lim0 = prune_lim(key_dist2(best), px, py, lfac);
     const bool left = cw >= 1 && box_dist2(px, py, rb.pre[IX(cw, n_l1 + 1)]) <= lim0;
     const bool right = cw + 1 < n_l1 && box_dist2(px, py, rb.suf[IX(cw + 1, n_l1 + 1)]) <= lim0;
     if (STATS) cnt.l2 += (cw >= 1 ? 1 : 0) + (cw + 1 < n_l1 ? 1 : 0);
     if (left) {
         if (STATS) cnt.l1++;
-        if (box_dist2(px, py, rb.l1[IX(cw - 1, n_l1)]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK) {
+        if (box_dist2(px, py, rb.l1[IX(cw - 1, n_l1)]) <= lim0) {
             scan_chunk<G, STATS>(px, py, vert, seg, cw - 1, n_seg, lane_g, best, cnt);
             best = group_min_key<G>(best, mask);
         }
         if (cw >= 2) {
             if (STATS) cnt.l2++;
-            if (box_dist2(px, py, rb.pre[IX(cw - 1, n_l1 + 1)]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK)
-                search_range<G, STATS>(px, py, vert, seg, rb, n_seg, 0, cw - 1, lane_g, mask, best, cnt);
+            if (box_dist2(px, py, rb.pre[IX(cw - 1, n_l1 + 1)]) <= prune_lim(key_dist2(best), px, py, lfac))
+                search_range<G, STATS>(px, py, vert, seg, rb, n_seg, 0, cw - 1, lane_g, mask, lfac, best, cnt);
         }
     }
     if (right) {
         if (STATS) cnt.l1++;
-        if (box_dist2(px, py, rb.l1[IX(cw + 1, n_l1)]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK) {
+        if (box_dist2(px, py, rb.l1[IX(cw + 1, n_l1)]) <= prune_lim(key_dist2(best), px, py, lfac)) {
             scan_chunk<G, STATS>(px, py, vert, seg, cw + 1, n_seg, lane_g, best, cnt);
             best = group_min_key<G>(best, mask);
         }
         if (cw + 2 < n_l1) {
             if (STATS) cnt.l2++;
-            if (box_dist2(px, py, rb.suf[IX(cw + 2, n_l1 + 1)]) <= __uint_as_float((unsigned)(best >> 32)) * SLACK)
-                search_range<G, STATS>(px, py, vert, seg, rb, n_seg, cw + 2, n_l1, lane_g, mask, best, cnt);
+            if (box_dist2(px, py, rb.suf[IX(cw + 2, n_l1 + 1)]) <= prune_lim(key_dist2(best), px, py, lfac))
+                search_range<G, STATS>(px, py, vert, seg, rb, n_seg, cw + 2, n_l1, lane_g, mask, lfac, best, cnt);
         }
     }
     float b2 = __uint_as_float((unsigned)(best >> 32));
@@ -619,15 +659,14 @@ template <int G>
 __device__ __forceinline__ void nearest_vertex(float px, float py, const float2* vert, const float4* l1,
                                                const float4* l2, int n_ref, int n_l1, int n_l2, int lane_g,
                                                unsigned mask, int& jb, float& best2) {
-    constexpr float SLACK = 1.0f + 1.0f / 1024.0f;
     float dx = px - vert[IX(jb, n_ref)].x, dy = py - vert[IX(jb, n_ref)].y;
     float b2 = fmaf(dx, dx, dy * dy);
     int bi = jb;
     for (int g = 0; g < n_l2; ++g) {
-        if (box_dist2(px, py, l2[IX(g, n_l2)]) > b2 * SLACK) continue;
+        if (box_dist2(px, py, l2[IX(g, n_l2)]) > prune_lim(b2, px, py, 0.0f)) continue;
         const int c1 = min((g + 1) * REF_L2, n_l1);
         for (int c = g * REF_L2; c < c1; ++c) {
-            if (box_dist2(px, py, l1[IX(c, n_l1)]) > b2 * SLACK) continue;
+            if (box_dist2(px, py, l1[IX(c, n_l1)]) > prune_lim(b2, px, py, 0.0f)) continue;
             const int i1 = min((c + 1) * REF_L1 + 1, n_ref);
             for (int i = c * REF_L1 + lane_g; i < i1; i += G) {
                 const float ex = px - vert[IX(i, n_ref)].x, ey = py - vert[IX(i, n_ref)].y;
@@ -663,12 +702,6 @@ __device__ __forceinline__ float2 circle_centre(const float4& c, const float2* v
     return make_float2(fmaf(vv.x, st, c.x), fmaf(vv.y, st, c.y));
 }
 
-// Distance from a squared distance as d2 * rsqrt(d2) (a few ulp, against the many more
-// instructions of the correctly rounded square root); the argument of the reciprocal square
-// root is raised to the smallest normal, so 0 gives 0 without a compare and a select (and a
-// subnormal d2 gives at most 1.1e-19 m).  The obstacle term uses it only inside the safety
-// band, where c_safe is continuous in it.
-__device__ __forceinline__ float dist_of(float d2) { return d2 * rsqrtf(fmaxf(d2, 1.17549435e-38f)); }
 
 // Warp min / max of a float: one redux.sync on binary32 (a NaN lane is ignored, like fminf and
 // fmaxf; the results only bound the warp's broad phase).
@@ -898,14 +931,21 @@ template <int G, bool STATS, bool SIMPLE = false>
 __device__ __forceinline__ float state_cost(const PlanConst& pc, const SceneLayout& L, const Scene& sc,
                                             const float2* table, const StepIn& s, int t, int tb0, int tb1,
                                             bool has_table, bool moving, bool multi_head, bool dconst, int lane,
-                                            int lane_g, unsigned mask, int& jb, int& jbp, Counters& cnt) {
+                                            int lane_g, unsigned mask, int& jb, Counters& cnt) {
     float d2r;
     if (SIMPLE || pc.ref_mode == 0) {
-        // search hint: the last closest segment moved on by its last change
-        const int jh = min(max(2 * jb - jbp, 0), L.n_seg - 1);
-        jbp = jb;
+        // search hint: the last closest segment moved on by the projection of the new position on
+        // it, in units of its length (on a lane of equal segments, the segment that holds the
+        // projection)
+        int jh;
+        {
+            const float2 pa = sc.vert[IX(jb, L.n_ref)];
+            const float4 ps = sc.seg[IX(jb, L.n_seg)];
+            const float tq = fminf(fmaxf(fmaf(s.nx - pa.x, ps.z, (s.ny - pa.y) * ps.w), -64.0f), 64.0f);
+            jh = min(max(jb + (int)floorf(tq), 0), L.n_seg - 1);
+        }
         nearest_segment<G, STATS>(s.nx, s.ny, sc.vert, sc.seg, sc.head, ref_boxes(sc.base, L), L.n_seg, L.n_l1,
-                                  lane_g, mask, jh, multi_head, jb, d2r, cnt);
+                                  lane_g, mask, jh, multi_head, search_lfac(sc.base, L), jb, d2r, cnt);
     } else {
         nearest_vertex<G>(s.nx, s.ny, sc.vert, sc.l1, ref_boxes(sc.base, L).l2, L.n_ref, L.n_l1, L.n_l2, lane_g, mask,
                           jb, d2r);
@@ -1010,7 +1050,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
     if (EXT && pc.model == 1) *steer_slot(smem, L) = make_float2(d0, 0.0f);
     sincosf(r.th, &r.sth, &r.cth);
     r.tdp = fmaf(tp.x, tp.x, tp.y * tp.y);      // |P_0 - T_P|^2 with P_0 = (0, 0)
-    int jb = jb0, jbp = jb0;   // closest segment of the last evaluated step and of the one before
+    int jb = jb0;              // closest segment of the last evaluated step
     float s_hi = 0.0f, s_c = 0.0f, q_last = 0.0f;
     Counters cnt{0, 0, 0, 0, 0, 0, 0};
 
@@ -1020,7 +1060,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
             const StepIn s = dyn_step<BF16, EXT, SIMPLE>(pc, sc.ctl[IX(t, T)], sc.c0[IX(t, T)], zz, tp, r,
                                                          steer_slot(smem, L));
             const float qx = state_cost<G, STATS, SIMPLE>(pc, L, sc, table, s, t, t, t, has_table, moving, multi_head,
-                                                  dconst, lane, lane_g, mask, jb, jbp, cnt);
+                                                  dconst, lane, lane_g, mask, jb, cnt);
             if (EXT && prefix && lane_g == 0 && k < K) prefix[(size_t)t * K + k] = s_hi - s_c;   // cost of steps < t
             kahan_add(s_hi, s_c, qx + s.qu);    // Eq. (6)
             q_last = qx;
@@ -1204,7 +1244,7 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
             }
             const int tb1 = min(t0 + G - 1, T - 1);
             const float qx = state_cost<1, STATS, SIMPLE>(pc, L, sc, table, e, tm, t0, tb1, has_table, moving, multi_head,
-                                                  dconst, lane, 0, mask, jb, jbp, cnt);
+                                                  dconst, lane, 0, mask, jb, cnt);
             const float c = qx + e.qu;
             float pre_own = 0.0f;
 #pragma unroll
