@@ -532,14 +532,16 @@ __device__ __forceinline__ float dist_of(float d2) { return d2 * rsqrtf(fmaxf(d2
 
 // The pruning bound of the segment search: a box whose computed squared distance from p exceeds
 // prune_lim(best) holds no segment whose computed squared distance (seg_dist2) is at or below
-// best.  In binary32 the computed distances differ from the exact ones by rounding that scales
-// with the coordinates involved (|p|, the distance itself and the segment length: the rounded
-// segment vector and projection, and an end point that may lie outside its box by a rounding
-// of the vertex coordinates), each term a few 2^-24 times its size; the bound allows 2^-20
-// times their sum (lfac = 4 x the longest segment) on the distance, plus 2^-20 relative.
-__device__ __forceinline__ float prune_lim(float best2, float px, float py, float lfac) {
+// best.  The rounding in seg_dist2 is relative to the differences it forms (p - a, the projection
+// on e, the residual), so it is a few 2^-24 of (distance + segment length); a segment's far end
+// a + e lies within 2^-24 |e| of its vertex (e is the rounded difference of the two binary32
+// vertices), hence of its box; box_dist2 is within a few 2^-24 relative.  The bound allows 2^-20
+// of (2 distance + 4 longest segment) on the distance (lfac = 4 x the longest segment), plus
+// 2^-20 relative: several times the sum of those terms, and independent of how far p is from
+// the origin of the frame.
+__device__ __forceinline__ float prune_lim(float best2, float lfac) {
     const float d = dist_of(best2);
-    const float e = 0x1p-20f * (fabsf(px) + fabsf(py) + 2.0f * d + lfac);
+    const float e = 0x1p-20f * fmaf(2.0f, d, lfac);
     const float r = fmaf(d, 0x1p-20f, d + e);
     return r * r;
 }
@@ -554,13 +556,13 @@ __device__ __forceinline__ void search_range(float px, float py, const float2* v
 #pragma unroll 1
     for (int g = lo / REF_L2; g <= (hi - 1) / REF_L2; ++g) {
         if (STATS) cnt.l2++;
-        if (box_dist2(px, py, rb.l2[IX(g, (hi - 1) / REF_L2 + 1)]) > prune_lim(key_dist2(best), px, py, lfac))
+        if (box_dist2(px, py, rb.l2[IX(g, (hi - 1) / REF_L2 + 1)]) > prune_lim(key_dist2(best), lfac))
             continue;
         const int c1 = min(hi, (g + 1) * REF_L2);
 #pragma unroll 1
         for (int c = max(lo, g * REF_L2); c < c1; ++c) {
             if (STATS) cnt.l1++;
-            if (box_dist2(px, py, rb.l1[IX(c, hi)]) <= prune_lim(key_dist2(best), px, py, lfac)) {
+            if (box_dist2(px, py, rb.l1[IX(c, hi)]) <= prune_lim(key_dist2(best), lfac)) {
                 scan_chunk<G, STATS>(px, py, vert, seg, c, n_seg, lane_g, best, cnt);
                 best = group_min_key<G>(best, mask);
             }
@@ -590,7 +592,7 @@ __device__ __forceinline__ void nearest_segment(float px, float py, const float2
     best = group_min_key<G>(best, mask);
     // one box bounds every chunk before cw and one every chunk after it: when neither can hold
     // a closer segment, the common case, the search ends here
-    const float lim0 = prune_lim(key_dist2(best), px, py, lfac);
+    const float lim0 = prune_lim(key_dist2(best), lfac);
     const bool left = cw >= 1 && box_dist2(px, py, rb.pre[IX(cw, n_l1 + 1)]) <= lim0;
     const bool right = cw + 1 < n_l1 && box_dist2(px, py, rb.suf[IX(cw + 1, n_l1 + 1)]) <= lim0;
     if (STATS) cnt.l2 += (cw >= 1 ? 1 : 0) + (cw + 1 < n_l1 ? 1 : 0);
@@ -602,19 +604,19 @@ __device__ __forceinline__ void nearest_segment(float px, float py, const float2
         }
         if (cw >= 2) {
             if (STATS) cnt.l2++;
-            if (box_dist2(px, py, rb.pre[IX(cw - 1, n_l1 + 1)]) <= prune_lim(key_dist2(best), px, py, lfac))
+            if (box_dist2(px, py, rb.pre[IX(cw - 1, n_l1 + 1)]) <= prune_lim(key_dist2(best), lfac))
                 search_range<G, STATS>(px, py, vert, seg, rb, n_seg, 0, cw - 1, lane_g, mask, lfac, best, cnt);
         }
     }
     if (right) {
         if (STATS) cnt.l1++;
-        if (box_dist2(px, py, rb.l1[IX(cw + 1, n_l1)]) <= prune_lim(key_dist2(best), px, py, lfac)) {
+        if (box_dist2(px, py, rb.l1[IX(cw + 1, n_l1)]) <= prune_lim(key_dist2(best), lfac)) {
             scan_chunk<G, STATS>(px, py, vert, seg, cw + 1, n_seg, lane_g, best, cnt);
             best = group_min_key<G>(best, mask);
         }
         if (cw + 2 < n_l1) {
             if (STATS) cnt.l2++;
-            if (box_dist2(px, py, rb.suf[IX(cw + 2, n_l1 + 1)]) <= prune_lim(key_dist2(best), px, py, lfac))
+            if (box_dist2(px, py, rb.suf[IX(cw + 2, n_l1 + 1)]) <= prune_lim(key_dist2(best), lfac))
                 search_range<G, STATS>(px, py, vert, seg, rb, n_seg, cw + 2, n_l1, lane_g, mask, lfac, best, cnt);
         }
     }
@@ -663,10 +665,10 @@ __device__ __forceinline__ void nearest_vertex(float px, float py, const float2*
     float b2 = fmaf(dx, dx, dy * dy);
     int bi = jb;
     for (int g = 0; g < n_l2; ++g) {
-        if (box_dist2(px, py, l2[IX(g, n_l2)]) > prune_lim(b2, px, py, 0.0f)) continue;
+        if (box_dist2(px, py, l2[IX(g, n_l2)]) > prune_lim(b2, 0.0f)) continue;
         const int c1 = min((g + 1) * REF_L2, n_l1);
         for (int c = g * REF_L2; c < c1; ++c) {
-            if (box_dist2(px, py, l1[IX(c, n_l1)]) > prune_lim(b2, px, py, 0.0f)) continue;
+            if (box_dist2(px, py, l1[IX(c, n_l1)]) > prune_lim(b2, 0.0f)) continue;
             const int i1 = min((c + 1) * REF_L1 + 1, n_ref);
             for (int i = c * REF_L1 + lane_g; i < i1; i += G) {
                 const float ex = px - vert[IX(i, n_ref)].x, ey = py - vert[IX(i, n_ref)].y;
