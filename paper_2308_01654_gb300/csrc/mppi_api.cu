@@ -315,7 +315,7 @@ int mppi_create(const mppi_params* params, int device, void* cuda_stream, int32_
         size_t n;
     } allocs[] = {
         {(void**)&b.state, sizeof(DevState)},
-        {(void**)&b.scene, (size_t)Lmax.bytes},
+        {(void**)&b.scene, (size_t)Lmax.total},
         {(void**)&b.table, sizeof(float2) * (size_t)T * std::max(c->cap_circ, 1)},
         {(void**)&b.z, zbytes},
         {(void**)&b.S, sizeof(double) * K},

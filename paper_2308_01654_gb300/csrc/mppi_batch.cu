@@ -191,7 +191,8 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 2) batch_rollout_kernel(Bat
         }
         const BatchInst& d = a.inst[td.x];
         const int k = td.y + (int)threadIdx.x / G;   // G lanes per sample
-        rollout_sample<G, TIME, BF16, false, false>(s_pc, s_L, smem, reinterpret_cast<const NT*>(a.z) + d.z_off,
+        rollout_sample<G, TIME, BF16, false, false>(s_pc, s_L, smem, a.scene + d.scene_off,
+                                       reinterpret_cast<const NT*>(a.z) + d.z_off,
                                        a.table + d.table_off, s_x0, 0.0f, s_moving != 0, s_multi != 0, s_jb0, k,
                                        a.S + d.s_off,
                                        nullptr);
@@ -462,7 +463,7 @@ int mppi_batch_create(int32_t max_slots, int32_t max_batch, int64_t max_samples,
     B->max_steps = max_rollout_steps;
     B->max_tiles = max_samples / 16 + max_batch;
     const SceneLayout Lmax = make_layout(max_T, max_ref, max_circ);
-    B->max_scene = up((size_t)Lmax.bytes);
+    B->max_scene = up((size_t)Lmax.total);
     B->rollout_smem = up(rollout_smem_bytes(Lmax, BATCH_MAX_THREADS, false));   // blob and the boxes built after it
     B->max_in = 4 + 2 * (size_t)max_ref + 5 * (size_t)max_circ + 2 * (size_t)max_T * max_circ;
     B->max_out = out_elems(max_T);
@@ -627,7 +628,7 @@ static int build_submission(mppi_batch* B, Pipeline& p, mppi_request* req, int n
         p.s_counts[(size_t)i] = K;
         z_off += (long long)K * T;
         s_off += K;
-        scene_off += (long long)up((size_t)d.L.bytes);
+        scene_off += (long long)up((size_t)d.L.total);
         in_off += (long long)(4 + nr + nc + nt);
         table_off += (long long)T * std::max(r.n_circ, 1);
         out_off += (long long)out_elems(T);

@@ -52,7 +52,11 @@ struct SceneLayout {
     int off_proj;    // float4           (dx, dy, 0, 0): unit direction of the lane (first to last vertex)
     int off_order;   // int    [n_circ]  input index of each sorted circle (its column of the centre table)
     int off_skey;    // float  [n_circ]  the sorted keys
-    int bytes;       // total, a multiple of 16
+    int bytes;       // the staged part (all of the above), a multiple of 16
+    // after the staged part, read from global memory (through L1) by the segment search:
+    int off_pbox;    // float4 [n_ref]   box of the vertices 0 .. i
+    int off_sbox;    // float4 [n_ref]   box of the vertices i .. n_ref - 1
+    int total;       // the whole scene buffer, a multiple of 16
 };
 
 // Per-plan constants in the precision the kernels use.
@@ -113,12 +117,12 @@ struct PlanBuffers {
 };
 
 // Shared memory each rollout block builds after the staged blob: the level-2 boxes, the
-// prefix and suffix boxes of the chunk sequence, the circle index (a float4 of scalars and
-// CIRC_BUCKETS + 1 bucket starts into the sorted circles) and a float4 of search scalars.
+// circle index (a float4 of scalars and CIRC_BUCKETS + 1 bucket starts into the sorted
+// circles) and a float4 of search scalars.
 constexpr int CIRC_BUCKETS = 64;
 
 __host__ __device__ inline size_t block_extra_bytes(const SceneLayout& L) {
-    return (size_t)16 * (L.n_l2 + 2 * (L.n_l1 + 1)) + 32 + (size_t)4 * ((CIRC_BUCKETS + 1 + 3) & ~3);
+    return (size_t)16 * L.n_l2 + 32 + (size_t)4 * ((CIRC_BUCKETS + 1 + 3) & ~3);
 }
 
 // Per-thread slots after the block's extras: the compensated steering angle of the

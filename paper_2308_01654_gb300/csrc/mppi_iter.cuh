@@ -19,6 +19,11 @@ __device__ __forceinline__ float2 local_vertex(const double* ref, int i, double 
     return make_float2((float)(ref[2 * i] - ox), (float)(ref[2 * i + 1] - oy));
 }
 
+// (min x, min y, max x, max y) of two boxes
+__device__ __forceinline__ float4 box_union(float4 a, float4 b) {
+    return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
+}
+
 __device__ __forceinline__ float4 seg_record(const double* ref, int i, double ox, double oy) {
     const float2 a = local_vertex(ref, i, ox, oy), b = local_vertex(ref, i + 1, ox, oy);
     const float ex = b.x - a.x, ey = b.y - a.y;
@@ -68,10 +73,11 @@ __device__ __forceinline__ int circle_rank(const PlanInputs& in, int k, float kk
 
 // The preparation in independent phases: 0 controls and x0, 1 vertices, 2 segments and the
 // segment nearest x0, 3 level-1 boxes, 4 circles and the lane direction, 5 the per-step
-// centre table, 6 the largest step of each tabulated centre.  phase < 0 runs them all in
-// turn (one block per plan in the batched planner); the single-plan kernel gives each phase
-// its own row of blocks, so the phases run side by side instead of one after another.
-constexpr int PREP_PHASES = 7;
+// centre table, 6 the largest step of each tabulated centre, 7 the prefix and suffix boxes of
+// the vertices.  phase < 0 runs them all in turn (one block per plan in the batched planner);
+// the single-plan kernel gives each phase its own row of blocks, so the phases run side by side
+// instead of one after another.
+constexpr int PREP_PHASES = 8;
 
 __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayout& L, const PlanInputs& in,
                                            const PlanBuffers& b, int tid, int nth, int phase = -1) {
@@ -201,6 +207,74 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
             const int pos = __reduce_add_sync(
                 0xffffffffu, (unsigned)circle_rank(in, k, circle_key(in, k, ox, oy, pj), ox, oy, pj, lane, 32));
             if (lane == 0) disp[pos] = isfinite(m) ? (float)(m * 1.001) + 1e-5f : INFINITY;
+        }
+    }
+    if ((all || phase == 7) && tid < (int)blockDim.x) {
+        // prefix and suffix boxes of the vertices, by the first block of the phase (every thread of
+        // it takes part): each thread a run of consecutive vertices, the runs combined in order by a
+        // warp scan and a scan of the warp totals; the suffix pass takes the runs in reverse
+        float4* pre = reinterpret_cast<float4*>(sc + L.off_pbox);
+        float4* suf = reinterpret_cast<float4*>(sc + L.off_sbox);
+        __shared__ float4 s_wbox[32];
+        const float4 empty = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
+        const int nb = blockDim.x, th = threadIdx.x, nw = (nb + 31) >> 5;
+        const int run = (L.n_ref + nb - 1) / nb;
+        for (int dir = 0; dir < 2; ++dir) {
+            const int r = dir ? nb - 1 - th : th;
+            const int i0 = min(r * run, L.n_ref), i1 = min(i0 + run, L.n_ref);
+            float4 agg = empty;
+            for (int i = i0; i < i1; ++i) {
+                const float2 v = local_vertex(in.ref, i, ox, oy);
+                agg = box_union(agg, make_float4(v.x, v.y, v.x, v.y));
+            }
+            float4 inc = agg;          // inclusive scan in thread order within the warp
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                float4 u;
+                u.x = __shfl_up_sync(0xffffffffu, inc.x, o);
+                u.y = __shfl_up_sync(0xffffffffu, inc.y, o);
+                u.z = __shfl_up_sync(0xffffffffu, inc.z, o);
+                u.w = __shfl_up_sync(0xffffffffu, inc.w, o);
+                if (lane >= o) inc = box_union(inc, u);
+            }
+            if (lane == 31) s_wbox[wid] = inc;
+            __syncthreads();
+            if (wid == 0) {
+                float4 t = lane < nw ? s_wbox[lane] : empty;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    float4 u;
+                    u.x = __shfl_up_sync(0xffffffffu, t.x, o);
+                    u.y = __shfl_up_sync(0xffffffffu, t.y, o);
+                    u.z = __shfl_up_sync(0xffffffffu, t.z, o);
+                    u.w = __shfl_up_sync(0xffffffffu, t.w, o);
+                    if (lane >= o) t = box_union(t, u);
+                }
+                if (lane < nw) s_wbox[lane] = t;
+            }
+            __syncthreads();
+            // this thread's exclusive prefix: the earlier warps and the earlier lanes of its warp
+            float4 carry = wid > 0 ? s_wbox[wid - 1] : empty;
+            float4 prev;
+            prev.x = __shfl_up_sync(0xffffffffu, inc.x, 1);
+            prev.y = __shfl_up_sync(0xffffffffu, inc.y, 1);
+            prev.z = __shfl_up_sync(0xffffffffu, inc.z, 1);
+            prev.w = __shfl_up_sync(0xffffffffu, inc.w, 1);
+            if (lane > 0) carry = box_union(carry, prev);
+            if (dir == 0) {
+                for (int i = i0; i < i1; ++i) {
+                    const float2 v = local_vertex(in.ref, i, ox, oy);
+                    carry = box_union(carry, make_float4(v.x, v.y, v.x, v.y));
+                    pre[i] = carry;
+                }
+            } else {
+                for (int i = i1 - 1; i >= i0; --i) {
+                    const float2 v = local_vertex(in.ref, i, ox, oy);
+                    carry = box_union(carry, make_float4(v.x, v.y, v.x, v.y));
+                    suf[i] = carry;
+                }
+            }
+            __syncthreads();           // s_wbox is reused by the second pass
         }
     }
     if (bad) atomicOr(&b.state->flags, FLAG_NONFINITE_INPUT);
@@ -344,12 +418,12 @@ __device__ __forceinline__ unsigned long long group_min_key(unsigned long long k
     return k;
 }
 
-// One level-1 chunk; the lanes of a group split its REF_L1 segments.
+// REF_L1 consecutive segments from i0 (a level-1 chunk, or the search window); the lanes of a
+// group split them.
 template <int G, bool STATS>
-__device__ __forceinline__ void scan_chunk(float px, float py, const float2* vert, const float4* seg, int c,
+__device__ __forceinline__ void scan_chunk(float px, float py, const float2* vert, const float4* seg, int i0,
                                            int n_seg, int lane_g, unsigned long long& best, Counters& cnt) {
     constexpr int PER = (REF_L1 + G - 1) / G;
-    const int i0 = c * REF_L1;
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
         const int o = lane_g + q * G;
@@ -362,10 +436,11 @@ __device__ __forceinline__ void scan_chunk(float px, float py, const float2* ver
     }
 }
 
-// Boxes built by each rollout block in shared memory right after the staged blob, from
-// the staged chunk boxes: the level-2 boxes (each the union of REF_L2 chunk boxes), and the
-// prefix and suffix boxes of the chunk sequence, pre[i] = box of the chunks 0 .. i-1 and
-// suf[i] = box of the chunks i .. n_l1-1 (i = 0 .. n_l1; the empty box never passes a test).
+// The boxes of the segment search: the staged chunk boxes (l1), the level-2 boxes each rollout
+// block builds in shared memory right after the staged blob (each the union of REF_L2 chunk
+// boxes), and the prefix and suffix boxes of the vertices that scene preparation leaves in
+// global memory after the staged part, pre[i] = box of the vertices 0 .. i (the segments
+// 0 .. i-1) and suf[i] = box of the vertices i .. n_ref-1 (the segments i .. n_seg-1).
 struct RefBoxes {
     const float4* l1;
     const float4* l2;
@@ -373,12 +448,13 @@ struct RefBoxes {
     const float4* suf;
 };
 
-__device__ __forceinline__ RefBoxes ref_boxes(const unsigned char* smem, const SceneLayout& L) {
+__device__ __forceinline__ RefBoxes ref_boxes(const unsigned char* smem, const unsigned char* gscene,
+                                              const SceneLayout& L) {
     RefBoxes r;
     r.l1 = reinterpret_cast<const float4*>(smem + L.off_l1);
     r.l2 = reinterpret_cast<const float4*>(smem + L.bytes);
-    r.pre = r.l2 + L.n_l2;
-    r.suf = r.pre + (L.n_l1 + 1);
+    r.pre = reinterpret_cast<const float4*>(gscene + L.off_pbox);
+    r.suf = reinterpret_cast<const float4*>(gscene + L.off_sbox);
     return r;
 }
 
@@ -394,7 +470,7 @@ struct CircleIndex {
 };
 
 __device__ __forceinline__ const unsigned char* circle_index_base(const unsigned char* smem, const SceneLayout& L) {
-    return smem + L.bytes + 16 * (L.n_l2 + 2 * (L.n_l1 + 1));
+    return smem + L.bytes + 16 * L.n_l2;
 }
 
 __device__ __forceinline__ CircleIndex circle_index(const unsigned char* smem, const SceneLayout& L) {
@@ -430,53 +506,15 @@ __device__ __forceinline__ int lower_bound_f(const float* skey, int n, float v) 
     return lo;
 }
 
-__device__ __forceinline__ float4 box_union(float4 a, float4 b) {
-    return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
-}
 
 __device__ __forceinline__ void build_boxes(unsigned char* smem, const SceneLayout& L) {
-    const RefBoxes r = ref_boxes(smem, L);
-    float4* l2 = const_cast<float4*>(r.l2);
-    float4* pre = const_cast<float4*>(r.pre);
-    float4* suf = const_cast<float4*>(r.suf);
-    const float4 empty = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
+    const float4* l1 = reinterpret_cast<const float4*>(smem + L.off_l1);
+    float4* l2 = reinterpret_cast<float4*>(smem + L.bytes);
     for (int g = threadIdx.x; g < L.n_l2; g += blockDim.x) {
-        float4 a = r.l1[g * REF_L2];
+        float4 a = l1[g * REF_L2];
         const int c1 = min((g + 1) * REF_L2, L.n_l1);
-        for (int c = g * REF_L2 + 1; c < c1; ++c) a = box_union(a, r.l1[c]);
+        for (int c = g * REF_L2 + 1; c < c1; ++c) a = box_union(a, l1[c]);
         l2[g] = a;
-    }
-    // warp 0 scans the chunks forwards (prefix boxes), warp 1 backwards (suffix boxes)
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    for (int side = w; side < 2; side += nw) {
-        float4 carry = empty;
-        for (int base = 0; base < L.n_l1; base += 32) {
-            const int j = base + lane;
-            const int c = side == 0 ? j : L.n_l1 - 1 - j;
-            float4 v = j < L.n_l1 ? r.l1[c] : empty;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                float4 u;
-                u.x = __shfl_up_sync(0xffffffffu, v.x, o);
-                u.y = __shfl_up_sync(0xffffffffu, v.y, o);
-                u.z = __shfl_up_sync(0xffffffffu, v.z, o);
-                u.w = __shfl_up_sync(0xffffffffu, v.w, o);
-                if (lane >= o) v = box_union(v, u);
-            }
-            v = box_union(v, carry);
-            if (j < L.n_l1) {
-                if (side == 0) pre[c + 1] = v;
-                else suf[c] = v;
-            }
-            carry.x = __shfl_sync(0xffffffffu, v.x, 31);
-            carry.y = __shfl_sync(0xffffffffu, v.y, 31);
-            carry.z = __shfl_sync(0xffffffffu, v.z, 31);
-            carry.w = __shfl_sync(0xffffffffu, v.w, 31);
-        }
-        if (lane == 0) {
-            if (side == 0) pre[0] = empty;
-            else suf[L.n_l1] = empty;
-        }
     }
     // circle index.  Scene preparation stored the circles sorted by their key (the first centre
     // projected on the lane direction, non-finite keys last) with the sorted keys; the block adds
@@ -563,63 +601,43 @@ __device__ __forceinline__ void search_range(float px, float py, const float2* v
         for (int c = max(lo, g * REF_L2); c < c1; ++c) {
             if (STATS) cnt.l1++;
             if (box_dist2(px, py, rb.l1[IX(c, hi)]) <= prune_lim(key_dist2(best), lfac)) {
-                scan_chunk<G, STATS>(px, py, vert, seg, c, n_seg, lane_g, best, cnt);
+                scan_chunk<G, STATS>(px, py, vert, seg, c * REF_L1, n_seg, lane_g, best, cnt);
                 best = group_min_key<G>(best, mask);
             }
         }
     }
 }
 
-// Closest point of the polyline (ties -> lowest segment).  The chunk of the predicted
-// segment jh is scanned first; one box of all the chunks before it and one of all the chunks
-// after it bound the rest.  Only on a side whose box passes is the neighbouring chunk tested
-// (and scanned if its box passes), then the box of the chunks beyond it, and a range whose box
-// passes is searched under its level-2 and chunk boxes.  A box is skipped only when its
-// lower bound exceeds the best distance by more than binary32 rounding can account for
-// (prune_lim), so no segment that can be the closest is missed and the result does not
-// depend on jh.  Two segments that share a vertex can be closer than binary32 resolves
-// (next to the vertex on the outside of a bend their distances differ by a second-order
-// term): the winner's neighbours of another heading are re-ordered against it in binary64
-// when their binary32 distances are within 4e-6.
+// Closest point of the polyline (ties -> lowest segment).  The window of REF_L1 segments around
+// the hint jh (from jh - 1, moved inside the polyline) is scanned first; the prefix box of the
+// vertices before it and the suffix box of those after it bound the rest, and a side whose box
+// passes is searched under its level-2 and chunk boxes (rare: the window keeps a segment on
+// either side of the hint).  A box is skipped only when its lower bound exceeds the best
+// distance by more than binary32 rounding can account for (prune_lim), so no segment that can
+// be the closest is missed and the result does not depend on jh.  Two segments that share a
+// vertex can be closer than binary32 resolves (next to the vertex on the outside of a bend
+// their distances differ by a second-order term): the winner's neighbours of another heading
+// are re-ordered against it in binary64 when their binary32 distances are within 4e-6.
 template <int G, bool STATS>
 __device__ __forceinline__ void nearest_segment(float px, float py, const float2* vert, const float4* seg,
                                                 const float* head, const RefBoxes& rb, int n_seg, int n_l1,
                                                 int lane_g, unsigned mask, int jh, bool refine, float lfac,
                                                 int& jb, float& best2, Counters& cnt) {
-    const int cw = jh / REF_L1;
+    const int w0 = max(min(jh - 1, n_seg - REF_L1), 0), w1 = w0 + REF_L1;
     unsigned long long best = ~0ull;
-    scan_chunk<G, STATS>(px, py, vert, seg, cw, n_seg, lane_g, best, cnt);
+    scan_chunk<G, STATS>(px, py, vert, seg, w0, n_seg, lane_g, best, cnt);
     best = group_min_key<G>(best, mask);
-    // one box bounds every chunk before cw and one every chunk after it: when neither can hold
-    // a closer segment, the common case, the search ends here
+    // segments 0 .. w0-1 lie in the box of the vertices 0 .. w0, segments w1 .. n_seg-1 in that of
+    // the vertices w1 .. n_seg: when neither box can hold a closer segment, the common case, the
+    // search ends here
     const float lim0 = prune_lim(key_dist2(best), lfac);
-    const bool left = cw >= 1 && box_dist2(px, py, rb.pre[IX(cw, n_l1 + 1)]) <= lim0;
-    const bool right = cw + 1 < n_l1 && box_dist2(px, py, rb.suf[IX(cw + 1, n_l1 + 1)]) <= lim0;
-    if (STATS) cnt.l2 += (cw >= 1 ? 1 : 0) + (cw + 1 < n_l1 ? 1 : 0);
-    if (left) {
-        if (STATS) cnt.l1++;
-        if (box_dist2(px, py, rb.l1[IX(cw - 1, n_l1)]) <= lim0) {
-            scan_chunk<G, STATS>(px, py, vert, seg, cw - 1, n_seg, lane_g, best, cnt);
-            best = group_min_key<G>(best, mask);
-        }
-        if (cw >= 2) {
-            if (STATS) cnt.l2++;
-            if (box_dist2(px, py, rb.pre[IX(cw - 1, n_l1 + 1)]) <= prune_lim(key_dist2(best), lfac))
-                search_range<G, STATS>(px, py, vert, seg, rb, n_seg, 0, cw - 1, lane_g, mask, lfac, best, cnt);
-        }
-    }
-    if (right) {
-        if (STATS) cnt.l1++;
-        if (box_dist2(px, py, rb.l1[IX(cw + 1, n_l1)]) <= prune_lim(key_dist2(best), lfac)) {
-            scan_chunk<G, STATS>(px, py, vert, seg, cw + 1, n_seg, lane_g, best, cnt);
-            best = group_min_key<G>(best, mask);
-        }
-        if (cw + 2 < n_l1) {
-            if (STATS) cnt.l2++;
-            if (box_dist2(px, py, rb.suf[IX(cw + 2, n_l1 + 1)]) <= prune_lim(key_dist2(best), lfac))
-                search_range<G, STATS>(px, py, vert, seg, rb, n_seg, cw + 2, n_l1, lane_g, mask, lfac, best, cnt);
-        }
-    }
+    const bool left = w0 >= 1 && box_dist2(px, py, __ldg(rb.pre + IX(w0, n_seg + 1))) <= lim0;
+    const bool right = w1 < n_seg && box_dist2(px, py, __ldg(rb.suf + IX(w1, n_seg + 1))) <= lim0;
+    if (STATS) cnt.l2 += (w0 >= 1 ? 1 : 0) + (w1 < n_seg ? 1 : 0);
+    if (left) search_range<G, STATS>(px, py, vert, seg, rb, n_seg, 0, (w0 - 1) / REF_L1 + 1, lane_g, mask, lfac,
+                                     best, cnt);
+    if (right) search_range<G, STATS>(px, py, vert, seg, rb, n_seg, w1 / REF_L1, n_l1, lane_g, mask, lfac, best,
+                                      cnt);
     float b2 = __uint_as_float((unsigned)(best >> 32));
     int bi = (int)(best & 0xffffffffu);
     const int b0 = bi;
@@ -833,6 +851,7 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const unsigne
 // The scene blob as staged in shared memory (base: its first byte; the level-2 boxes follow it).
 struct Scene {
     const unsigned char* base;
+    const unsigned char* gscene;   // the scene buffer in global memory (the search's vertex boxes)
     const float4* ctl;
     const float* c0;
     const float2* vert;
@@ -844,9 +863,11 @@ struct Scene {
     const float* disp;
 };
 
-__device__ __forceinline__ Scene scene_of(const SceneLayout& L, const unsigned char* smem) {
+__device__ __forceinline__ Scene scene_of(const SceneLayout& L, const unsigned char* smem,
+                                          const unsigned char* gscene) {
     Scene s;
     s.base = smem;
+    s.gscene = gscene;
     s.ctl = reinterpret_cast<const float4*>(smem + L.off_ctl);
     s.c0 = reinterpret_cast<const float*>(smem + L.off_c0);
     s.vert = reinterpret_cast<const float2*>(smem + L.off_vert);
@@ -946,10 +967,10 @@ __device__ __forceinline__ float state_cost(const PlanConst& pc, const SceneLayo
             const float tq = fminf(fmaxf(fmaf(s.nx - pa.x, ps.z, (s.ny - pa.y) * ps.w), -64.0f), 64.0f);
             jh = min(max(jb + (int)floorf(tq), 0), L.n_seg - 1);
         }
-        nearest_segment<G, STATS>(s.nx, s.ny, sc.vert, sc.seg, sc.head, ref_boxes(sc.base, L), L.n_seg, L.n_l1,
+        nearest_segment<G, STATS>(s.nx, s.ny, sc.vert, sc.seg, sc.head, ref_boxes(sc.base, sc.gscene, L), L.n_seg, L.n_l1,
                                   lane_g, mask, jh, multi_head, search_lfac(sc.base, L), jb, d2r, cnt);
     } else {
-        nearest_vertex<G>(s.nx, s.ny, sc.vert, sc.l1, ref_boxes(sc.base, L).l2, L.n_ref, L.n_l1, L.n_l2, lane_g, mask,
+        nearest_vertex<G>(s.nx, s.ny, sc.vert, sc.l1, ref_boxes(sc.base, sc.gscene, L).l2, L.n_ref, L.n_l1, L.n_l2, lane_g, mask,
                           jb, d2r);
     }
     const float thr = sc.head[IX(min(jb, L.n_seg - 1), L.n_seg)];
@@ -1024,12 +1045,13 @@ __device__ __forceinline__ void check_smem(const SceneLayout& L, bool model1) {
 // constants (the same arithmetic, so the same bits, with fewer instructions).
 template <int G, bool TIME, bool BF16, bool STATS, bool EXT, bool SIMPLE = false>
 __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneLayout& L, const unsigned char* smem,
+                                               const unsigned char* gscene,
                                                const typename NoiseT<BF16>::type* __restrict__ z,
                                                const float2* table, float4 x0, float d0, bool moving,
                                                bool multi_head, int jb0, int k, double* S_out,
                                                unsigned long long* stats,
                                                float* prefix = nullptr) {
-    const Scene sc = scene_of(L, smem);
+    const Scene sc = scene_of(L, smem, gscene);
     const int lane = threadIdx.x & 31;
     const int lane_g = threadIdx.x & (G - 1);
     const unsigned mask = group_mask<G>();

@@ -43,6 +43,9 @@ SceneLayout make_layout(int T, int n_ref, int n_circ) {
     L.off_order = o; o = align16(o + 4 * n_circ);
     L.off_skey = o; o = align16(o + 4 * n_circ);
     L.bytes = o;
+    L.off_pbox = o; o = align16(o + 16 * n_ref);
+    L.off_sbox = o; o = align16(o + 16 * n_ref);
+    L.total = o;
     return L;
 }
 
@@ -198,11 +201,11 @@ __global__ void __launch_bounds__(MAX_ROLLOUT_THREADS, 1) rollout_kernel(PlanCon
         const int k = (blockIdx.x * blockDim.x + threadIdx.x) / G;
         const bool moving = b.state->moving != 0, multi = b.state->multi_head != 0;
         if (SIMPLE && !moving && !multi)
-            rollout_sample<G, TIME, BF16, STATS, EXT, true>(pc, L, smem, z, b.table, b.state->x0f, b.state->delta0f,
+            rollout_sample<G, TIME, BF16, STATS, EXT, true>(pc, L, smem, b.scene, z, b.table, b.state->x0f, b.state->delta0f,
                                                            false, false, (int)(b.state->jkey & 0xffffffffu), k, b.S,
                                                            b.stats, nullptr);
         else
-            rollout_sample<G, TIME, BF16, STATS, EXT>(pc, L, smem, z, b.table, b.state->x0f, b.state->delta0f, moving,
+            rollout_sample<G, TIME, BF16, STATS, EXT>(pc, L, smem, b.scene, z, b.table, b.state->x0f, b.state->delta0f, moving,
                                                       multi, (int)(b.state->jkey & 0xffffffffu), k, b.S, b.stats,
                                                       pc.cost_to_go ? b.ctg_prefix : nullptr);
     }

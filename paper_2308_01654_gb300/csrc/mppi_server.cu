@@ -93,7 +93,7 @@ static int sfail(mppi_server* s, int st, const std::string& m) {
 static size_t footprint_of(const mppi_params& p, int n_ref, int n_circ) {
     const size_t K = (size_t)p.K, T = (size_t)p.T;
     const mppi::SceneLayout L = mppi::make_layout(p.T, n_ref, n_circ);
-    return K * T * (p.noise_bf16 ? 4 : 8) + K * (8 + 4) + (size_t)L.bytes + T * (size_t)(n_circ > 0 ? n_circ : 1) * 8;
+    return K * T * (p.noise_bf16 ? 4 : 8) + K * (8 + 4) + (size_t)L.total + T * (size_t)(n_circ > 0 ? n_circ : 1) * 8;
 }
 
 static void scheduler_loop(mppi_server* S) {

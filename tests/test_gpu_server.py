@@ -105,9 +105,10 @@ def test_server_agrees_with_the_single_plan_path():
 def test_hbm_budget_limits_what_is_in_flight():
     probs = sessions(n=6)
     params = [mp.make_params(p.params) for p in probs]
-    # room for the largest request (noise, costs and weights, ~60 KB for its scene) but not for all six
+    # room for the largest request (noise, costs and weights, and up to ~250 KB for its scene with
+    # the search's vertex boxes and its centre table) but not for all six
     biggest = max(p.K * p.T * 8 + p.K * 12 for p in probs)
-    budget = biggest + 60_000
+    budget = biggest + 250_000
     assert sum(p.K * p.T * 8 for p in probs) > budget
     reqs = [(s, probs[s].circles) for s in range(6)]
     with server_for(probs, hbm_budget_bytes=budget) as srv:
