@@ -586,9 +586,10 @@ __device__ __forceinline__ float prune_lim(float best2, float lfac) {
 
 __device__ __forceinline__ float key_dist2(unsigned long long key) { return __uint_as_float((unsigned)(key >> 32)); }
 
-// The chunks lo .. hi-1 under the level-2 boxes (the search's rare fallback).
+// The chunks lo .. hi-1 under the level-2 boxes (the search's rare fallback: out of line, so the
+// common path keeps its registers).
 template <int G, bool STATS>
-__device__ __forceinline__ void search_range(float px, float py, const float2* vert, const float4* seg,
+__device__ __noinline__ void search_range(float px, float py, const float2* vert, const float4* seg,
                                              const RefBoxes& rb, int n_seg, int lo, int hi, int lane_g,
                                              unsigned mask, float lfac, unsigned long long& best, Counters& cnt) {
 #pragma unroll 1
@@ -810,8 +811,7 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const unsigne
             const float p2 = pr * pr;
             if (dconst) {
                 // equal ego radii: the closest ego circle gives the pair minimum (sqrt and the
-                // subtraction are monotone), one square root per circle; the minimum over the
-                // in-band circles is taken without a branch
+                // subtraction are monotone), one square root per circle
                 float d2m;
                 if (SIMPLE || pc.n_ego == 3) {        // the paper's ego model: three circles, no bound checks
                     const float e0 = al - pc.ego_off[0], e1 = al - pc.ego_off[1], e2 = al - pc.ego_off[2];
@@ -825,10 +825,11 @@ __device__ __forceinline__ float obstacle_min(const PlanConst& pc, const unsigne
                         d2m = fminf(d2m, fmaf(de, de, p2));
                     }
                 }
-                const bool in_band = d2m <= c.w;
-                if (STATS && in_band) cnt.pair++;
-                const float dd = dist_of(d2m) - (c.z + pc.ego_rad[0]);
-                dobj = in_band ? fminf(dobj, dd) : dobj;
+                // every candidate enters the minimum: a pair outside the band has a clearance above
+                // the band, so it neither lowers the minimum below an in-band pair's nor, alone,
+                // brings the clearance under d_safe (c_safe stays 0, as with no pair)
+                if (STATS && d2m <= c.w) cnt.pair++;
+                dobj = fminf(dobj, dist_of(d2m) - (c.z + pc.ego_rad[0]));
             } else {
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
