@@ -161,11 +161,13 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
         const float2 pj = lane_direction(in.ref, L.n_ref);
         int* order = reinterpret_cast<int*>(sc + L.off_order);
         float* skey = reinterpret_cast<float*>(sc + L.off_skey);
-        for (int k = tid; k < L.n_circ; k += nth) {
+        // one warp per circle: the lanes count the circles ordered before it in strides of 32
+        for (int k = wid; k < L.n_circ; k += nwarps) {
             const double* c = in.circ + 5 * k;
-            for (int j = 0; j < 5; ++j) bad |= !isfinite(c[j]);
             const float kk = circle_key(in, k, ox, oy, pj);
-            const int pos = circle_rank(in, k, kk, ox, oy, pj, 0, 1);
+            const int pos = __reduce_add_sync(0xffffffffu, (unsigned)circle_rank(in, k, kk, ox, oy, pj, lane, 32));
+            if (lane != 0) continue;
+            for (int j = 0; j < 5; ++j) bad |= !isfinite(c[j]);
             const float r = (float)c[2];
             // band limit (m + r + r_ego)^2 for the constant-d_safe, equal-ego-radius case
             const float m = pc.collision_only ? fmaxf(pc.d_safe_0, 0.0f) : pc.d_safe_0;
@@ -223,9 +225,12 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
             const int r = dir ? nb - 1 - th : th;
             const int i0 = min(r * run, L.n_ref), i1 = min(i0 + run, L.n_ref);
             float4 agg = empty;
-            for (int i = i0; i < i1; ++i) {
-                const float2 v = local_vertex(in.ref, i, ox, oy);
-                agg = box_union(agg, make_float4(v.x, v.y, v.x, v.y));
+            for (int i = i0; i < i1; i += 4) {          // four independent loads in flight
+                float2 v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = local_vertex(in.ref, min(i + q, i1 - 1), ox, oy);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) agg = box_union(agg, make_float4(v[q].x, v[q].y, v[q].x, v[q].y));
             }
             float4 inc = agg;          // inclusive scan in thread order within the warp
 #pragma unroll
@@ -261,17 +266,20 @@ __device__ __forceinline__ void prep_scene(const PlanConst& pc, const SceneLayou
             prev.z = __shfl_up_sync(0xffffffffu, inc.z, 1);
             prev.w = __shfl_up_sync(0xffffffffu, inc.w, 1);
             if (lane > 0) carry = box_union(carry, prev);
-            if (dir == 0) {
-                for (int i = i0; i < i1; ++i) {
-                    const float2 v = local_vertex(in.ref, i, ox, oy);
-                    carry = box_union(carry, make_float4(v.x, v.y, v.x, v.y));
-                    pre[i] = carry;
+            for (int i = i0; i < i1; i += 4) {
+                // the run in groups of four (forward for the prefix, backward for the suffix)
+                float2 v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int iq = dir == 0 ? min(i + q, i1 - 1) : max(i1 - 1 - (i - i0) - q, i0);
+                    v[q] = local_vertex(in.ref, iq, ox, oy);
                 }
-            } else {
-                for (int i = i1 - 1; i >= i0; --i) {
-                    const float2 v = local_vertex(in.ref, i, ox, oy);
-                    carry = box_union(carry, make_float4(v.x, v.y, v.x, v.y));
-                    suf[i] = carry;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (i + q >= i1) break;
+                    carry = box_union(carry, make_float4(v[q].x, v[q].y, v[q].x, v[q].y));
+                    if (dir == 0) pre[i + q] = carry;
+                    else suf[i1 - 1 - (i - i0) - q] = carry;
                 }
             }
             __syncthreads();           // s_wbox is reused by the second pass
