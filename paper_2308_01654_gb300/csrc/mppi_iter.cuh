@@ -617,11 +617,47 @@ __device__ __noinline__ void search_range(float px, float py, const float2* vert
     }
 }
 
+// One side of the search beyond the window: from chunk c outward (dir -1: towards the start,
+// +1: towards the end), a chunk whose box passes is scanned, and the walk stops as soon as the
+// vertex box of everything beyond the chunk fails; after SIDE_WALK chunks the rest of the side is
+// searched under the level-2 boxes.  On a curved lane the box of everything before (or after) a
+// point spans the curve's width, so it passes for most rollouts off the lane: the walk then
+// ends after the few chunks within the rollout's distance instead of testing every level-2 box.
+constexpr int SIDE_WALK = 8;
+
+template <int G, bool STATS>
+__device__ __forceinline__ void side_walk(float px, float py, const float2* vert, const float4* seg,
+                                          const RefBoxes& rb, int n_seg, int n_l1, int lane_g, unsigned mask,
+                                          float lfac, int c, int dir, unsigned long long& best, Counters& cnt) {
+    for (int s = 0;; ++s) {
+        float lim = prune_lim(key_dist2(best), lfac);
+        if (STATS) cnt.l1++;
+        if (box_dist2(px, py, rb.l1[IX(c, n_l1)]) <= lim) {
+            scan_chunk<G, STATS>(px, py, vert, seg, c * REF_L1, n_seg, lane_g, best, cnt);
+            best = group_min_key<G>(best, mask);
+            lim = prune_lim(key_dist2(best), lfac);
+        }
+        // the chunks beyond c: 0 .. c-1 (the vertices 0 .. REF_L1 c) or c+1 .. n_l1-1 (the
+        // vertices REF_L1 (c+1) .. n_seg)
+        if (dir < 0 ? c == 0 : c == n_l1 - 1) return;
+        if (STATS) cnt.l2++;
+        const float4 bb = dir < 0 ? __ldg(rb.pre + IX(REF_L1 * c, n_seg + 1))
+                                  : __ldg(rb.suf + IX(REF_L1 * (c + 1), n_seg + 1));
+        if (box_dist2(px, py, bb) > lim) return;
+        c += dir;
+        if (s + 1 == SIDE_WALK) {
+            if (dir < 0) search_range<G, STATS>(px, py, vert, seg, rb, n_seg, 0, c + 1, lane_g, mask, lfac, best, cnt);
+            else search_range<G, STATS>(px, py, vert, seg, rb, n_seg, c, n_l1, lane_g, mask, lfac, best, cnt);
+            return;
+        }
+    }
+}
+
 // Closest point of the polyline (ties -> lowest segment).  The window of REF_L1 segments around
 // the hint jh (from jh - 1, moved inside the polyline) is scanned first; the prefix box of the
 // vertices before it and the suffix box of those after it bound the rest, and a side whose box
-// passes is searched under its level-2 and chunk boxes (rare: the window keeps a segment on
-// either side of the hint).  A box is skipped only when its lower bound exceeds the best
+// passes is searched outward from the window (side_walk; on a straight lane rare: the window
+// keeps a segment on either side of the hint).  A box is skipped only when its lower bound exceeds the best
 // distance by more than binary32 rounding can account for (prune_lim), so no segment that can
 // be the closest is missed and the result does not depend on jh.  Two segments that share a
 // vertex can be closer than binary32 resolves (next to the vertex on the outside of a bend
@@ -643,10 +679,9 @@ __device__ __forceinline__ void nearest_segment(float px, float py, const float2
     const bool left = w0 >= 1 && box_dist2(px, py, __ldg(rb.pre + IX(w0, n_seg + 1))) <= lim0;
     const bool right = w1 < n_seg && box_dist2(px, py, __ldg(rb.suf + IX(w1, n_seg + 1))) <= lim0;
     if (STATS) cnt.l2 += (w0 >= 1 ? 1 : 0) + (w1 < n_seg ? 1 : 0);
-    if (left) search_range<G, STATS>(px, py, vert, seg, rb, n_seg, 0, (w0 - 1) / REF_L1 + 1, lane_g, mask, lfac,
-                                     best, cnt);
-    if (right) search_range<G, STATS>(px, py, vert, seg, rb, n_seg, w1 / REF_L1, n_l1, lane_g, mask, lfac, best,
-                                      cnt);
+    if (left) side_walk<G, STATS>(px, py, vert, seg, rb, n_seg, n_l1, lane_g, mask, lfac, (w0 - 1) / REF_L1, -1, best,
+                                  cnt);
+    if (right) side_walk<G, STATS>(px, py, vert, seg, rb, n_seg, n_l1, lane_g, mask, lfac, w1 / REF_L1, 1, best, cnt);
     float b2 = __uint_as_float((unsigned)(best >> 32));
     int bi = (int)(best & 0xffffffffu);
     const int b0 = bi;
