@@ -216,8 +216,9 @@ int mppi_autotune(mppi_ctx* ctx, const double* x0, const double* ref_xy, int32_t
 
 /* Work counters of the rollout kernel's pruned searches for one iteration on the given
    inputs (host arrays, as for mppi_plan), summed over all samples and steps, in this
-   order: range boxes tested (the prefix and suffix boxes around the scanned chunk and
-   the level-2 boxes of groups of 16 chunks), chunk boxes tested (4 segments each),
+   order: range boxes tested (the vertex prefix and suffix boxes around the scanned window
+   and beyond each chunk of a side walk, and the level-2 boxes of groups of 16 chunks),
+   chunk boxes tested (4 segments each),
    segments evaluated, binary64 near-tie refinements, circles tested by
    the broad phase, candidate circles evaluated, and square roots taken for d_obj (one
    per candidate circle within the safety band of the nearest ego circle when the ego
