@@ -13,7 +13,7 @@ import pytest
 import oracle
 import paper_2308_01654_gb300 as mp
 from paper_2308_01654_gb300 import scenarios as sc
-from parity import U_ABS_TOL, argmin_ok, assert_costs, assert_update
+from parity import MAX_EXCUSED_FAIL, U_ABS_TOL, argmin_ok, assert_costs, assert_update
 
 pytestmark = pytest.mark.gpu
 
@@ -179,6 +179,37 @@ def test_groups_give_identical_costs(scene, obstacles):
         S[g] = outs[0][3]
     for g in (2, 4, 8, 16, 32, -2, -4, -8, -16):
         np.testing.assert_array_equal(S[g], S[1], err_msg=f"group {g}")
+
+
+def _hairpin_lane():
+    """Out along y = 0, a half turn of radius 1.5 m, back along y = 3: segments of the return leg
+    (hundreds of indices away) lie 3 m from the outgoing leg, so the search's side walks run to
+    their level-2 fallback, and rollouts between the legs pass the tie of two headings 180 deg
+    apart (a few of them within 1e-4 m of it)."""
+    out = np.stack([np.arange(0.0, 20.0, 0.1), np.zeros(200)], axis=1)
+    a = np.linspace(-np.pi / 2, np.pi / 2, 48)[1:-1]
+    turn = np.stack([20.0 + 1.5 * np.cos(a), 1.5 + 1.5 * np.sin(a)], axis=1)
+    back = np.stack([np.arange(20.0, 0.0, -0.1), np.full(200, 3.0)], axis=1)
+    return np.concatenate([out, turn, back])
+
+
+def test_hairpin_lane_parity_and_lane_splits():
+    """The exact search on a lane that comes back on itself: every sample cost against the oracle's
+    brute-force search (samples within 1e-5 of a heading tie excused, at most 0.1 %), and every
+    lane split bit for bit."""
+    prob = sc.tiny(K=2048, T=40)                     # 16 m along the outgoing leg, short of the turn
+    prob.params.update(dt=0.05, sigma=[1.0, 0.3], seed=11)
+    prob.ref = _hairpin_lane()
+    prob.x0 = np.array([0.0, 0.4, 0.0, 8.0])
+    prob.circles = np.array([[12.0, 1.5, 0.6, 0.0, 0.0]])
+    prob.centres = None
+    outs, _, _, _ = run_gpu(prob)
+    orc = oracle.plan(prob)
+    rep = check_iteration(prob, outs[0], orc, max_excused_fail=MAX_EXCUSED_FAIL)
+    print("hairpin", rep)
+    for g in (2, 4, -2, -4, -8):
+        o, _, _, _ = run_gpu(prob, params=dict(prob.params, group=g))
+        np.testing.assert_array_equal(o[0][3], outs[0][3], err_msg=f"group {g}")
 
 
 @pytest.mark.parametrize("variant", ["vertex", "collision_only", "vcap", "gamma", "terminal", "dsafe_v",
