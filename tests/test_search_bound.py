@@ -112,7 +112,8 @@ def points_past_ends(rng, vx, vy, m):
 def test_no_box_can_be_skipped_against_its_own_closest_segment(kind, scale):
     """For every point and every prefix range (segments 0 .. i-1, the box of the vertices 0 .. i)
     and suffix range (segments i .., the vertices i .. n-1) — the boxes the search tests around its
-    window and in its side walks — the box's computed squared distance is at most prune_lim of the
+    window and in its side walks — and every chunk and level-2 range (the boxes of its range
+    search), the box's computed squared distance is at most prune_lim of the
     smallest computed squared distance of a segment inside it.  Then no best distance can let the
     search skip a box that holds a segment at or below it (were the box skipped against best, its
     own closest segment would be above best)."""
@@ -140,6 +141,13 @@ def test_no_box_can_be_skipped_against_its_own_closest_segment(kind, scale):
             assert np.all(bp <= prune_lim(seg_lo[:, i - 1], lfac)), (kind, scale, "prefix", i)
             bs = box_dist2(px, py, suf_x0[i], suf_y0[i], suf_x1[i], suf_y1[i])
             assert np.all(bs <= prune_lim(seg_hi[:, i], lfac)), (kind, scale, "suffix", i)
+        # the chunk boxes (4 segments: vertices 4c .. 4c + 4) and level-2 boxes (16 chunks)
+        for width in (4, 64):
+            for c0 in range(0, n - 1, width):
+                c1 = min(c0 + width, n - 1)
+                b = box_dist2(px, py, vx[c0:c1 + 1].min(), vy[c0:c1 + 1].min(), vx[c0:c1 + 1].max(),
+                              vy[c0:c1 + 1].max())
+                assert np.all(b <= prune_lim(d2[:, c0:c1].min(1), lfac)), (kind, scale, width, c0)
 
 
 def test_bound_is_close_to_the_best_distance():
