@@ -150,6 +150,26 @@ def test_no_box_can_be_skipped_against_its_own_closest_segment(kind, scale):
                 assert np.all(b <= prune_lim(d2[:, c0:c1].min(1), lfac)), (kind, scale, width, c0)
 
 
+@pytest.mark.parametrize("scale", [0.0, 1e4])
+def test_vertex_mode_boxes(scale):
+    """The closest-vertex reading (ref_mode 1) prunes its chunk and level-2 boxes with prune_lim and
+    no length term: a box of vertices holds no vertex whose computed squared distance is below
+    prune_lim's argument when the box is skipped."""
+    rng = np.random.default_rng(7 + int(scale))
+    for kind in ("straight", "zigzag", "walk"):
+        origin = rng.uniform(-scale, scale, 2)
+        vx, vy = lane(rng, kind, 257, origin)
+        px, py = points_near(rng, vx, vy, 400)
+        dx = (px[:, None] - vx[None, :]).astype(F)
+        dy = (py[:, None] - vy[None, :]).astype(F)
+        d2 = fma(dx, dx, (dy * dy).astype(F))
+        for width in (5, 65):                     # a chunk covers its 4 segments' 5 vertices
+            for c0 in range(0, 256, width - 1):
+                c1 = min(c0 + width, 257)
+                b = box_dist2(px, py, vx[c0:c1].min(), vy[c0:c1].min(), vx[c0:c1].max(), vy[c0:c1].max())
+                assert np.all(b <= prune_lim(d2[:, c0:c1].min(1), F(0.0))), (kind, scale, width, c0)
+
+
 def test_bound_is_close_to_the_best_distance():
     """On a 2000-point lane of 0.1 m segments a point 2 m off the lane may skip every box more than
     about 1.3 cm farther than its best segment (the bound adds 2^-20 (2d + 4 l) to d, and 2^-20 d)."""
