@@ -1123,8 +1123,12 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
     Counters cnt{0, 0, 0, 0, 0, 0, 0};
 
     if constexpr (!TIME) {
+        // the noise is read one step ahead (its latency is spent on the previous step's work)
+        typename NoiseT<BF16>::type znext = z[kk];
         for (int t = 0; t < T; ++t) {
-            const float2 zz = NoiseT<BF16>::load(z + (size_t)t * K + kk);
+            const typename NoiseT<BF16>::type zcur = znext;
+            znext = z[(size_t)min(t + 1, T - 1) * K + kk];
+            const float2 zz = noise_value<BF16>(zcur);
             const StepIn s = dyn_step<BF16, EXT, SIMPLE>(pc, sc.ctl[IX(t, T)], sc.c0[IX(t, T)], zz, tp, r,
                                                          steer_slot(smem, L));
             const float qx = state_cost<G, STATS, SIMPLE>(pc, L, sc, table, s, t, t, t, has_table, moving, multi_head,
@@ -1134,8 +1138,8 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
             q_last = qx;
         }
     } else {
-        // the two-lane plain form reads its noise one block of steps ahead (the load's latency
-        // is then spent on the previous block's work)
+        // the noise of a lane's own step is read one block of steps ahead (the load's latency is
+        // then spent on the previous block's work; the two-lane plain form and the general split)
         typename NoiseT<BF16>::type zpre = z[(size_t)min(lane_g, min(G, T) - 1) * K + kk];
         for (int t0 = 0; t0 < T; t0 += G) {
             // nv real steps in this block; past the last step a lane re-evaluates step T - 1
@@ -1240,8 +1244,14 @@ __device__ __forceinline__ void rollout_sample(const PlanConst& pc, const SceneL
                 }
             } else {
             // own step: perturbed controls and the steering tangent (independent of the state)
+            const typename NoiseT<BF16>::type zcur = zpre;
+            {
+                const int tn = t0 + G;
+                const int tmn = tn < T ? tn + min(lane_g, min(G, T - tn) - 1) : T - 1;
+                zpre = z[(size_t)tmn * K + kk];
+            }
             const float4 ct = sc.ctl[IX(tm, T)];
-            const Perturbed pe = perturb(ct.x, ct.y, NoiseT<BF16>::load(z + (size_t)tm * K + kk), pc.sig_a, pc.sig_d,
+            const Perturbed pe = perturb(ct.x, ct.y, noise_value<BF16>(zcur), pc.sig_a, pc.sig_d,
                                          pc.amin, pc.amax, pc.dmin, pc.dmax);
             float tn_own;
             if (EXT && pc.model == 1) {
